@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: Newton linear-solve throughput of the nested block-preconditioned
+Newton step on one GB300 (FP64, and FP32 preconditioner levels), plus BSR SpMV
+bandwidth.
+
+Workload (one bench step = one generalized-alpha time step, every part of the
+hot path: stage values, element assembly, Dirichlet elimination, diagonal
+scaling, outer FGMRES with the SCR preconditioner to 1e-10, Newton update):
+the 48^3-hex cube (663,552 P1 tets, 117,649 nodes, 470,596 linear unknowns),
+compressible neo-Hookean Gibbs material mu = 1e5 Pa, nu = 0.3 (kappa from
+nu), rho0 = 1e3, dead load 2e4 Pa on the top face ramped over 10 steps,
+dt = 1e-3, rho_inf = 0.5, sub-solver tolerances 1e-2. K timed steps run
+t = 0, dt, ..., (K-1) dt from rest (K = 10 is the whole 10-step run).
+
+metric value = linear unknowns x Newton linear solves per second over all
+ranks (replicas: every rank solves its own copy; no collective in the path).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hyel|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton linear-solve time & BSR SpMV GB/s on 1 GB300, FP64 vs mixed at 1e-9 rel"
+UNIT = "unknowns*solves/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="hyel", choices=["hyel", "reference"])
+    p.add_argument("--n", type=int, default=48, help="hexes per cube edge")
+    p.add_argument("--nu", type=float, default=0.3)
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload(args):
+    from paper_1809_06350_gb300 import inputs
+    dt = 1e-3
+    mesh = inputs.cube_mesh(args.n, jitter=0.05, seed=0)
+    mu = 1e5
+    mat = inputs.material_nh(mu, inputs.kappa_from_nu(mu, args.nu), 1e3)
+    load = {"p_max": 2e4, "t_ramp": 10 * dt}
+    return mesh, mat, load, dt
+
+
+def config_dict(args, mesh):
+    N = mesh["X"].shape[0]
+    return {"workload": f"cube{args.n}^3 compression, nu={args.nu}", "tets": int(mesh["tets"].shape[0]),
+            "nodes": int(N), "unknowns": int(4 * N), "dt": 1e-3, "rho_inf": 0.5, "outer_rtol": 1e-10,
+            "sub_rtol": 1e-2, "steps_per_run": "t = 0..K-1 from rest, load ramp over 10 steps",
+            "l2": "working set larger than L2 (FP64 blocks 218 MB, Krylov bases > 1 GB); no flush",
+            "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                r = [x.strip() for x in r]
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    src = os.path.join(ROOT, "paper_1809_06350_gb300", "csrc", "sparse.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith("- ") and ":" in line)
+        fields = {k.strip("- ").strip(): v.strip() for k, v in fields.items()}
+        if fields.get("source_sha256_16") != sha:
+            return None
+        return float(fields["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+def cpu_sample(n_sample=12, steps=2, args=None):
+    """The oracle (complex-step assembly + SuperLU direct solves) on a
+    bounded sample: the same cube workload at n_sample^3 hexes."""
+    import numpy as np
+    from oracle import newton as Nw
+    from oracle import system as S
+    from paper_1809_06350_gb300 import inputs
+    mesh = inputs.cube_mesh(n_sample, jitter=0.05, seed=0)
+    mu = 1e5
+    nu = args.nu if args else 0.3
+    mat = inputs.material_nh(mu, inputs.kappa_from_nu(mu, nu), 1e3)
+    dt = 1e-3
+    prob = S.Problem(mesh, mat, load={"p_max": 2e4, "t_ramp": 10 * dt})
+    z = inputs.zero_state(prob.N)
+    yn = {k: z[k] for k in ("u", "p", "v")}
+    ydn = {k: z[k] for k in ("udot", "pdot", "vdot")}
+    solves = 0
+    t0 = time.perf_counter()
+    for k in range(steps):
+        y1, yd1, info = Nw.newton_step(prob, yn, ydn, k * dt, dt)
+        solves += info["iterations"]
+        yn = {kk: y1[kk] for kk in ("u", "p", "v")}
+        ydn = {kk: yd1[kk] for kk in ("udot", "pdot", "vdot")}
+    sec = time.perf_counter() - t0
+    n = 4 * prob.N
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": n * solves / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle Newton steps t=0..{steps - 1} on the {n_sample}^3-hex cube "
+                      f"(n={n} unknowns, {solves} direct solves, {sec:.1f} s); rate in unknowns*solves/s"}
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    base = cpu_sample(args=args)
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        cpu_sample(n_sample=8, steps=1, args=args)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_sample(n_sample=10, steps=1, args=args)["value"])
+    sec = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    mesh, _, _, _ = workload(args)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(1, args.steps + args.warmup),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, mesh),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": "each step: oracle Newton step t=0 on the 10^3-hex cube (direct solve)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_hyel(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1809_06350_gb300 import build as bld
+    from paper_1809_06350_gb300 import hyel as H
+
+    bld.build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    mesh, mat, load, dt = workload(args)
+    N = mesh["X"].shape[0]
+    n_unk = 4 * N
+    ctx = H.hyel_create(local_rank, stream.cuda_stream)
+    inp = H.MeshInputs(mesh, mat, None, load)
+    H.hyel_mesh_upload(ctx, inp.X, inp.tets, inp.bc, inp.mat)
+    names = ("u", "p", "v", "udot", "pdot", "vdot")
+    sizes = {"u": 3 * N, "p": N, "v": 3 * N, "udot": 3 * N, "pdot": N, "vdot": 3 * N}
+    dev = {k: torch.zeros(sizes[k], dtype=torch.float64, device="cuda") for k in names}
+    state = H.state_struct(*(dev[k] for k in names))
+
+    def reset():
+        for t in dev.values():
+            t.zero_()
+
+    def run_steps(K, sp, t_offset=0, host=None):
+        its = 0
+        for k in range(K):
+            if host is not None:
+                for nm in names:
+                    dev[nm].copy_(host[nm], non_blocking=True)
+            tp = H.time_params(dt=dt, t_n=(t_offset + k) * dt)
+            st, rc = H.hyel_newton_step(ctx, tp, sp, state, raise_on_error=False)
+            if rc not in (H.HYEL_OK, H.HYEL_ENOCONV):
+                raise H.HyelError(rc, H.hyel_last_error(ctx))
+            its += st.iterations
+            if host is not None:
+                for nm in names:
+                    host[nm].copy_(dev[nm], non_blocking=True)
+        return its
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(K, sp, host=None, profile=False):
+        reset()
+        if host is not None:
+            for t in host.values():
+                t.zero_()
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            H.hyel_profile(ctx, 1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = H.hyel_launch_count()
+        e0.record(stream)
+        its = run_steps(K, sp, host=host)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = H.hyel_launch_count() - l0
+        prof = H.hyel_profile_read(ctx) if profile else None
+        if profile:
+            H.hyel_profile(ctx, 0)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            it = torch.tensor([its], device="cuda", dtype=torch.float64)
+            dist.all_reduce(it, op=dist.ReduceOp.SUM)
+            its_total = int(it.item())
+        else:
+            its_total = its
+        return ms, its, its_total, launches, prof
+
+    sp64 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP64)
+    sp32 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32)
+    # warm-up (also builds the Krylov workspaces)
+    reset()
+    run_steps(args.warmup, sp64)
+    if not args.no_mixed:
+        reset()
+        run_steps(1, sp32)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ms, its, its_total, launches, prof = timed(args.steps, sp64, profile=True)
+    ck = clocks.stop()
+
+    mixed = None
+    if not args.no_mixed:
+        msm, itsm, itsm_total, _, profm = timed(args.steps, sp32, profile=True)
+        mixed = {"value": n_unk * itsm_total / (msm / 1e3), "unit": UNIT, "ms_per_step": msm / args.steps,
+                 "newton_solves": itsm, "speedup_vs_fp64": ms / msm,
+                 "spmv_A32_gbs": (profm["spmv_A32"]["bytes"] / (profm["spmv_A32"]["ms"] / 1e3) / 1e9
+                                  if profm["spmv_A32"]["ms"] > 0 else None)}
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.zeros(sizes[k], dtype=torch.float64, pin_memory=True) for k in names}
+        mse, itse, itse_total, _, _ = timed(args.steps, sp64, host=host)
+        per = 8 * sum(sizes.values())
+        e2e = {"value": n_unk * itse_total / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": per,
+               "d2h_bytes_per_step": per}
+
+    value = n_unk * its_total / (ms / 1e3)
+    peak, peak_kind = peaks()
+    spmv = prof["spmv_A64"]
+    achieved = spmv["bytes"] / spmv["launches"] / (spmv["ms"] / spmv["launches"] / 1e3) / 1e9 if spmv["ms"] > 0 else None
+    roof = {"kernel": "k_spmv_A<double> (3x3 BSR SpMV of A, FP64, SELL-32)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": profile_traffic("spmv_A64_cube48"),
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "bytes_per_launch": spmv["bytes"] / max(1, spmv["launches"]),
+            "avg_launch_us": 1e3 * spmv["ms"] / max(1, spmv["launches"]),
+            "launches": spmv["launches"]}
+    kclass = {k: {"ms": v["ms"], "launches": v["launches"],
+                  "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None)} for k, v in prof.items()}
+    H.hyel_destroy(ctx)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_sample(args=args)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jittered cube, no dataset)",
+            "config": config_dict(args, mesh), "clocks": ck, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "cpu_baseline": cpu,
+            "newton_solves": its, "solve_ms_per_newton_it": None,
+            "mixed_fp32_preconditioner": mixed, "kernel_classes": kclass}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_hyel(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

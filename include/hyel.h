@@ -1,0 +1,279 @@
+/*
+ * hyel.h -- C ABI of libhyel: one Newton step of the VMS / generalized-alpha
+ * hyper-elastodynamics scheme on P1 tetrahedra, with the nested block
+ * preconditioned FGMRES solve, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: J. Liu, A. L. Marsden, "A robust and efficient iterative method for
+ * hyper-elastodynamics with nested block preconditioning" (arXiv:1809.06350).
+ * Section, equation, algorithm and appendix references below are to that
+ * paper; equations are named by their LaTeX labels.
+ *
+ * Conventions (every entry point):
+ *   - Returns int: HYEL_OK (0) or a negative HYEL_E* code. After a non-zero
+ *     return, hyel_last_error(ctx) holds a one-line message.
+ *   - The caller owns every pointer it passes. Host arrays are copied before
+ *     the call returns. Device arrays are borrowed for the duration of the call
+ *     and must be valid on the context's device.
+ *   - All device work is ordered on the CUDA stream given to hyel_create (or
+ *     hyel_set_stream). A call synchronizes that stream only when it returns
+ *     host-visible results (norms, statistics, convergence decisions).
+ *   - The context allocates and owns its internal device workspace (mesh,
+ *     matrix, Krylov bases); it never allocates outputs for the caller.
+ *   - Vectors of the reduced linear system are ordered x = [x_v ; x_p]:
+ *     x_v[3a+i] (node a, component i) then x_p[a]; length 4N.
+ *   - Nodal vectors: u, v, udot, vdot are [N][3] interleaved; p, pdot are [N].
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef HYEL_H
+#define HYEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define HYEL_OK           0
+#define HYEL_EINVAL      -1  /* invalid argument (null pointer, bad size, bad enum) */
+#define HYEL_ECUDA       -2  /* a CUDA runtime call failed */
+#define HYEL_ENOMEM      -3  /* device allocation failed */
+#define HYEL_ENOCONV     -4  /* a solver level or Newton hit its iteration cap */
+#define HYEL_EBREAKDOWN  -5  /* GMRES breakdown without convergence */
+#define HYEL_ENAN        -6  /* NaN or Inf met in a norm */
+#define HYEL_EINVERTED   -7  /* an element has J <= 0 (or V <= 0 at upload) */
+#define HYEL_ESINGULAR   -8  /* a 3x3 diagonal block of A is singular */
+#define HYEL_ESTATE      -9  /* call out of order (e.g. solve before assemble) */
+
+typedef struct hyel_ctx hyel_ctx;
+
+/* ---------------------------------------------------------------- inputs */
+
+/* Volumetric model (§2, §5): Gibbs energy of the compressible neo-Hookean
+ * model of §5.1 (rho(p) = rho0 (p + sqrt(p^2+kappa^2))/kappa,
+ * beta(p) = 1/sqrt(p^2+kappa^2)), or the fully incompressible G_vol = p/rho0
+ * of §5.2 (rho = rho0, beta = 0). */
+enum { HYEL_VOL_GIBBS = 0, HYEL_VOL_INCOMPRESSIBLE = 1 };
+
+/* Material (§2 constitutive relations, §5.1 and §5.2 energies).
+ * Isochoric energy per unit reference volume:
+ *   mu/2 (tr C~ - 3) + sum_{i=1..n_fibres} k1/(2 k2) (exp(k2 E_i^2) - 1),
+ *   E_i = H_i : C~ - 1,  H_i = kd I + (1 - 3 kd) a_i (x) a_i.
+ * tau_M = c_m h^e / (c rho0), h^e the longest reference edge of the element,
+ * c = sqrt((kappa + 4 mu/3)/rho0) (Gibbs) or sqrt(mu/rho0) (incompressible)
+ * evaluated with the element's mu, kappa (§3.1).
+ * Per-element host arrays (length E) override the global values when given. */
+typedef struct {
+    int32_t vol_model;          /* HYEL_VOL_* */
+    int32_t n_fibres;           /* 0 (neo-Hookean) or 2 (HGO) */
+    double  rho0;               /* reference density */
+    double  mu, kappa;          /* shear and bulk moduli (kappa unused if incompressible) */
+    double  k1, k2, kd;         /* fibre stiffness, exponent, dispersion */
+    double  c_m;                /* stabilization constant (paper: 1e-3) */
+    double  body[3];            /* body force per unit mass b */
+    const double *mu_e;         /* host [E] or NULL */
+    const double *kappa_e;      /* host [E] or NULL */
+    const double *k1_e;         /* host [E] or NULL */
+    const double *k2_e;         /* host [E] or NULL */
+    const double *fibre_a1;     /* host [E][3], required when n_fibres == 2 */
+    const double *fibre_a2;     /* host [E][3], required when n_fibres == 2 */
+} hyel_material;
+
+/* Boundary data (eq. strong_form_dirichlet_u).
+ * Dirichlet: u_i = g = value * s(t), v_i = dg/dt on the listed (node, comp),
+ * s(t) = min(t / t_ramp, 1). Neumann: a dead nominal traction
+ * H = p_max * s(t) * traction_dir on the listed reference triangles; it enters
+ * R_m as -int N_A H_i dGamma_X (Appendix A), i.e. a third of each triangle's
+ * reference area to each vertex. */
+typedef struct {
+    int64_t        n_dirichlet;
+    const int32_t *dir_node;      /* host [n_dirichlet] */
+    const int32_t *dir_comp;      /* host [n_dirichlet], 0..2 */
+    const double  *dir_value;     /* host [n_dirichlet] or NULL (all zero) */
+    int64_t        n_traction_tris;
+    const int32_t *traction_tris; /* host [n_traction_tris][3] */
+    double         traction_dir[3];
+    double         p_max;
+    double         t_ramp;        /* > 0 */
+} hyel_bc;
+
+/* Device state arrays (caller-owned). For hyel_assemble they hold stage
+ * values: u, p, v at t_{n+alpha_f} and udot, pdot, vdot at t_{n+alpha_m}.
+ * For hyel_newton_step they hold y_n and ydot_n on entry and y_{n+1},
+ * ydot_{n+1} on return. Lengths: u, v, udot, vdot [3N]; p, pdot [N]. */
+typedef struct {
+    double *u, *p, *v;
+    double *udot, *pdot, *vdot;
+} hyel_state;
+
+/* Time stepping and Newton control (§3.2, §3.3).
+ * alpha_m = (3 - rho_inf)/(2 (1 + rho_inf)), alpha_f = gamma = 1/(1 + rho_inf).
+ * Newton stops when ||R||/||R_(0)|| <= tol_r or ||R|| <= tol_a, ||R_(0)|| being
+ * the residual norm at the predictor. rhs_literal = 0 uses the exact
+ * right-hand side of eq. NR_smaller_eqn_1 (with the K_{.,udot} R_k terms);
+ * 1 uses -[R_m ; R_p] as printed in step 5 of the multi-corrector stage. */
+typedef struct {
+    double  rho_inf;
+    double  dt;
+    double  t_n;
+    double  tol_r, tol_a;
+    int32_t l_max;
+    int32_t rhs_literal;
+} hyel_time_params;
+
+/* Precision of the preconditioner levels (intermediate and inner solvers,
+ * their SpMVs and Gram-Schmidt). The outer FGMRES, its Gram-Schmidt and
+ * Givens, the residual assembly and the Newton update are always FP64. */
+enum { HYEL_PREC_FP64 = 0, HYEL_PREC_FP32 = 1 };
+
+/* One Krylov level: stop when ||r|| <= max(rtol ||b||, atol) or after maxit
+ * iterations; restart every `restart` iterations. Zero initial guess. */
+typedef struct {
+    double  rtol, atol;
+    int32_t maxit, restart;
+} hyel_krylov_level;
+
+/* Nested solver (§4.4): outer FGMRES on the scaled system with the SCR
+ * preconditioner of Algorithm 1; `a` controls the two intermediate A-solves
+ * (eq. seg_sol_int_disp, seg_sol_disp), `s` the Schur solve (eq. seg_sol_pres)
+ * right-preconditioned by point-Jacobi on diag(S^), S^ = D - C diag(A)^-1 B,
+ * and `inner` the A-solve inside the matrix-free S product (Algorithm 2,
+ * eq. S_inner_A_eqn). A-solves are right-preconditioned by the inverses of the
+ * 3x3 node-diagonal blocks of A. `check_every` = number of Krylov iterations
+ * launched between host-side convergence checks (>= 1). */
+typedef struct {
+    hyel_krylov_level outer, a, s, inner;
+    int32_t precision;      /* HYEL_PREC_* */
+    int32_t check_every;
+} hyel_solver_params;
+
+typedef struct {
+    int32_t status;         /* HYEL_OK or the failing code */
+    int32_t outer_its;      /* FGMRES iterations */
+    int64_t a_its, s_its, inner_its;       /* total iterations per level */
+    int32_t a_solves, s_solves, inner_solves;
+    double  rel_residual;   /* true ||r - A x|| / ||r|| of the scaled system */
+    double  ms_setup, ms_solve;
+} hyel_solve_stats;
+
+typedef struct {
+    int32_t status;
+    int32_t iterations;     /* Newton corrections taken */
+    int32_t converged;
+    int32_t pad_;
+    double  res_norm0, res_norm;
+    int64_t outer_its, a_its, s_its, inner_its;
+    double  ms_assemble, ms_solve, ms_total;
+} hyel_newton_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`; all work goes to `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream). */
+int hyel_create(hyel_ctx **out, int device, void *cuda_stream);
+int hyel_destroy(hyel_ctx *ctx);
+int hyel_set_stream(hyel_ctx *ctx, void *cuda_stream);
+/* Message of the last failure on this context ("" if none). NULL ctx gives the
+ * message of the last failed hyel_create on this thread. */
+const char *hyel_last_error(const hyel_ctx *ctx);
+
+/* ---------------------------------------------------------------- mesh */
+
+/* Upload a P1 tetrahedral mesh (§3.1). X: host [n_nodes][3] reference
+ * coordinates; tets: host [n_tets][4] node indices. Tetrahedra with negative
+ * signed volume are reoriented; a zero-volume tetrahedron is HYEL_EINVERTED.
+ * Builds the node-adjacency block pattern (sliced by 32 rows, see DESIGN), the
+ * element-to-block-slot gather lists and the per-element reference geometry
+ * (shape-function gradients, volume, tau_M). Replaces any previous mesh. */
+int hyel_mesh_upload(hyel_ctx *ctx, int64_t n_nodes, const double *X,
+                     int64_t n_tets, const int32_t *tets,
+                     const hyel_bc *bc, const hyel_material *mat);
+
+/* info[0] = N, [1] = E, [2] = nnzb (node-pair blocks), [3] = padded block
+ * slots (multiple of 32), [4] = device bytes held by the context. */
+int hyel_mesh_info(hyel_ctx *ctx, int64_t *info, int n);
+
+/* ---------------------------------------------------------------- assembly */
+
+/* Assemble at a stage state (Appendix A; §3.3 steps 2 and 4): residuals R_m,
+ * R_p (with traction at t_n + alpha_f dt) and the consistent tangent blocks
+ * A = K_{m,vdot} + (a_f g dt/a_m) K_{m,udot}, B = K_{m,pdot},
+ * C = K_{p,vdot} + (a_f g dt/a_m) K_{p,udot}, D = K_{p,pdot}
+ * (eq. def_matrix_A, def_matrix_D), stored internally with Dirichlet rows and
+ * columns of constrained velocity components replaced by identity.
+ *   res_out  device [4N] or NULL: [R_m ; R_p], zero on Dirichlet components.
+ *   rhs_out  device [4N] or NULL: right-hand side of eq. NR_smaller_eqn_1
+ *            (or the literal step-5 form), zero on Dirichlet components.
+ *   norms_out host [4] or NULL: ||R||, ||R_k||, ||R_p||, ||R_m|| over free
+ *            components, R_k = udot_{n+am} - v_{n+af}. (Synchronizes.)
+ * Returns HYEL_EINVERTED if some element has J <= 0 (then outputs are void). */
+int hyel_assemble(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_state *stage,
+                  double *res_out, double *rhs_out, double *norms_out);
+
+/* Copy the assembled (unscaled) blocks to host arrays in block-CSR order:
+ * row_ptr [N+1], col [nnzb] (ascending within a row), A [nnzb][3][3]
+ * (row-major), B [nnzb][3], C [nnzb][3], D [nnzb]. Any pointer may be NULL. */
+int hyel_matrix_download(hyel_ctx *ctx, int32_t *row_ptr, int32_t *col,
+                         double *A, double *B, double *C, double *D);
+
+/* ---------------------------------------------------------------- operators */
+
+enum { HYEL_OP_FULL = 0, HYEL_OP_A = 1, HYEL_OP_B = 2, HYEL_OP_C = 3, HYEL_OP_D = 4 };
+enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2 };
+
+/* y = op(M) x on device vectors. FULL: [4N] -> [4N]; A: [3N] -> [3N];
+ * B: [N] -> [3N]; C: [3N] -> [N]; D: [N] -> [N]. x, y are double for the
+ * FP64 matrices and float for HYEL_MAT_SCALED32. Scaled matrices exist after
+ * hyel_solve_setup (or a solve) on the current assembly. */
+int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y);
+
+/* Prepare the scaled system for the current assembly (§4.1): W_ii =
+ * |A_ii|^-1/2 (1 if |A_ii| < 1e-15), scaled FP64 and FP32 blocks, 3x3
+ * block-Jacobi inverses of A and diag(S^). w_out: device [4N] or NULL. */
+int hyel_solve_setup(hyel_ctx *ctx, double *w_out);
+
+/* y = S x for the scaled system (Algorithm 2: D x - C A^-1 (B x)), the inner
+ * A-solve controlled by params->inner and params->precision. x, y: device
+ * [N] double. */
+int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params,
+                     const double *x, double *y, hyel_solve_stats *stats);
+
+/* ---------------------------------------------------------------- solve */
+
+/* Solve A x = rhs for the last assembled matrix (§4): symmetric diagonal
+ * scaling, FGMRES with the nested SCR preconditioner, unscaling.
+ * rhs, x: device [4N] double. stats: host or NULL. Returns HYEL_ENOCONV if the
+ * outer solver reached its iteration cap (x then holds the last iterate). */
+int hyel_solve_nested(hyel_ctx *ctx, const hyel_solver_params *params,
+                      const double *rhs, double *x, hyel_solve_stats *stats);
+
+/* One generalized-alpha time step (§3.3): predictor, then up to l_max Newton
+ * corrections, each assembling, solving with hyel_solve_nested and updating
+ * by eq. NR_smaller_eqn_2 and step 7. state: y_n, ydot_n in, y_{n+1},
+ * ydot_{n+1} out (overwritten only on return). */
+int hyel_newton_step(hyel_ctx *ctx, const hyel_time_params *tp,
+                     const hyel_solver_params *sp, hyel_state *state,
+                     hyel_newton_stats *stats);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Kernel classes timed with CUDA events on the context's stream when enabled. */
+enum { HYEL_K_SPMV_A64 = 0, HYEL_K_SPMV_A32 = 1, HYEL_K_SPMV_FULL64 = 2,
+       HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_NCLASSES = 5 };
+
+/* enable != 0 starts event timing of the kernel classes (and clears the
+ * totals); 0 stops it. */
+int hyel_profile(hyel_ctx *ctx, int enable);
+/* Totals since the last enable: ms[k], launches[k], algorithmic bytes[k] for
+ * k < HYEL_K_NCLASSES (arrays of HYEL_K_NCLASSES, any may be NULL).
+ * Synchronizes. */
+int hyel_profile_read(hyel_ctx *ctx, double *ms, int64_t *launches, double *bytes);
+
+/* Number of kernel launches this library has issued in the process so far
+ * (all contexts). count: host. */
+int hyel_launch_count(int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYEL_H */

@@ -1,0 +1,318 @@
+// C-ABI entry points of libhyel (see include/hyel.h): argument checks, error
+// translation, context and memory management, kernel-class event timing.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+
+#include "internal.h"
+
+struct hyel_ctx {
+    hyel::Ctx c;
+};
+
+namespace hyel {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        char buf[512];
+        std::snprintf(buf, sizeof buf, "CUDA error %s (%s) in %s", cudaGetErrorName(e), cudaGetErrorString(e), what);
+        (void)cudaGetLastError();
+        throw Error{e == cudaErrorMemoryAllocation ? HYEL_ENOMEM : HYEL_ECUDA, buf};
+    }
+}
+
+void *dalloc(Ctx &c, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        fail(HYEL_ENOMEM, "cudaMalloc failed (" + std::to_string(bytes) + " bytes)");
+    }
+    c.allocations.push_back(p);
+    c.bytes_held += bytes;
+    return p;
+}
+
+void dfree_all(Ctx &c) {
+    if (!c.allocations.empty()) cudaStreamSynchronize(c.stream);
+    for (void *p : c.allocations) cudaFree(p);
+    c.allocations.clear();
+    c.bytes_held = 0;
+}
+
+void prof_begin(Ctx &c, int cls, cudaEvent_t *ev) {
+    (void)cls;
+    *ev = nullptr;
+    if (!c.prof.on) return;
+    if (c.prof.pool.empty()) {
+        cudaEvent_t e;
+        HYEL_CK(cudaEventCreate(&e));
+        c.prof.pool.push_back(e);
+    }
+    *ev = c.prof.pool.back();
+    c.prof.pool.pop_back();
+    HYEL_CK(cudaEventRecord(*ev, c.stream));
+}
+
+void prof_end(Ctx &c, int cls, cudaEvent_t ev, double bytes) {
+    if (!c.prof.on || !ev) return;
+    cudaEvent_t e2;
+    if (c.prof.pool.empty()) {
+        HYEL_CK(cudaEventCreate(&e2));
+    } else {
+        e2 = c.prof.pool.back();
+        c.prof.pool.pop_back();
+    }
+    HYEL_CK(cudaEventRecord(e2, c.stream));
+    c.prof.pending.push_back({ev, e2, cls, bytes});
+    if (c.prof.pending.size() >= 4096) {  // drain to bound the number of live events
+        HYEL_CK(cudaStreamSynchronize(c.stream));
+        for (auto &r : c.prof.pending) {
+            float ms = 0;
+            HYEL_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+            c.prof.ms[r.cls] += ms;
+            c.prof.launches[r.cls] += 1;
+            c.prof.bytes[r.cls] += r.bytes;
+            c.prof.pool.push_back(r.a);
+            c.prof.pool.push_back(r.b);
+        }
+        c.prof.pending.clear();
+    }
+}
+
+}  // namespace hyel
+
+namespace {
+
+thread_local std::string g_create_error;
+
+template <typename F>
+int guarded(hyel_ctx *ctx, F &&f) {
+    if (!ctx) return HYEL_EINVAL;
+    ctx->c.last_error.clear();
+    try {
+        cudaError_t e = cudaSetDevice(ctx->c.device);
+        if (e != cudaSuccess) hyel::check_cuda(e, "cudaSetDevice");
+        f(ctx->c);
+        return HYEL_OK;
+    } catch (const hyel::Error &e) {
+        ctx->c.last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        ctx->c.last_error = "host allocation failed";
+        return HYEL_ENOMEM;
+    } catch (const std::exception &e) {
+        ctx->c.last_error = e.what();
+        return HYEL_EINVAL;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int hyel_create(hyel_ctx **out, int device, void *cuda_stream) {
+    if (!out) return HYEL_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device < 0 || device >= count) {
+        g_create_error = "hyel_create: no such CUDA device";
+        (void)cudaGetLastError();
+        return e != cudaSuccess ? HYEL_ECUDA : HYEL_EINVAL;
+    }
+    hyel_ctx *ctx = new hyel_ctx();
+    ctx->c.device = device;
+    ctx->c.stream = (cudaStream_t)cuda_stream;
+    int rc = guarded(ctx, [](hyel::Ctx &c) {
+        HYEL_CK(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
+        HYEL_CK(cudaMallocHost(&c.h_red, 64 * sizeof(double)));
+        HYEL_CK(cudaMallocHost(&c.h_err, 4 * sizeof(unsigned)));
+    });
+    if (rc != HYEL_OK) {
+        g_create_error = ctx->c.last_error;
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return HYEL_OK;
+}
+
+int hyel_destroy(hyel_ctx *ctx) {
+    if (!ctx) return HYEL_EINVAL;
+    cudaSetDevice(ctx->c.device);
+    cudaStreamSynchronize(ctx->c.stream);
+    hyel::free_workspace(ctx->c);
+    hyel::dfree_all(ctx->c);
+    for (auto &r : ctx->c.prof.pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->c.prof.pool) cudaEventDestroy(e);
+    if (ctx->c.h_red) cudaFreeHost(ctx->c.h_red);
+    if (ctx->c.h_err) cudaFreeHost(ctx->c.h_err);
+    delete ctx;
+    return HYEL_OK;
+}
+
+int hyel_set_stream(hyel_ctx *ctx, void *cuda_stream) {
+    return guarded(ctx, [&](hyel::Ctx &c) { c.stream = (cudaStream_t)cuda_stream; });
+}
+
+const char *hyel_last_error(const hyel_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->c.last_error.c_str();
+}
+
+int hyel_mesh_upload(hyel_ctx *ctx, int64_t n_nodes, const double *X, int64_t n_tets, const int32_t *tets,
+                     const hyel_bc *bc, const hyel_material *mat) {
+    return guarded(ctx, [&](hyel::Ctx &c) { hyel::mesh_upload(c, n_nodes, X, n_tets, tets, bc, mat); });
+}
+
+int hyel_mesh_info(hyel_ctx *ctx, int64_t *info, int n) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!info || n < 0) hyel::fail(HYEL_EINVAL, "mesh_info: null output");
+        int64_t v[5] = {c.mesh.N, c.mesh.E, c.mesh.nnzb, c.mesh.nslots, (int64_t)c.bytes_held};
+        for (int k = 0; k < n && k < 5; k++) info[k] = v[k];
+    });
+}
+
+int hyel_assemble(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_state *stage, double *res_out,
+                  double *rhs_out, double *norms_out) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!tp || !stage || !stage->u || !stage->p || !stage->v || !stage->udot || !stage->pdot || !stage->vdot)
+            hyel::fail(HYEL_EINVAL, "assemble: null argument");
+        hyel::TimeConsts tc = hyel::time_consts(c.mesh, *tp);
+        hyel::assemble(c, tc, *stage, res_out, rhs_out, norms_out);
+    });
+}
+
+int hyel_matrix_download(hyel_ctx *ctx, int32_t *row_ptr, int32_t *col, double *A, double *B, double *C,
+                         double *D) {
+    return guarded(ctx, [&](hyel::Ctx &c) { hyel::matrix_download(c, row_ptr, col, A, B, C, D); });
+}
+
+int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!x || !y) hyel::fail(HYEL_EINVAL, "spmv: null vector");
+        if (op < HYEL_OP_FULL || op > HYEL_OP_D) hyel::fail(HYEL_EINVAL, "spmv: bad op");
+        if (matrix < HYEL_MAT_ASSEMBLED || matrix > HYEL_MAT_SCALED32) hyel::fail(HYEL_EINVAL, "spmv: bad matrix");
+        if (!c.mat.assembled) hyel::fail(HYEL_ESTATE, "spmv: nothing assembled");
+        if (matrix != HYEL_MAT_ASSEMBLED && !c.mat.scaled) hyel::fail(HYEL_ESTATE, "spmv: call hyel_solve_setup first");
+        hyel::DeviceMatrix &M = c.mat;
+        if (matrix == HYEL_MAT_SCALED32) {
+            const float *xf = (const float *)x;
+            float *yf = (float *)y;
+            switch (op) {
+                case HYEL_OP_A: hyel::spmv_A<float>(c, M.Af, xf, yf, nullptr); break;
+                case HYEL_OP_B: hyel::spmv_B<float>(c, M.Bf, xf, yf, nullptr, nullptr); break;
+                case HYEL_OP_C: hyel::spmv_C<float>(c, M.Cf, xf, yf, nullptr, nullptr); break;
+                case HYEL_OP_D: hyel::spmv_D<float>(c, M.Df, xf, yf, nullptr); break;
+                default: hyel::fail(HYEL_EINVAL, "spmv: FULL is available for FP64 matrices only");
+            }
+        } else {
+            const double *Av = matrix == HYEL_MAT_ASSEMBLED ? M.A : M.As;
+            const double *Bv = matrix == HYEL_MAT_ASSEMBLED ? M.B : M.Bs;
+            const double *Cv = matrix == HYEL_MAT_ASSEMBLED ? M.C : M.Cs;
+            const double *Dv = matrix == HYEL_MAT_ASSEMBLED ? M.D : M.Ds;
+            const double *xd = (const double *)x;
+            double *yd = (double *)y;
+            switch (op) {
+                case HYEL_OP_FULL: hyel::spmv_full64(c, Av, Bv, Cv, Dv, xd, yd, nullptr); break;
+                case HYEL_OP_A: hyel::spmv_A<double>(c, Av, xd, yd, nullptr); break;
+                case HYEL_OP_B: hyel::spmv_B<double>(c, Bv, xd, yd, nullptr, nullptr); break;
+                case HYEL_OP_C: hyel::spmv_C<double>(c, Cv, xd, yd, nullptr, nullptr); break;
+                case HYEL_OP_D: hyel::spmv_D<double>(c, Dv, xd, yd, nullptr); break;
+            }
+        }
+        HYEL_CK(cudaGetLastError());
+    });
+}
+
+int hyel_solve_setup(hyel_ctx *ctx, double *w_out) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        hyel::solve_setup(c);
+        if (w_out)
+            HYEL_CK(cudaMemcpyAsync(w_out, c.mat.w, 4 * c.mesh.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        HYEL_CK(cudaStreamSynchronize(c.stream));
+    });
+}
+
+int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params, const double *x, double *y,
+                     hyel_solve_stats *stats) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!params || !x || !y) hyel::fail(HYEL_EINVAL, "schur_apply: null argument");
+        hyel::schur_apply(c, *params, x, y, stats);
+    });
+}
+
+int hyel_solve_nested(hyel_ctx *ctx, const hyel_solver_params *params, const double *rhs, double *x,
+                      hyel_solve_stats *stats) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!params || !rhs || !x) hyel::fail(HYEL_EINVAL, "solve_nested: null argument");
+        hyel::solve_nested(c, *params, rhs, x, stats);
+    });
+}
+
+int hyel_newton_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solver_params *sp, hyel_state *state,
+                     hyel_newton_stats *stats) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!tp || !sp || !state || !state->u || !state->p || !state->v || !state->udot || !state->pdot ||
+            !state->vdot)
+            hyel::fail(HYEL_EINVAL, "newton_step: null argument");
+        hyel::newton_step(c, *tp, *sp, *state, stats);
+    });
+}
+
+int hyel_profile(hyel_ctx *ctx, int enable) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        HYEL_CK(cudaStreamSynchronize(c.stream));
+        for (auto &r : c.prof.pending) {
+            c.prof.pool.push_back(r.a);
+            c.prof.pool.push_back(r.b);
+        }
+        c.prof.pending.clear();
+        for (int k = 0; k < HYEL_K_NCLASSES; k++) {
+            c.prof.ms[k] = 0;
+            c.prof.launches[k] = 0;
+            c.prof.bytes[k] = 0;
+        }
+        c.prof.on = enable != 0;
+    });
+}
+
+int hyel_launch_count(int64_t *count) {
+    if (!count) return HYEL_EINVAL;
+    *count = (int64_t)hyel::g_launches.load(std::memory_order_relaxed);
+    return HYEL_OK;
+}
+
+int hyel_profile_read(hyel_ctx *ctx, double *ms, int64_t *launches, double *bytes) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        HYEL_CK(cudaStreamSynchronize(c.stream));
+        for (auto &r : c.prof.pending) {
+            float t = 0;
+            HYEL_CK(cudaEventElapsedTime(&t, r.a, r.b));
+            c.prof.ms[r.cls] += t;
+            c.prof.launches[r.cls] += 1;
+            c.prof.bytes[r.cls] += r.bytes;
+            c.prof.pool.push_back(r.a);
+            c.prof.pool.push_back(r.b);
+        }
+        c.prof.pending.clear();
+        for (int k = 0; k < HYEL_K_NCLASSES; k++) {
+            if (ms) ms[k] = c.prof.ms[k];
+            if (launches) launches[k] = c.prof.launches[k];
+            if (bytes) bytes[k] = c.prof.bytes[k];
+        }
+    });
+}
+
+}  // extern "C"

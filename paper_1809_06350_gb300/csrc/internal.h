@@ -1,0 +1,194 @@
+// Internal declarations of libhyel: context, device layouts, kernel launchers.
+//
+// Device layouts (all owned by the context):
+//   * Element data, structure-of-arrays over elements e (coalesced per thread):
+//     geo[k*E + e] for k = 0..11 the reference shape-function gradients
+//     g[A][I] = dN_A/dX_I, k = 12 the volume V, k = 13 tau_M.
+//   * Block pattern "SELL-32": rows (nodes) grouped in slices of 32; slice s
+//     owns slice_len[s] block columns starting at slice_ptr[s]; the block in
+//     slice column b for row lane t (row = 32 s + t) lives at slot b*32 + t.
+//     Column indices col[slot] (int32); a row's valid entries come first
+//     (ascending column), padding repeats the row's own index with zero values.
+//   * Block values in component-major order per 32-slot group, so that a warp
+//     reading one component of 32 consecutive rows issues one coalesced load:
+//     A[(b*9 + r*3 + c)*32 + t], B[(b*3 + r)*32 + t], C[(b*3 + c)*32 + t],
+//     D[b*32 + t].
+//   * Assembly staging: per element 18 records of 16 doubles (128 B each):
+//     records 0..15 are the node pairs (a,b) -> [A 9 | B 3 | C 3 | D 1],
+//     record 16 the element residual [a][R_m x,y,z | R_p], record 17 the
+//     K_{.,udot} R_k correction in the same form. Record (e, k) sits at
+//     stage[(((e >> 5) * 18 + k) * 32 + (e & 31)) * 16].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hyel.h"
+
+namespace hyel {
+
+constexpr int kRecords = 18;
+constexpr int kRecordDoubles = 16;
+
+// Throws are confined to host code; every C-ABI entry point converts them to
+// a status code and a message.
+struct Error {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what);
+#define HYEL_CK(call) ::hyel::check_cuda((call), #call)
+
+// Device error word bits (set by kernels, read by the host at sync points).
+enum : unsigned { ERR_INVERTED = 1u, ERR_NAN = 2u, ERR_SINGULAR = 4u };
+
+struct DeviceMesh {
+    int64_t N = 0, E = 0, nnzb = 0;
+    int32_t nslices = 0;
+    int64_t ncols = 0;   // total slice columns
+    int64_t nslots = 0;  // ncols * 32
+    int32_t n_fibres = 0;
+    int32_t vol_model = 0;
+    double rho0 = 0, kd = 0, body[3] = {0, 0, 0};
+    // traction and Dirichlet ramp
+    double t_ramp = 1.0;
+    // device arrays
+    int4 *tets = nullptr;        // [E]
+    double *geo = nullptr;       // [14][E]
+    double *mat = nullptr;       // [4][E]: mu, kappa, k1, k2
+    double *fib = nullptr;       // [6][E]: a1, a2 (n_fibres == 2)
+    int32_t *slice_ptr = nullptr;  // [nslices + 1]
+    int32_t *col_slice = nullptr;  // [ncols]: slice owning each slice column
+    int32_t *row_len = nullptr;    // [N]
+    int32_t *col = nullptr;        // [nslots]
+    int32_t *diag_slot = nullptr;  // [N]
+    int32_t *mirror = nullptr;     // [nslots]: slot of (c, r) for slot (r, c); -1 on padding
+    int32_t *slot_ptr = nullptr;   // [nslots + 1]
+    int32_t *slot_list = nullptr;  // [16 E]: staging record index e*18 + pair
+    int32_t *node_ptr = nullptr;   // [N + 1]
+    int32_t *node_list = nullptr;  // [4 E]: e*4 + a
+    uint8_t *dir = nullptr;        // [N] bit c set if component c is constrained
+    double *dir_val = nullptr;     // [3N] prescribed value at full ramp
+    double *trac = nullptr;        // [3N] int N_A H dGamma at full load
+    // host copies for downloads
+    std::vector<int32_t> h_row_ptr, h_col;  // block CSR
+    std::vector<int64_t> h_csr_slot;        // CSR position -> slot
+};
+
+struct DeviceMatrix {
+    double *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr;      // assembled
+    double *As = nullptr, *Bs = nullptr, *Cs = nullptr, *Ds = nullptr;  // scaled FP64
+    float *Af = nullptr, *Bf = nullptr, *Cf = nullptr, *Df = nullptr;   // scaled FP32
+    double *w = nullptr;        // [4N] scaling
+    double *jac64 = nullptr;    // [9][N] inverses of scaled diagonal blocks of A
+    float *jac32 = nullptr;
+    double *shat64 = nullptr;   // [N] 1 / diag(S^) of the scaled system
+    float *shat32 = nullptr;
+    bool assembled = false;
+    bool scaled = false;
+};
+
+struct GmState {
+    int done;       // stop iterating in this cycle
+    int converged;  // res <= tol
+    int k;          // iterations completed in the current cycle
+    int flags;      // 1 = NaN/Inf, 2 = breakdown
+    double beta, bnorm, tol, res, inv_scale;
+};
+
+struct Profile {
+    bool on = false;
+    struct Rec {
+        cudaEvent_t a, b;
+        int cls;
+        double bytes;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[HYEL_K_NCLASSES] = {0};
+    int64_t launches[HYEL_K_NCLASSES] = {0};
+    double bytes[HYEL_K_NCLASSES] = {0};
+};
+
+struct Workspace;  // Krylov workspaces (solver.cu)
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    DeviceMesh mesh;
+    DeviceMatrix mat;
+    double *stage = nullptr;     // staging records
+    double *vec = nullptr;       // scratch nodal vectors (see newton.cu)
+    double *red = nullptr;       // reduction partials
+    unsigned *counter = nullptr; // last-block counters
+    unsigned *err = nullptr;     // device error word
+    unsigned *h_err = nullptr;   // pinned mirror
+    double *h_red = nullptr;     // pinned scalars
+    Workspace *ws = nullptr;
+    Profile prof;
+    size_t bytes_held = 0;
+    int num_sms = 152;
+    std::vector<void *> allocations;
+};
+
+// process-wide count of kernel launches issued by this library
+void count_launch();
+
+// memory helpers
+void *dalloc(Ctx &c, size_t bytes);
+void dfree_all(Ctx &c);
+template <typename T>
+T *dalloc_n(Ctx &c, size_t n) { return static_cast<T *>(dalloc(c, n * sizeof(T))); }
+
+// profiling
+void prof_begin(Ctx &c, int cls, cudaEvent_t *ev);
+void prof_end(Ctx &c, int cls, cudaEvent_t ev, double bytes);
+
+// mesh.cu
+void mesh_upload(Ctx &c, int64_t N, const double *X, int64_t E, const int32_t *tets,
+                 const hyel_bc *bc, const hyel_material *mat);
+
+// assemble.cu
+struct TimeConsts {
+    double am, af, gam, dt, c1, c2;  // c1 = af*gam*dt, c2 = c1^2/am
+    double t_alpha, load;            // load factor s(t_alpha)
+    int literal;
+};
+TimeConsts time_consts(const DeviceMesh &m, const hyel_time_params &tp);
+// Assembles residual, rhs, tangent; returns squared norms (host) when norms != nullptr.
+void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_out, double *rhs_out,
+              double *norms4);
+void matrix_download(Ctx &c, int32_t *row_ptr, int32_t *col, double *A, double *B, double *C, double *D);
+
+// sparse.cu
+void solve_setup(Ctx &c);
+template <typename T>
+void spmv_A(Ctx &c, const T *Av, const T *x, T *y, const int *done);
+void spmv_full64(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,
+                 double *y, const int *done);
+template <typename T>
+void spmv_B(Ctx &c, const T *B, const T *xp, T *yv, const T *r, const int *done);   // yv = r - B xp (r may be null: yv = B xp)
+template <typename T>
+void spmv_C(Ctx &c, const T *C, const T *xv, T *yp, const T *r, const int *done);   // yp = r - C xv (r null: C xv)
+template <typename T>
+void spmv_D(Ctx &c, const T *D, const T *xp, T *yp, const int *done);
+template <typename T>
+void spmv_DC(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp, const int *done);  // D xp - C xv
+
+// solver.cu
+void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double *x, hyel_solve_stats *st);
+void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y, hyel_solve_stats *st);
+void free_workspace(Ctx &c);
+
+// newton.cu
+void newton_step(Ctx &c, const hyel_time_params &tp, const hyel_solver_params &sp, hyel_state &s,
+                 hyel_newton_stats *st);
+
+// launch geometry
+inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace hyel

@@ -1,0 +1,420 @@
+// Sparse kernels on the SELL-32 block storage: symmetric diagonal scaling
+// (§4.1), FP32 copies, 3x3 block-Jacobi inverses of A, the diagonal of
+// S^ = D - C diag(A)^-1 B (§4.2), and the block SpMVs used by the solver.
+//
+// SpMV mapping: one thread per block row (node); a warp covers one 32-row
+// slice, so every load of a block component is one coalesced 32-wide access.
+// x is gathered by column (three consecutive values per node). Accumulation
+// is in the value type (FP64, or FP32 for the single-precision copies), in a
+// fixed order: results are bitwise reproducible.
+#include <cmath>
+
+#include "internal.h"
+
+namespace hyel {
+
+namespace {
+
+struct ScaleArgs {
+    const int32_t *diag_slot, *col_slice, *slice_ptr, *row_len, *col, *mirror;
+    const double *A, *B, *C, *D;
+    double *As, *Bs, *Cs, *Ds;
+    float *Af, *Bf, *Cf, *Df;
+    double *w;  // [4N]
+    double *jac64;
+    float *jac32;
+    double *shat64;
+    float *shat32;
+    unsigned *err;
+    int64_t N, nslots;
+};
+
+__global__ void k_scale_diag(ScaleArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int64_t q = a.diag_slot[i], b = q >> 5, t = q & 31;
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        const double d = fabs(a.A[(b * 9 + 4 * r) * 32 + t]);
+        a.w[3 * i + r] = d >= 1e-15 ? 1.0 / sqrt(d) : 1.0;
+    }
+    const double d = fabs(a.D[b * 32 + t]);
+    a.w[3 * a.N + i] = d >= 1e-15 ? 1.0 / sqrt(d) : 1.0;
+}
+
+__global__ void k_scale_values(ScaleArgs a) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.nslots) return;
+    const int64_t b = q >> 5;
+    const int t = (int)(q & 31);
+    const int s = a.col_slice[b];
+    const int64_t r = (int64_t)s * 32 + t;
+    double wr[3] = {0, 0, 0}, wc[3] = {0, 0, 0}, wpr = 0, wpc = 0;
+    if (r < a.N && b - a.slice_ptr[s] < a.row_len[r]) {
+        const int64_t c = a.col[q];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            wr[k] = a.w[3 * r + k];
+            wc[k] = a.w[3 * c + k];
+        }
+        wpr = a.w[3 * a.N + r];
+        wpc = a.w[3 * a.N + c];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const int64_t o = (b * 9 + 3 * i + j) * 32 + t;
+            const double v = a.A[o] * wr[i] * wc[j];
+            a.As[o] = v;
+            a.Af[o] = (float)v;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int64_t o = (b * 3 + i) * 32 + t;
+        const double vb = a.B[o] * wr[i] * wpc;
+        const double vc = a.C[o] * wpr * wc[i];
+        a.Bs[o] = vb;
+        a.Bf[o] = (float)vb;
+        a.Cs[o] = vc;
+        a.Cf[o] = (float)vc;
+    }
+    const int64_t o = b * 32 + t;
+    const double vd = a.D[o] * wpr * wpc;
+    a.Ds[o] = vd;
+    a.Df[o] = (float)vd;
+}
+
+// Inverse of each scaled 3x3 diagonal block of A, stored [9][N].
+__global__ void k_jacobi(ScaleArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int64_t q = a.diag_slot[i], b = q >> 5, t = q & 31;
+    double m[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s = 0; s < 3; s++) m[r][s] = a.As[(b * 9 + 3 * r + s) * 32 + t];
+    double inv[3][3];
+    inv[0][0] = m[1][1] * m[2][2] - m[1][2] * m[2][1];
+    inv[0][1] = m[0][2] * m[2][1] - m[0][1] * m[2][2];
+    inv[0][2] = m[0][1] * m[1][2] - m[0][2] * m[1][1];
+    inv[1][0] = m[1][2] * m[2][0] - m[1][0] * m[2][2];
+    inv[1][1] = m[0][0] * m[2][2] - m[0][2] * m[2][0];
+    inv[1][2] = m[0][2] * m[1][0] - m[0][0] * m[1][2];
+    inv[2][0] = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+    inv[2][1] = m[0][1] * m[2][0] - m[0][0] * m[2][1];
+    inv[2][2] = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+    const double det = m[0][0] * inv[0][0] + m[0][1] * inv[1][0] + m[0][2] * inv[2][0];
+    double scale = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s = 0; s < 3; s++) scale = fmax(scale, fabs(m[r][s]));
+    if (!(fabs(det) > 1e-300 && fabs(det) > 1e-14 * scale * scale * scale)) {
+        atomicOr(a.err, ERR_SINGULAR);
+        return;
+    }
+    const double id = 1.0 / det;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s = 0; s < 3; s++) {
+            const double v = inv[r][s] * id;
+            a.jac64[(3 * r + s) * a.N + i] = v;
+            a.jac32[(3 * r + s) * a.N + i] = (float)v;
+        }
+}
+
+// diag(S^)_i = D_ii - sum_c sum_s C_(i,c)[s] B_(c,i)[s] / A_(c,c)[s][s]  (scaled system)
+__global__ void k_schur_hat(ScaleArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int t = (int)(i & 31);
+    const int64_t b0 = a.slice_ptr[i >> 5];
+    const int len = a.row_len[i];
+    double acc = 0.0;
+    for (int j = 0; j < len; j++) {
+        const int64_t b = b0 + j, q = b * 32 + t;
+        const int64_t c = a.col[q];
+        const int64_t mq = a.mirror[q], mb = mq >> 5, mt = mq & 31;
+        const int64_t dq = a.diag_slot[c], db = dq >> 5, dt = dq & 31;
+#pragma unroll
+        for (int s = 0; s < 3; s++) {
+            const double ad = a.As[(db * 9 + 4 * s) * 32 + dt];
+            acc += a.Cs[(b * 3 + s) * 32 + t] * a.Bs[(mb * 3 + s) * 32 + mt] / ad;
+        }
+    }
+    const int64_t dq = a.diag_slot[i], db = dq >> 5, dt = dq & 31;
+    const double sh = a.Ds[db * 32 + dt] - acc;
+    const double inv = fabs(sh) > 1e-300 ? 1.0 / sh : 1.0;
+    a.shat64[i] = inv;
+    a.shat32[i] = (float)inv;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_spmv_A(const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ row_len,
+                                                const int32_t *__restrict__ col, const T *__restrict__ A,
+                                                const T *__restrict__ x, T *__restrict__ y, int64_t N,
+                                                const int *done) {
+    if (done && *done) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const int t = (int)(r & 31);
+    const int64_t b0 = slice_ptr[r >> 5];
+    const int len = row_len[r];
+    T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 4
+    for (int j = 0; j < len; j++) {
+        const int64_t b = b0 + j;
+        const int64_t c = __ldg(col + b * 32 + t);
+        const T *Ab = A + b * 288 + t;
+        const T x0 = __ldg(x + 3 * c), x1 = __ldg(x + 3 * c + 1), x2 = __ldg(x + 3 * c + 2);
+        a0 = fma(__ldg(Ab + 0), x0, a0);
+        a0 = fma(__ldg(Ab + 32), x1, a0);
+        a0 = fma(__ldg(Ab + 64), x2, a0);
+        a1 = fma(__ldg(Ab + 96), x0, a1);
+        a1 = fma(__ldg(Ab + 128), x1, a1);
+        a1 = fma(__ldg(Ab + 160), x2, a1);
+        a2 = fma(__ldg(Ab + 192), x0, a2);
+        a2 = fma(__ldg(Ab + 224), x1, a2);
+        a2 = fma(__ldg(Ab + 256), x2, a2);
+    }
+    y[3 * r] = a0;
+    y[3 * r + 1] = a1;
+    y[3 * r + 2] = a2;
+}
+
+__global__ void __launch_bounds__(128) k_spmv_full64(const int32_t *__restrict__ slice_ptr,
+                                                     const int32_t *__restrict__ row_len,
+                                                     const int32_t *__restrict__ col, const double *__restrict__ A,
+                                                     const double *__restrict__ B, const double *__restrict__ C,
+                                                     const double *__restrict__ D, const double *__restrict__ x,
+                                                     double *__restrict__ y, int64_t N, const int *done) {
+    if (done && *done) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const int t = (int)(r & 31);
+    const int64_t b0 = slice_ptr[r >> 5];
+    const int len = row_len[r];
+    const double *xp = x + 3 * N;
+    double a0 = 0, a1 = 0, a2 = 0, ap = 0;
+#pragma unroll 2
+    for (int j = 0; j < len; j++) {
+        const int64_t b = b0 + j;
+        const int64_t c = __ldg(col + b * 32 + t);
+        const double *Ab = A + b * 288 + t;
+        const double *Bb = B + b * 96 + t;
+        const double *Cb = C + b * 96 + t;
+        const double x0 = __ldg(x + 3 * c), x1 = __ldg(x + 3 * c + 1), x2 = __ldg(x + 3 * c + 2), xq = __ldg(xp + c);
+        a0 = fma(__ldg(Ab + 0), x0, a0);
+        a0 = fma(__ldg(Ab + 32), x1, a0);
+        a0 = fma(__ldg(Ab + 64), x2, a0);
+        a0 = fma(__ldg(Bb + 0), xq, a0);
+        a1 = fma(__ldg(Ab + 96), x0, a1);
+        a1 = fma(__ldg(Ab + 128), x1, a1);
+        a1 = fma(__ldg(Ab + 160), x2, a1);
+        a1 = fma(__ldg(Bb + 32), xq, a1);
+        a2 = fma(__ldg(Ab + 192), x0, a2);
+        a2 = fma(__ldg(Ab + 224), x1, a2);
+        a2 = fma(__ldg(Ab + 256), x2, a2);
+        a2 = fma(__ldg(Bb + 64), xq, a2);
+        ap = fma(__ldg(Cb + 0), x0, ap);
+        ap = fma(__ldg(Cb + 32), x1, ap);
+        ap = fma(__ldg(Cb + 64), x2, ap);
+        ap = fma(__ldg(D + b * 32 + t), xq, ap);
+    }
+    y[3 * r] = a0;
+    y[3 * r + 1] = a1;
+    y[3 * r + 2] = a2;
+    y[3 * N + r] = ap;
+}
+
+// yv = r - B xp   (r == nullptr: yv = B xp)
+template <typename T>
+__global__ void k_spmv_B(const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ row_len,
+                         const int32_t *__restrict__ col, const T *__restrict__ B, const T *__restrict__ xp,
+                         T *__restrict__ yv, const T *__restrict__ rin, int64_t N, const int *done) {
+    if (done && *done) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const int t = (int)(r & 31);
+    const int64_t b0 = slice_ptr[r >> 5];
+    const int len = row_len[r];
+    T a0 = 0, a1 = 0, a2 = 0;
+    for (int j = 0; j < len; j++) {
+        const int64_t b = b0 + j;
+        const int64_t c = __ldg(col + b * 32 + t);
+        const T xq = __ldg(xp + c);
+        const T *Bb = B + b * 96 + t;
+        a0 = fma(__ldg(Bb), xq, a0);
+        a1 = fma(__ldg(Bb + 32), xq, a1);
+        a2 = fma(__ldg(Bb + 64), xq, a2);
+    }
+    if (rin) {
+        yv[3 * r] = rin[3 * r] - a0;
+        yv[3 * r + 1] = rin[3 * r + 1] - a1;
+        yv[3 * r + 2] = rin[3 * r + 2] - a2;
+    } else {
+        yv[3 * r] = a0;
+        yv[3 * r + 1] = a1;
+        yv[3 * r + 2] = a2;
+    }
+}
+
+// yp = r - C xv   (r == nullptr: yp = C xv)
+template <typename T>
+__global__ void k_spmv_C(const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ row_len,
+                         const int32_t *__restrict__ col, const T *__restrict__ C, const T *__restrict__ xv,
+                         T *__restrict__ yp, const T *__restrict__ rin, int64_t N, const int *done) {
+    if (done && *done) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const int t = (int)(r & 31);
+    const int64_t b0 = slice_ptr[r >> 5];
+    const int len = row_len[r];
+    T a = 0;
+    for (int j = 0; j < len; j++) {
+        const int64_t b = b0 + j;
+        const int64_t c = __ldg(col + b * 32 + t);
+        const T *Cb = C + b * 96 + t;
+        a = fma(__ldg(Cb), __ldg(xv + 3 * c), a);
+        a = fma(__ldg(Cb + 32), __ldg(xv + 3 * c + 1), a);
+        a = fma(__ldg(Cb + 64), __ldg(xv + 3 * c + 2), a);
+    }
+    yp[r] = rin ? rin[r] - a : a;
+}
+
+// yp = D xp - C xv  (xv == nullptr: yp = D xp)
+template <typename T>
+__global__ void k_spmv_DC(const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ row_len,
+                          const int32_t *__restrict__ col, const T *__restrict__ D, const T *__restrict__ C,
+                          const T *__restrict__ xp, const T *__restrict__ xv, T *__restrict__ yp, int64_t N,
+                          const int *done) {
+    if (done && *done) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const int t = (int)(r & 31);
+    const int64_t b0 = slice_ptr[r >> 5];
+    const int len = row_len[r];
+    T a = 0, m = 0;
+    for (int j = 0; j < len; j++) {
+        const int64_t b = b0 + j;
+        const int64_t c = __ldg(col + b * 32 + t);
+        a = fma(__ldg(D + b * 32 + t), __ldg(xp + c), a);
+        if (xv) {
+            const T *Cb = C + b * 96 + t;
+            m = fma(__ldg(Cb), __ldg(xv + 3 * c), m);
+            m = fma(__ldg(Cb + 32), __ldg(xv + 3 * c + 1), m);
+            m = fma(__ldg(Cb + 64), __ldg(xv + 3 * c + 2), m);
+        }
+    }
+    yp[r] = a - m;
+}
+
+ScaleArgs scale_args(Ctx &c) {
+    ScaleArgs a;
+    DeviceMesh &m = c.mesh;
+    DeviceMatrix &M = c.mat;
+    a.diag_slot = m.diag_slot;
+    a.col_slice = m.col_slice;
+    a.slice_ptr = m.slice_ptr;
+    a.row_len = m.row_len;
+    a.col = m.col;
+    a.mirror = m.mirror;
+    a.A = M.A;
+    a.B = M.B;
+    a.C = M.C;
+    a.D = M.D;
+    a.As = M.As;
+    a.Bs = M.Bs;
+    a.Cs = M.Cs;
+    a.Ds = M.Ds;
+    a.Af = M.Af;
+    a.Bf = M.Bf;
+    a.Cf = M.Cf;
+    a.Df = M.Df;
+    a.w = M.w;
+    a.jac64 = M.jac64;
+    a.jac32 = M.jac32;
+    a.shat64 = M.shat64;
+    a.shat32 = M.shat32;
+    a.err = c.err;
+    a.N = m.N;
+    a.nslots = m.nslots;
+    return a;
+}
+
+}  // namespace
+
+void solve_setup(Ctx &c) {
+    if (!c.mat.assembled) fail(HYEL_ESTATE, "solve_setup: nothing assembled");
+    if (c.mat.scaled) return;
+    ScaleArgs a = scale_args(c);
+    const int64_t N = c.mesh.N;
+    HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
+    (k_scale_diag<<<blocks_for(N, 256), 256, 0, c.stream>>>(a), ::hyel::count_launch());
+    (k_scale_values<<<blocks_for(c.mesh.nslots, 256), 256, 0, c.stream>>>(a), ::hyel::count_launch());
+    (k_jacobi<<<blocks_for(N, 256), 256, 0, c.stream>>>(a), ::hyel::count_launch());
+    (k_schur_hat<<<blocks_for(N, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
+    HYEL_CK(cudaGetLastError());
+    HYEL_CK(cudaMemcpyAsync(c.h_err, c.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    if (*c.h_err & ERR_SINGULAR) fail(HYEL_ESINGULAR, "solve_setup: a 3x3 diagonal block of A is singular");
+    c.mat.scaled = true;
+}
+
+template <typename T>
+void spmv_A(Ctx &c, const T *Av, const T *x, T *y, const int *done) {
+    const DeviceMesh &m = c.mesh;
+    const int cls = sizeof(T) == 8 ? HYEL_K_SPMV_A64 : HYEL_K_SPMV_A32;
+    cudaEvent_t ev;
+    prof_begin(c, cls, &ev);
+    (k_spmv_A<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, done), ::hyel::count_launch());
+    // algorithmic bytes: 9 values + 1 column index per block, x and y once
+    prof_end(c, cls, ev, (double)m.nnzb * (9.0 * sizeof(T) + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * sizeof(T));
+}
+template void spmv_A<double>(Ctx &, const double *, const double *, double *, const int *);
+template void spmv_A<float>(Ctx &, const float *, const float *, float *, const int *);
+
+void spmv_full64(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x, double *y,
+                 const int *done) {
+    const DeviceMesh &m = c.mesh;
+    cudaEvent_t ev;
+    prof_begin(c, HYEL_K_SPMV_FULL64, &ev);
+    (k_spmv_full64<<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, A, B, C, D, x, y, m.N,
+                                                              done), ::hyel::count_launch());
+    prof_end(c, HYEL_K_SPMV_FULL64, ev, (double)m.nnzb * (16.0 * 8 + 4.0) + 4.0 * (m.N + 1) + 2.0 * 4 * m.N * 8);
+}
+
+template <typename T>
+void spmv_B(Ctx &c, const T *B, const T *xp, T *yv, const T *r, const int *done) {
+    const DeviceMesh &m = c.mesh;
+    (k_spmv_B<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, B, xp, yv, r, m.N, done), ::hyel::count_launch());
+}
+template <typename T>
+void spmv_C(Ctx &c, const T *C, const T *xv, T *yp, const T *r, const int *done) {
+    const DeviceMesh &m = c.mesh;
+    (k_spmv_C<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, C, xv, yp, r, m.N, done), ::hyel::count_launch());
+}
+template <typename T>
+void spmv_D(Ctx &c, const T *D, const T *xp, T *yp, const int *done) {
+    const DeviceMesh &m = c.mesh;
+    (k_spmv_DC<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, D, (const T *)nullptr, xp,
+                                                             (const T *)nullptr, yp, m.N, done), ::hyel::count_launch());
+}
+template <typename T>
+void spmv_DC(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp, const int *done) {
+    const DeviceMesh &m = c.mesh;
+    (k_spmv_DC<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, D, C, xp, xv, yp, m.N, done), ::hyel::count_launch());
+}
+#define HYEL_INST(T)                                                                         \
+    template void spmv_B<T>(Ctx &, const T *, const T *, T *, const T *, const int *);       \
+    template void spmv_C<T>(Ctx &, const T *, const T *, T *, const T *, const int *);       \
+    template void spmv_D<T>(Ctx &, const T *, const T *, T *, const int *);                  \
+    template void spmv_DC<T>(Ctx &, const T *, const T *, const T *, const T *, T *, const int *);
+HYEL_INST(double)
+HYEL_INST(float)
+#undef HYEL_INST
+
+}  // namespace hyel

@@ -1,0 +1,317 @@
+"""ctypes binding of libhyel (include/hyel.h): the same entry points, argument
+marshalling only. Every computation runs in the CUDA library; if the library
+is missing this module raises instead of falling back to anything else.
+
+Device arrays are passed as raw pointers (``tensor.data_ptr()`` of CUDA
+tensors); the stream is PyTorch's current stream unless given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libhyel.so")
+
+HYEL_OK = 0
+HYEL_EINVAL, HYEL_ECUDA, HYEL_ENOMEM, HYEL_ENOCONV = -1, -2, -3, -4
+HYEL_EBREAKDOWN, HYEL_ENAN, HYEL_EINVERTED, HYEL_ESINGULAR, HYEL_ESTATE = -5, -6, -7, -8, -9
+HYEL_VOL_GIBBS, HYEL_VOL_INCOMPRESSIBLE = 0, 1
+HYEL_PREC_FP64, HYEL_PREC_FP32 = 0, 1
+HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D = 0, 1, 2, 3, 4
+HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32 = 0, 1, 2
+HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER = range(5)
+HYEL_K_NCLASSES = 5
+K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather"]
+
+# every symbol include/hyel.h declares
+EXPORTS = [
+    "hyel_create", "hyel_destroy", "hyel_set_stream", "hyel_last_error", "hyel_mesh_upload",
+    "hyel_mesh_info", "hyel_assemble", "hyel_matrix_download", "hyel_spmv", "hyel_solve_setup",
+    "hyel_schur_apply", "hyel_solve_nested", "hyel_newton_step", "hyel_profile", "hyel_profile_read",
+    "hyel_launch_count",
+]
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class HyelMaterial(C.Structure):
+    _fields_ = [("vol_model", C.c_int32), ("n_fibres", C.c_int32), ("rho0", C.c_double), ("mu", C.c_double),
+                ("kappa", C.c_double), ("k1", C.c_double), ("k2", C.c_double), ("kd", C.c_double),
+                ("c_m", C.c_double), ("body", C.c_double * 3), ("mu_e", _dp), ("kappa_e", _dp),
+                ("k1_e", _dp), ("k2_e", _dp), ("fibre_a1", _dp), ("fibre_a2", _dp)]
+
+
+class HyelBC(C.Structure):
+    _fields_ = [("n_dirichlet", C.c_int64), ("dir_node", _ip), ("dir_comp", _ip), ("dir_value", _dp),
+                ("n_traction_tris", C.c_int64), ("traction_tris", _ip), ("traction_dir", C.c_double * 3),
+                ("p_max", C.c_double), ("t_ramp", C.c_double)]
+
+
+class HyelState(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("u", "p", "v", "udot", "pdot", "vdot")]
+
+
+class HyelTimeParams(C.Structure):
+    _fields_ = [("rho_inf", C.c_double), ("dt", C.c_double), ("t_n", C.c_double), ("tol_r", C.c_double),
+                ("tol_a", C.c_double), ("l_max", C.c_int32), ("rhs_literal", C.c_int32)]
+
+
+class HyelKrylovLevel(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32)]
+
+
+class HyelSolverParams(C.Structure):
+    _fields_ = [("outer", HyelKrylovLevel), ("a", HyelKrylovLevel), ("s", HyelKrylovLevel),
+                ("inner", HyelKrylovLevel), ("precision", C.c_int32), ("check_every", C.c_int32)]
+
+
+class HyelSolveStats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("outer_its", C.c_int32), ("a_its", C.c_int64), ("s_its", C.c_int64),
+                ("inner_its", C.c_int64), ("a_solves", C.c_int32), ("s_solves", C.c_int32),
+                ("inner_solves", C.c_int32), ("rel_residual", C.c_double), ("ms_setup", C.c_double),
+                ("ms_solve", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class HyelNewtonStats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("converged", C.c_int32), ("pad_", C.c_int32),
+                ("res_norm0", C.c_double), ("res_norm", C.c_double), ("outer_its", C.c_int64),
+                ("a_its", C.c_int64), ("s_its", C.c_int64), ("inner_its", C.c_int64),
+                ("ms_assemble", C.c_double), ("ms_solve", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
+
+
+class HyelError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hyel error {code}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def lib():
+    """Load libhyel.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhyel.so is not built ({LIB_PATH}); run "
+                               "`python -m paper_1809_06350_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        sig = {
+            "hyel_create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
+            "hyel_destroy": (C.c_int, [vp]),
+            "hyel_set_stream": (C.c_int, [vp, vp]),
+            "hyel_last_error": (C.c_char_p, [vp]),
+            "hyel_mesh_upload": (C.c_int, [vp, C.c_int64, _dp, C.c_int64, _ip, C.POINTER(HyelBC),
+                                           C.POINTER(HyelMaterial)]),
+            "hyel_mesh_info": (C.c_int, [vp, C.POINTER(C.c_int64), C.c_int]),
+            "hyel_assemble": (C.c_int, [vp, C.POINTER(HyelTimeParams), C.POINTER(HyelState), vp, vp, _dp]),
+            "hyel_matrix_download": (C.c_int, [vp, _ip, _ip, _dp, _dp, _dp, _dp]),
+            "hyel_spmv": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
+            "hyel_solve_setup": (C.c_int, [vp, vp]),
+            "hyel_schur_apply": (C.c_int, [vp, C.POINTER(HyelSolverParams), vp, vp, C.POINTER(HyelSolveStats)]),
+            "hyel_solve_nested": (C.c_int, [vp, C.POINTER(HyelSolverParams), vp, vp, C.POINTER(HyelSolveStats)]),
+            "hyel_newton_step": (C.c_int, [vp, C.POINTER(HyelTimeParams), C.POINTER(HyelSolverParams),
+                                           C.POINTER(HyelState), C.POINTER(HyelNewtonStats)]),
+            "hyel_profile": (C.c_int, [vp, C.c_int]),
+            "hyel_profile_read": (C.c_int, [vp, _dp, C.POINTER(C.c_int64), _dp]),
+            "hyel_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(ctx, rc):
+    if rc != HYEL_OK:
+        msg = lib().hyel_last_error(ctx)
+        raise HyelError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+# ------------------------------------------------------------------ entry points (same names)
+
+def hyel_create(device=0, stream=None):
+    ctx = C.c_void_p()
+    rc = lib().hyel_create(C.byref(ctx), int(device), C.c_void_p(stream or 0))
+    if rc != HYEL_OK:
+        raise HyelError(rc, lib().hyel_last_error(None).decode())
+    return ctx
+
+
+def hyel_destroy(ctx):
+    return _check(ctx, lib().hyel_destroy(ctx))
+
+
+def hyel_set_stream(ctx, stream):
+    return _check(ctx, lib().hyel_set_stream(ctx, C.c_void_p(stream or 0)))
+
+
+def hyel_last_error(ctx):
+    return lib().hyel_last_error(ctx).decode()
+
+
+def hyel_mesh_upload(ctx, X, tets, bc, mat):
+    X = _arr(X, np.float64)
+    tets = _arr(tets, np.int32)
+    return _check(ctx, lib().hyel_mesh_upload(ctx, X.shape[0], _ptr(X, C.c_double), tets.shape[0],
+                                              _ptr(tets, C.c_int32), C.byref(bc), C.byref(mat)))
+
+
+def hyel_mesh_info(ctx):
+    out = (C.c_int64 * 5)()
+    _check(ctx, lib().hyel_mesh_info(ctx, out, 5))
+    return {"N": out[0], "E": out[1], "nnzb": out[2], "nslots": out[3], "bytes": out[4]}
+
+
+def hyel_assemble(ctx, tp, stage, res_out=0, rhs_out=0, want_norms=True):
+    norms = (C.c_double * 4)()
+    _check(ctx, lib().hyel_assemble(ctx, C.byref(tp), C.byref(stage), C.c_void_p(res_out or 0),
+                                    C.c_void_p(rhs_out or 0), norms if want_norms else None))
+    return list(norms)
+
+
+def hyel_matrix_download(ctx, N, nnzb):
+    rp = np.zeros(N + 1, np.int32)
+    col = np.zeros(nnzb, np.int32)
+    A = np.zeros(nnzb * 9)
+    B = np.zeros(nnzb * 3)
+    Cm = np.zeros(nnzb * 3)
+    D = np.zeros(nnzb)
+    _check(ctx, lib().hyel_matrix_download(ctx, _ptr(rp, C.c_int32), _ptr(col, C.c_int32), _ptr(A, C.c_double),
+                                           _ptr(B, C.c_double), _ptr(Cm, C.c_double), _ptr(D, C.c_double)))
+    return rp, col, A.reshape(nnzb, 3, 3), B.reshape(nnzb, 3), Cm.reshape(nnzb, 3), D
+
+
+def hyel_spmv(ctx, op, matrix, x_ptr, y_ptr):
+    return _check(ctx, lib().hyel_spmv(ctx, int(op), int(matrix), C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
+def hyel_solve_setup(ctx, w_out=0):
+    return _check(ctx, lib().hyel_solve_setup(ctx, C.c_void_p(w_out or 0)))
+
+
+def hyel_schur_apply(ctx, params, x_ptr, y_ptr):
+    st = HyelSolveStats()
+    _check(ctx, lib().hyel_schur_apply(ctx, C.byref(params), C.c_void_p(x_ptr), C.c_void_p(y_ptr), C.byref(st)))
+    return st
+
+
+def hyel_solve_nested(ctx, params, rhs_ptr, x_ptr, raise_on_error=True):
+    st = HyelSolveStats()
+    rc = lib().hyel_solve_nested(ctx, C.byref(params), C.c_void_p(rhs_ptr), C.c_void_p(x_ptr), C.byref(st))
+    if raise_on_error:
+        _check(ctx, rc)
+    return st, rc
+
+
+def hyel_newton_step(ctx, tp, sp, state, raise_on_error=True):
+    st = HyelNewtonStats()
+    rc = lib().hyel_newton_step(ctx, C.byref(tp), C.byref(sp), C.byref(state), C.byref(st))
+    if raise_on_error:
+        _check(ctx, rc)
+    return st, rc
+
+
+def hyel_profile(ctx, enable):
+    return _check(ctx, lib().hyel_profile(ctx, int(enable)))
+
+
+def hyel_profile_read(ctx):
+    ms = (C.c_double * HYEL_K_NCLASSES)()
+    n = (C.c_int64 * HYEL_K_NCLASSES)()
+    by = (C.c_double * HYEL_K_NCLASSES)()
+    _check(ctx, lib().hyel_profile_read(ctx, ms, n, by))
+    return {K_NAMES[k]: {"ms": ms[k], "launches": n[k], "bytes": by[k]} for k in range(HYEL_K_NCLASSES)}
+
+
+def hyel_launch_count():
+    n = C.c_int64()
+    rc = lib().hyel_launch_count(C.byref(n))
+    if rc != HYEL_OK:
+        raise HyelError(rc, "launch_count")
+    return n.value
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def level(rtol, maxit, restart, atol=1e-50):
+    return HyelKrylovLevel(rtol, atol, maxit, restart)
+
+
+def solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=HYEL_PREC_FP64, outer=(200, 200),
+                  a=(500, 500), s=(200, 200), inner=(500, 500), check_every=4, inner_rtol=None):
+    """Solver controls with the paper's defaults (§5: FGMRES(200), A: GMRES(500),
+    S: GMRES(200), inner GMRES(500), absolute tolerances 1e-50)."""
+    ir = sub_rtol if inner_rtol is None else inner_rtol
+    return HyelSolverParams(level(outer_rtol, *outer), level(sub_rtol, *a), level(sub_rtol, *s),
+                            level(ir, *inner), precision, check_every)
+
+
+def time_params(dt=1e-3, t_n=0.0, rho_inf=0.5, tol_r=1e-6, tol_a=1e-6, l_max=20, rhs_literal=0):
+    return HyelTimeParams(rho_inf, dt, t_n, tol_r, tol_a, l_max, rhs_literal)
+
+
+class MeshInputs:
+    """Keeps the host arrays that the C structs point to alive."""
+
+    def __init__(self, mesh, mat, fields=None, load=None):
+        fields = fields or {}
+        load = load or {"p_max": 0.0, "t_ramp": 1.0}
+        self.X = _arr(mesh["X"], np.float64)
+        self.tets = _arr(mesh["tets"], np.int32)
+        d = _arr(mesh["dirichlet"], np.int32)
+        self.dir_node = _arr(d[:, 0], np.int32)
+        self.dir_comp = _arr(d[:, 1], np.int32)
+        self.dir_val = _arr(mesh["dirichlet_values"], np.float64)
+        self.tris = _arr(mesh["traction_tris"], np.int32).reshape(-1, 3)
+        self.bc = HyelBC(len(self.dir_node), _ptr(self.dir_node, C.c_int32), _ptr(self.dir_comp, C.c_int32),
+                         _ptr(self.dir_val, C.c_double), self.tris.shape[0], _ptr(self.tris, C.c_int32),
+                         (C.c_double * 3)(*np.asarray(mesh["traction_dir"], dtype=np.float64)),
+                         float(load["p_max"]), float(load["t_ramp"]))
+        self.keep = {}
+
+        def opt(name):
+            if name in fields:
+                a = _arr(fields[name], np.float64)
+                self.keep[name] = a
+                return _ptr(a, C.c_double)
+            return None
+
+        fa1 = fa2 = None
+        if mat["fibres"]:
+            self.keep["a1"] = _arr(mesh["fibre_a1"], np.float64)
+            self.keep["a2"] = _arr(mesh["fibre_a2"], np.float64)
+            fa1 = _ptr(self.keep["a1"], C.c_double)
+            fa2 = _ptr(self.keep["a2"], C.c_double)
+        vol = HYEL_VOL_INCOMPRESSIBLE if mat["vol"] == "incompressible" else HYEL_VOL_GIBBS
+        self.mat = HyelMaterial(vol, int(mat["fibres"]), mat["rho0"], mat["mu"], mat["kappa"], mat["k1"],
+                                mat["k2"], mat["kd"], mat["c_m"], (C.c_double * 3)(*mat["body"]),
+                                opt("mu_e"), opt("kappa_e"), opt("k1_e"), opt("k2_e"), fa1, fa2)
+
+
+def state_struct(u, p, v, udot, pdot, vdot):
+    """HyelState from six CUDA tensors (float64, contiguous)."""
+    return HyelState(*(t.data_ptr() for t in (u, p, v, udot, pdot, vdot)))

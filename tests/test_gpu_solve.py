@@ -1,0 +1,136 @@
+"""GPU parity of the linear-algebra path against the oracle (config-1 cube).
+
+* block SpMVs (FP64 assembled/scaled, FP32 scaled) vs the oracle matrix;
+* the symmetric diagonal scaling W (§4.1) vs its definition;
+* the matrix-free Schur product (Algorithm 2) with a tight inner solve vs the
+  explicit dense S = D - C A^-1 B of the scaled system;
+* the nested FGMRES solve vs the oracle's direct solve: relative error <= 1e-9
+  at outer tolerance 1e-13, in FP64 and with FP32 preconditioner levels;
+* tight intermediate/inner tolerances give convergence in <= 2 outer
+  iterations (exact LDU preconditioner, §4.4);
+* status codes: iteration cap, NaN right-hand side.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+from paper_1809_06350_gb300 import hyel as H, inputs
+from oracle import system as S
+
+pytestmark = pytest.mark.gpu
+
+from gpu_support import GpuProblem  # noqa: E402
+
+DT = 1e-3
+
+
+@pytest.fixture(scope="module")
+def cube():
+    m = inputs.cube_mesh(8)
+    mat = inputs.material_nh(1e5, 1e6, 1e3)
+    gp = GpuProblem(m, mat, load={"p_max": 2e4, "t_ramp": DT})
+    prob = gp.prob
+    h = np.cbrt(prob.geo["V"].mean())
+    st = inputs.random_state(prob.N, seed=17, u_scale=0.02 * h, v_scale=0.02, p_scale=1e3, rate_scale=2.0)
+    dev, sst = gp.stage(st)
+    N = gp.N
+    rhs = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    H.hyel_assemble(gp.ctx, H.time_params(dt=DT), sst, 0, rhs.data_ptr())
+    am, af, gam = S.gen_alpha(0.5)
+    ga = (am, af, gam, DT)
+    rhs_o, _, _, _ = S.newton_rhs(prob, st, af * DT, ga)
+    K = S.assemble_matrix(prob, st, ga)
+    Kd, rhs_o = S.apply_dirichlet(K, rhs_o, S.dirichlet_dofs(prob))
+    yield {"gp": gp, "Kd": Kd, "rhs": rhs, "rhs_o": rhs_o, "dev": dev, "N": N}
+    gp.close()
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def test_spmv_full_and_blocks(cube):
+    gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
+    x = inputs.random_vector(4 * N, seed=1)
+    y = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    H.hyel_spmv(gp.ctx, H.HYEL_OP_FULL, H.HYEL_MAT_ASSEMBLED, _dev(x).data_ptr(), y.data_ptr())
+    ref = Kd @ x
+    bound = abs(Kd) @ np.abs(x)
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-13 * bound + 1e-300)
+    A, B, C, D = S.split_blocks(Kd, N)
+    for op, M, nin in ((H.HYEL_OP_A, A, 3 * N), (H.HYEL_OP_B, B, N), (H.HYEL_OP_C, C, 3 * N), (H.HYEL_OP_D, D, N)):
+        xi = inputs.random_vector(nin, seed=op)
+        yo = torch.zeros(M.shape[0], dtype=torch.float64, device="cuda")
+        H.hyel_spmv(gp.ctx, op, H.HYEL_MAT_ASSEMBLED, _dev(xi).data_ptr(), yo.data_ptr())
+        assert np.all(np.abs(yo.cpu().numpy() - M @ xi) <= 1e-13 * (abs(M) @ np.abs(xi)) + 1e-300)
+
+
+def test_scaling_and_fp32_spmv(cube):
+    gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
+    w = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    H.hyel_solve_setup(gp.ctx, w.data_ptr())
+    wo = S.diag_scaling(Kd)
+    assert np.max(np.abs(w.cpu().numpy() - wo) / wo) <= 1e-13
+    Ks = sp.diags(wo) @ Kd @ sp.diags(wo)
+    As = S.split_blocks(Ks, N)[0]
+    x = inputs.random_vector(3 * N, seed=9)
+    y = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
+    H.hyel_spmv(gp.ctx, H.HYEL_OP_A, H.HYEL_MAT_SCALED32, _dev(x, torch.float32).data_ptr(), y.data_ptr())
+    assert np.all(np.abs(y.cpu().numpy() - As @ x) <= 2e-6 * (abs(As) @ np.abs(x)))
+    y64 = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    H.hyel_spmv(gp.ctx, H.HYEL_OP_A, H.HYEL_MAT_SCALED64, _dev(x).data_ptr(), y64.data_ptr())
+    assert np.all(np.abs(y64.cpu().numpy() - As @ x) <= 1e-13 * (abs(As) @ np.abs(x)))
+
+
+@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
+def test_schur_product_algorithm2(cube, precision):
+    gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
+    H.hyel_solve_setup(gp.ctx)
+    wo = S.diag_scaling(Kd)
+    Ks = sp.diags(wo) @ Kd @ sp.diags(wo)
+    Sx = S.explicit_schur(Ks, N)
+    x = inputs.random_vector(N, seed=21)
+    y = torch.zeros(N, dtype=torch.float64, device="cuda")
+    tight = 1e-14 if precision == H.HYEL_PREC_FP64 else 1e-7
+    params = H.solver_params(precision=precision, inner_rtol=tight)
+    H.hyel_schur_apply(gp.ctx, params, _dev(x).data_ptr(), y.data_ptr())
+    ref = Sx @ x
+    err = np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= (1e-9 if precision == H.HYEL_PREC_FP64 else 1e-4), err
+
+
+@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
+def test_nested_solve_matches_direct(cube, precision):
+    gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
+    xo = S.direct_solve(Kd, cube["rhs_o"])
+    x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    params = H.solver_params(outer_rtol=1e-13, sub_rtol=1e-2, precision=precision)
+    st, rc = H.hyel_solve_nested(gp.ctx, params, cube["rhs"].data_ptr(), x.data_ptr())
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-9, (err, st.as_dict())
+    assert st.rel_residual <= 1e-12
+    assert st.outer_its >= 1
+
+
+def test_exact_ldu_preconditioner_converges_in_two(cube):
+    gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
+    x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    params = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-14)
+    st, rc = H.hyel_solve_nested(gp.ctx, params, cube["rhs"].data_ptr(), x.data_ptr())
+    assert st.outer_its <= 2, st.as_dict()
+
+
+def test_iteration_cap_and_nan(cube):
+    gp, N = cube["gp"], cube["N"]
+    x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    params = H.solver_params(outer_rtol=1e-14, sub_rtol=0.5, outer=(1, 1))
+    st, rc = H.hyel_solve_nested(gp.ctx, params, cube["rhs"].data_ptr(), x.data_ptr(), raise_on_error=False)
+    assert rc == H.HYEL_ENOCONV and st.outer_its == 1
+    bad = cube["rhs"].clone()
+    bad[5] = float("nan")
+    st, rc = H.hyel_solve_nested(gp.ctx, H.solver_params(), bad.data_ptr(), x.data_ptr(), raise_on_error=False)
+    assert rc == H.HYEL_ENAN
+    # still usable afterwards
+    st, rc = H.hyel_solve_nested(gp.ctx, H.solver_params(), cube["rhs"].data_ptr(), x.data_ptr())
+    assert rc == H.HYEL_OK
