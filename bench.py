@@ -233,6 +233,8 @@ def run_hyel(args, rank, world, local_rank):
         for t in dev.values():
             t.zero_()
 
+    acc = {"ms_solve": 0.0, "ms_assemble": 0.0}
+
     def run_steps(K, sp, t_offset=0, host=None):
         its = 0
         for k in range(K):
@@ -244,6 +246,8 @@ def run_hyel(args, rank, world, local_rank):
             if rc not in (H.HYEL_OK, H.HYEL_ENOCONV):
                 raise H.HyelError(rc, H.hyel_last_error(ctx))
             its += st.iterations
+            acc["ms_solve"] += st.ms_solve
+            acc["ms_assemble"] += st.ms_assemble
             if host is not None:
                 for nm in names:
                     host[nm].copy_(dev[nm], non_blocking=True)
@@ -298,8 +302,11 @@ def run_hyel(args, rank, world, local_rank):
 
     clocks = Clocks(local_rank)
     clocks.start()
+    acc["ms_solve"] = acc["ms_assemble"] = 0.0
     ms, its, its_total, launches, prof = timed(args.steps, sp64, profile=True)
     ck = clocks.stop()
+    solve_ms = acc["ms_solve"] / max(1, its)
+    asm_ms = acc["ms_assemble"] / max(1, its + args.steps)
 
     mixed = None
     if not args.no_mixed:
@@ -341,7 +348,7 @@ def run_hyel(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jittered cube, no dataset)",
             "config": config_dict(args, mesh), "clocks": ck, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "cpu_baseline": cpu,
-            "newton_solves": its, "solve_ms_per_newton_it": None,
+            "newton_solves": its, "solve_ms_per_newton_it": solve_ms, "assembly_ms_per_pass": asm_ms,
             "mixed_fp32_preconditioner": mixed, "kernel_classes": kclass}
     print(json.dumps(line), flush=True)
 

@@ -139,12 +139,18 @@ typedef struct {
  * right-preconditioned by point-Jacobi on diag(S^), S^ = D - C diag(A)^-1 B,
  * and `inner` the A-solve inside the matrix-free S product (Algorithm 2,
  * eq. S_inner_A_eqn). A-solves are right-preconditioned by the inverses of the
- * 3x3 node-diagonal blocks of A. `check_every` = number of Krylov iterations
- * launched between host-side convergence checks (>= 1). */
+ * 3x3 node-diagonal blocks of A.
+ * graph = 1 (default): the whole nested solve is one CUDA graph whose Krylov
+ * loops are device-driven `while` conditional nodes (no host round trip until
+ * the solve ends); the graph is built once per context and parameter set.
+ * graph = 0: the host drives the loops, checking convergence every
+ * `check_every` (>= 1) iterations. Both run the same kernels and give the
+ * same iterates. */
 typedef struct {
     hyel_krylov_level outer, a, s, inner;
     int32_t precision;      /* HYEL_PREC_* */
     int32_t check_every;
+    int32_t graph;
 } hyel_solver_params;
 
 typedef struct {

@@ -14,7 +14,14 @@ struct hyel_ctx {
 namespace hyel {
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+thread_local int *g_capture_count = nullptr;
+void count_launch() {
+    if (g_capture_count) {
+        ++*g_capture_count;
+        return;
+    }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 void fail(int code, const std::string &msg) { throw Error{code, msg}; }
 
@@ -50,7 +57,7 @@ void dfree_all(Ctx &c) {
 void prof_begin(Ctx &c, int cls, cudaEvent_t *ev) {
     (void)cls;
     *ev = nullptr;
-    if (!c.prof.on) return;
+    if (!c.prof.on || g_capture_count) return;  // no event nodes inside recorded graphs
     if (c.prof.pool.empty()) {
         cudaEvent_t e;
         HYEL_CK(cudaEventCreate(&e));
@@ -211,10 +218,10 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
             const float *xf = (const float *)x;
             float *yf = (float *)y;
             switch (op) {
-                case HYEL_OP_A: hyel::spmv_A<float>(c, M.Af, xf, yf, nullptr); break;
-                case HYEL_OP_B: hyel::spmv_B<float>(c, M.Bf, xf, yf, nullptr, nullptr); break;
-                case HYEL_OP_C: hyel::spmv_C<float>(c, M.Cf, xf, yf, nullptr, nullptr); break;
-                case HYEL_OP_D: hyel::spmv_D<float>(c, M.Df, xf, yf, nullptr); break;
+                case HYEL_OP_A: hyel::spmv_A<float>(c, M.Af, xf, yf); break;
+                case HYEL_OP_B: hyel::spmv_B<float>(c, M.Bf, xf, yf, nullptr); break;
+                case HYEL_OP_C: hyel::spmv_C<float>(c, M.Cf, xf, yf, nullptr); break;
+                case HYEL_OP_D: hyel::spmv_D<float>(c, M.Df, xf, yf); break;
                 default: hyel::fail(HYEL_EINVAL, "spmv: FULL is available for FP64 matrices only");
             }
         } else {
@@ -225,11 +232,11 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
             const double *xd = (const double *)x;
             double *yd = (double *)y;
             switch (op) {
-                case HYEL_OP_FULL: hyel::spmv_full64(c, Av, Bv, Cv, Dv, xd, yd, nullptr); break;
-                case HYEL_OP_A: hyel::spmv_A<double>(c, Av, xd, yd, nullptr); break;
-                case HYEL_OP_B: hyel::spmv_B<double>(c, Bv, xd, yd, nullptr, nullptr); break;
-                case HYEL_OP_C: hyel::spmv_C<double>(c, Cv, xd, yd, nullptr, nullptr); break;
-                case HYEL_OP_D: hyel::spmv_D<double>(c, Dv, xd, yd, nullptr); break;
+                case HYEL_OP_FULL: hyel::spmv_full64(c, Av, Bv, Cv, Dv, xd, yd); break;
+                case HYEL_OP_A: hyel::spmv_A<double>(c, Av, xd, yd); break;
+                case HYEL_OP_B: hyel::spmv_B<double>(c, Bv, xd, yd, nullptr); break;
+                case HYEL_OP_C: hyel::spmv_C<double>(c, Cv, xd, yd, nullptr); break;
+                case HYEL_OP_D: hyel::spmv_D<double>(c, Dv, xd, yd); break;
             }
         }
         HYEL_CK(cudaGetLastError());

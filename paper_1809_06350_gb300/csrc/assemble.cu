@@ -502,10 +502,12 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
     __syncthreads();
     if (last) {
         __threadfence();
-        if (threadIdx.x < 3) {
+        // warps 0..2 each sum one quantity over the block partials (fixed order)
+        if (w < 3) {
             double s = 0.0;
-            for (unsigned k = 0; k < gridDim.x; k++) s += ((volatile double *)a.partial)[3 * k + threadIdx.x];
-            sm[0][threadIdx.x] = s;
+            for (unsigned k = l; k < gridDim.x; k += 32) s += ((volatile double *)a.partial)[3 * k + w];
+            s = warp_sum(s);
+            if (l == 0) sm[0][w] = s;
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -135,8 +135,10 @@ struct Ctx {
     std::vector<void *> allocations;
 };
 
-// process-wide count of kernel launches issued by this library
+// process-wide count of kernel launches issued by this library; while a graph
+// is being recorded (g_capture_count set) launches are counted there instead
 void count_launch();
+extern thread_local int *g_capture_count;
 
 // memory helpers
 void *dalloc(Ctx &c, size_t bytes);
@@ -166,18 +168,26 @@ void matrix_download(Ctx &c, int32_t *row_ptr, int32_t *col, double *A, double *
 
 // sparse.cu
 void solve_setup(Ctx &c);
+// SpMVs. The *_ind forms take kd = (k, done) of a Krylov level (the first two
+// ints of its device state): they write basis column k+1 (column stride given)
+// and do nothing once the level is done; kd == nullptr means plain pointers.
 template <typename T>
-void spmv_A(Ctx &c, const T *Av, const T *x, T *y, const int *done);
+void spmv_A(Ctx &c, const T *Av, const T *x, T *y);
+template <typename T>
+void spmv_A_ind(Ctx &c, const T *Av, const T *x, T *y, int64_t ystride, const int *kd);
 void spmv_full64(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,
-                 double *y, const int *done);
+                 double *y);
+void spmv_full64_ind(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,
+                     double *y, int64_t stride, const int *kd);  // x column k -> y column k+1
 template <typename T>
-void spmv_B(Ctx &c, const T *B, const T *xp, T *yv, const T *r, const int *done);   // yv = r - B xp (r may be null: yv = B xp)
+void spmv_B(Ctx &c, const T *B, const T *xp, T *yv, const T *r);   // yv = r - B xp (r null: yv = B xp)
 template <typename T>
-void spmv_C(Ctx &c, const T *C, const T *xv, T *yp, const T *r, const int *done);   // yp = r - C xv (r null: C xv)
+void spmv_C(Ctx &c, const T *C, const T *xv, T *yp, const T *r);   // yp = r - C xv (r null: C xv)
 template <typename T>
-void spmv_D(Ctx &c, const T *D, const T *xp, T *yp, const int *done);
+void spmv_D(Ctx &c, const T *D, const T *xp, T *yp);
 template <typename T>
-void spmv_DC(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp, const int *done);  // D xp - C xv
+void spmv_DC_ind(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp, int64_t ystride,
+                 const int *kd);  // D xp - C xv
 
 // solver.cu
 void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double *x, hyel_solve_stats *st);

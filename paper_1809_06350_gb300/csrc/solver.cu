@@ -1,30 +1,37 @@
 // Krylov solvers and the nested block preconditioner (§4).
 //
-// * Right-preconditioned GMRES(m) and FGMRES(m) (§4, ref. Saad), zero initial
+// * Right-preconditioned GMRES(m) and FGMRES(m) (ref. Saad), zero initial
 //   guess, classical Gram-Schmidt with one full reorthogonalization (CGS2),
-//   Givens rotations on the device; stop when the rotated residual
-//   ||r|| <= max(rtol ||b||, atol) or at maxit.
+//   Givens rotations and back-substitution on the device; stop when the
+//   rotated residual ||r|| <= max(rtol ||b||, atol) or after maxit iterations.
+//   A restart takes the new starting vector from the Arnoldi relation,
+//   r = V_{k+1} Q^T (g_k e_k), so no extra operator application is needed.
 // * Outer FGMRES on the symmetrically scaled system (§4.1) with the SCR
 //   preconditioner of Algorithm 1; the Schur product of Algorithm 2 is
-//   matrix-free with an inner A-solve; S-solves are right-preconditioned by
-//   point-Jacobi on diag(S^), S^ = D - C diag(A)^-1 B (§4.2: the paper applies
-//   S^^-1 by algebraic multigrid); A-solves by the inverses of the 3x3 node
+//   matrix-free with an inner A-solve. S-solves are right-preconditioned by
+//   point-Jacobi on diag(S^), S^ = D - C diag(A)^-1 B (§4.2; the paper applies
+//   S^^-1 by algebraic multigrid), A-solves by the inverses of the 3x3 node
 //   diagonal blocks of A (the paper uses algebraic multigrid).
 // * Precision: the intermediate and inner levels (A-, S- and inner solves,
 //   their SpMVs and Gram-Schmidt) run in T = double or float; the outer
-//   FGMRES, its Gram-Schmidt and Givens stay FP64 and the flexible basis Z is
+//   FGMRES, its Gram-Schmidt and Givens stay FP64 and its flexible basis Z is
 //   FP64, so the outer iteration acts as iterative refinement.
+//
+// Control flow: every Krylov level keeps its state (iteration index, norms,
+// flags) in device memory and every kernel reads it there. The whole nested
+// solve is recorded once into a CUDA graph in which each level's iteration
+// loop is a `while` conditional node; the last kernel of an iteration sets the
+// loop condition. One graph launch performs the entire solve; the host reads
+// the level states once at the end. The same kernels can instead be replayed
+// by a host loop (params.graph = 0).
 //
 // Every reduction has a fixed grid and a fixed summation order (per-block
 // partials, then the last block to finish sums them in block order), so all
 // results are bitwise reproducible.
-//
-// Each iteration's kernels read the level's device state and return at once
-// when it is marked done, so the host may launch several iterations between
-// convergence checks (``check_every``) without changing the result.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <functional>
 
 #include "internal.h"
@@ -34,8 +41,24 @@ namespace hyel {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxK = 512;   // largest restart supported by the shared-memory coefficient buffers
-constexpr int KC = 8;        // columns per multi-dot chunk
+constexpr int kMaxK = 512;  // largest restart supported by the shared-memory coefficient buffers
+constexpr int KC = 8;       // columns per multi-dot chunk
+
+struct LevelState {
+    int k;          // basis vectors completed in the current cycle (iteration index j of the next one)
+    int done;       // current cycle finished
+    int stop;       // solve finished
+    int converged;  // res <= tol
+    int flags;      // 1 = NaN/Inf, 2 = breakdown without convergence
+    int total;      // iterations of this solve
+    int maxit, m;
+    int cycles;
+    int solves;        // completed solves since reset (statistics)
+    long long its;     // iterations since reset (statistics)
+    int status_any;    // OR of flags over solves since reset (1 nan, 2 breakdown, 4 cap reached)
+    int yok;           // y = R^-1 g was formed for the finished cycle
+    double beta, bnorm, tol, res, inv_scale;
+};
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -50,7 +73,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Mark this block done; returns true in the last block to finish (all other
-// blocks' partials are then visible to it).
+// blocks' writes are then visible to it).
 __device__ __forceinline__ bool last_block(unsigned *counter) {
     __shared__ bool last;
     __threadfence();
@@ -61,18 +84,93 @@ __device__ __forceinline__ bool last_block(unsigned *counter) {
     return last;
 }
 
-enum { MD_STORE = 0, MD_INIT_FIRST = 1, MD_INIT_RESTART = 2, MD_DOT = 3 };
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, unsigned v) {
+    if (h) cudaGraphSetConditional(h, v);
+}
 
-// h[k] = sum_i V[k*ld + i] w[i], k < nk. Modes:
-//   MD_STORE: out[k] = h[k].
-//   MD_INIT_FIRST / MD_INIT_RESTART (nk = 1, w = V): beta = ||V_0||, cycle start.
-//   MD_DOT: out[0] = h[0] (no state).
+// Sum over the grid's per-block partials p[b*stride + k] for k < nk, by the
+// last block: warp w handles columns w, w + nwarps, ...; its lanes stride over
+// the blocks; the order is fixed, so the sum is reproducible.
+__device__ __forceinline__ void sum_partials(const double *p, int stride, int nk, double *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < nk; k += nw) {
+        double s = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) s += ((volatile const double *)p)[(int64_t)b * stride + k];
+        s = warp_sum_d(s);
+        if (lane == 0) out[k] = s;
+    }
+}
+
+// Block-wide sum of one double (all threads get the result in thread 0).
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    v = warp_sum_d(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q];
+    __syncthreads();
+    return t;
+}
+
+// Start of a solve: V0 = b, x = 0, beta = ||b||, state, loop condition.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_multidot(const T *__restrict__ V, int64_t ld, int nk,
-                                                       const T *__restrict__ w, int64_t n, double *partial,
-                                                       unsigned *counter, double *out, GmState *st, int mode,
-                                                       double *g, int m, double rtol, double atol) {
-    if (st && mode == MD_STORE && st->done) return;
+__global__ void __launch_bounds__(kThreads) k_init(const T *__restrict__ b, T *__restrict__ V0, T *__restrict__ x,
+                                                   int64_t n, double *partial, unsigned *counter, LevelState *st,
+                                                   double *g, int m, double rtol, double atol, int maxit,
+                                                   cudaGraphConditionalHandle h) {
+    __shared__ double red[kThreads / 32];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    T ss = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const T v = b[i];
+        V0[i] = v;
+        x[i] = 0;
+        ss = fma(v, v, ss);
+    }
+    const double t = block_sum((double)ss, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    if (!last_block(counter)) return;
+    __shared__ double tot;
+    sum_partials(partial, 1, 1, &tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double beta = sqrt(tot);
+        st->k = 0;
+        st->total = 0;
+        st->cycles = 0;
+        st->maxit = maxit;
+        st->m = m;
+        st->beta = beta;
+        st->bnorm = beta;
+        st->tol = fmax(rtol * beta, atol);
+        st->res = beta;
+        st->inv_scale = beta > 0.0 ? 1.0 / beta : 0.0;
+        const int nan = isfinite(beta) ? 0 : 1;
+        st->flags = nan;
+        st->converged = (!nan && beta <= st->tol) ? 1 : 0;
+        st->stop = (st->converged || nan) ? 1 : 0;
+        st->done = st->stop;
+        if (st->stop) {
+            st->solves += 1;
+            st->status_any |= nan;
+        }
+        g[0] = beta;
+        for (int l = 1; l <= m; l++) g[l] = 0.0;
+        set_cond(h, st->stop ? 0u : 1u);
+        *counter = 0u;
+    }
+}
+
+// h[l] = V_l . w, l <= k (w = V_{k+1}); pass 1 stores into Hessenberg column k,
+// pass 2 into h2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_multidot(const T *__restrict__ V, int64_t n, double *partial,
+                                                       unsigned *counter, double *H, double *h2,
+                                                       const LevelState *st, int pass) {
+    if (st->done) return;
+    const int j = st->k, nk = j + 1, m = st->m;
+    const T *w = V + (int64_t)(j + 1) * n;
     __shared__ double red[kThreads / 32][KC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -85,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_multidot(const T *__restrict__ V, 
             const T wi = w[i];
 #pragma unroll
             for (int c = 0; c < KC; c++)
-                if (c < kc) acc[c] = fma(V[(int64_t)(k0 + c) * ld + i], wi, acc[c]);
+                if (c < kc) acc[c] = fma(V[(int64_t)(k0 + c) * n + i], wi, acc[c]);
         }
 #pragma unroll
         for (int c = 0; c < KC; c++) {
@@ -97,69 +195,51 @@ __global__ void __launch_bounds__(kThreads) k_multidot(const T *__restrict__ V, 
             double s = 0.0;
 #pragma unroll
             for (int q = 0; q < kThreads / 32; q++) s += red[q][threadIdx.x];
-            partial[(int64_t)blockIdx.x * nk + k0 + threadIdx.x] = s;
+            partial[(int64_t)blockIdx.x * (m + 1) + k0 + threadIdx.x] = s;
         }
         __syncthreads();
     }
     if (!last_block(counter)) return;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; b++) s += ((volatile double *)partial)[(int64_t)b * nk + k];
-        if (mode == MD_STORE || mode == MD_DOT) out[k] = s;
-        if (mode == MD_INIT_FIRST || mode == MD_INIT_RESTART) {
-            const double beta = sqrt(s);
-            if (mode == MD_INIT_FIRST) {
-                st->bnorm = beta;
-                st->tol = fmax(rtol * beta, atol);
-            }
-            st->beta = beta;
-            st->k = 0;
-            st->res = beta;
-            st->inv_scale = beta > 0.0 ? 1.0 / beta : 0.0;
-            st->converged = (beta <= st->tol) ? 1 : 0;
-            st->flags = isfinite(beta) ? 0 : 1;
-            st->done = (st->converged || st->flags) ? 1 : 0;
-            g[0] = beta;
-            for (int l = 1; l <= m; l++) g[l] = 0.0;
-        }
-    }
+    double *out = pass == 1 ? H + (int64_t)j * (m + 1) : h2;
+    sum_partials(partial, m + 1, nk, out);
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// w -= sum_k V_k h[k]
+// w -= sum_l V_l h_l with h the Hessenberg column k (first CGS pass).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_multiaxpy(const T *__restrict__ V, int64_t ld, int nk,
-                                                        const double *__restrict__ h, T *__restrict__ w, int64_t n,
-                                                        const GmState *st) {
+__global__ void __launch_bounds__(kThreads) k_multiaxpy(T *__restrict__ V, int64_t n, const double *__restrict__ H,
+                                                        const LevelState *st) {
     if (st->done) return;
+    const int j = st->k, nk = j + 1, m = st->m;
+    T *w = V + (int64_t)(j + 1) * n;
     __shared__ T hs[kMaxK];
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = (T)h[k];
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = (T)H[(int64_t)j * (m + 1) + k];
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         T acc = w[i];
         int k = 0;
         for (; k + 4 <= nk; k += 4) {
-            acc = fma(-V[(int64_t)k * ld + i], hs[k], acc);
-            acc = fma(-V[(int64_t)(k + 1) * ld + i], hs[k + 1], acc);
-            acc = fma(-V[(int64_t)(k + 2) * ld + i], hs[k + 2], acc);
-            acc = fma(-V[(int64_t)(k + 3) * ld + i], hs[k + 3], acc);
+            acc = fma(-V[(int64_t)k * n + i], hs[k], acc);
+            acc = fma(-V[(int64_t)(k + 1) * n + i], hs[k + 1], acc);
+            acc = fma(-V[(int64_t)(k + 2) * n + i], hs[k + 2], acc);
+            acc = fma(-V[(int64_t)(k + 3) * n + i], hs[k + 3], acc);
         }
-        for (; k < nk; k++) acc = fma(-V[(int64_t)k * ld + i], hs[k], acc);
+        for (; k < nk; k++) acc = fma(-V[(int64_t)k * n + i], hs[k], acc);
         w[i] = acc;
     }
 }
 
-// Second CGS pass update, norm of the new basis vector and the Givens step on
-// Hessenberg column j (done by the last block).
+// Second CGS pass, norm of the new basis vector, Givens step on column j, the
+// stopping decision, and (when the cycle ends) y = R^-1 g.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_axpy_norm_givens(const T *__restrict__ V, int64_t ld, int j,
-                                                               const double *__restrict__ h2, T *__restrict__ w,
-                                                               int64_t n, double *partial, unsigned *counter,
-                                                               double *H, double *cs, double *sn, double *g,
-                                                               GmState *st, int m) {
+__global__ void __launch_bounds__(kThreads) k_axpy_norm_givens(T *__restrict__ V, int64_t n,
+                                                               const double *__restrict__ h2, double *partial,
+                                                               unsigned *counter, double *H, double *cs, double *sn,
+                                                               double *g, double *y, LevelState *st) {
     if (st->done) return;
-    const int nk = j + 1;
+    const int j = st->k, nk = j + 1, m = st->m;
+    T *w = V + (int64_t)(j + 1) * n;
     __shared__ T hs[kMaxK];
     __shared__ double red[kThreads / 32];
     for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = (T)h2[k];
@@ -170,31 +250,26 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm_givens(const T *__restri
         T acc = w[i];
         int k = 0;
         for (; k + 4 <= nk; k += 4) {
-            acc = fma(-V[(int64_t)k * ld + i], hs[k], acc);
-            acc = fma(-V[(int64_t)(k + 1) * ld + i], hs[k + 1], acc);
-            acc = fma(-V[(int64_t)(k + 2) * ld + i], hs[k + 2], acc);
-            acc = fma(-V[(int64_t)(k + 3) * ld + i], hs[k + 3], acc);
+            acc = fma(-V[(int64_t)k * n + i], hs[k], acc);
+            acc = fma(-V[(int64_t)(k + 1) * n + i], hs[k + 1], acc);
+            acc = fma(-V[(int64_t)(k + 2) * n + i], hs[k + 2], acc);
+            acc = fma(-V[(int64_t)(k + 3) * n + i], hs[k + 3], acc);
         }
-        for (; k < nk; k++) acc = fma(-V[(int64_t)k * ld + i], hs[k], acc);
+        for (; k < nk; k++) acc = fma(-V[(int64_t)k * n + i], hs[k], acc);
         w[i] = acc;
         ss = fma(acc, acc, ss);
     }
-    const T s = warp_sum(ss);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < kThreads / 32; q++) t += red[q];
-        partial[blockIdx.x] = t;
-    }
+    const double tb = block_sum((double)ss, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tb;
     if (!last_block(counter)) return;
     double *Hc = H + (int64_t)j * (m + 1);
     for (int k = threadIdx.x; k < nk; k += blockDim.x) Hc[k] += h2[k];
+    __shared__ int s_done;
+    __shared__ double tot;
+    sum_partials(partial, 1, 1, &tot);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (unsigned b = 0; b < gridDim.x; b++) t += ((volatile double *)partial)[b];
-        const double hn = sqrt(t);
+        const double hn = sqrt(tot);
         Hc[j + 1] = hn;
         for (int l = 0; l < j; l++) {
             const double a0 = Hc[l], a1 = Hc[l + 1];
@@ -221,103 +296,176 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm_givens(const T *__restri
         g[j + 1] = -s2 * gj;
         const double res = fabs(g[j + 1]);
         st->k = j + 1;
+        st->total += 1;
         st->res = res;
         st->inv_scale = hn > 0.0 ? 1.0 / hn : 0.0;
-        int done = 0;
+        int done = 0, stop = 0;
         if (!isfinite(res) || !isfinite(hn)) {
             st->flags |= 1;
-            done = 1;
+            done = stop = 1;
+        } else if (r == 0.0) {  // singular Hessenberg: no least-squares solution this cycle
+            st->flags |= 2;
+            done = stop = 1;
         } else if (res <= st->tol) {
             st->converged = 1;
-            done = 1;
-        } else if (r == 0.0 || hn == 0.0) {
-            st->flags |= 2;  // breakdown without convergence
+            done = stop = 1;
+        } else if (hn == 0.0) {  // invariant subspace without convergence
+            st->flags |= 2;
+            done = stop = 1;
+        } else if (st->total >= st->maxit) {
+            done = stop = 1;
+        } else if (j + 1 == m) {
             done = 1;
         }
-        if (j + 1 == m) done = 1;
         st->done = done;
+        st->stop = stop;
+        s_done = done && isfinite(res) && isfinite(hn) && r != 0.0;
+        st->yok = s_done;
+        *counter = 0u;
+    }
+    __syncthreads();
+    if (s_done && threadIdx.x < 32) {  // y = R^-1 g over the k = j+1 columns (warp 0)
+        const int k = j + 1, lane = threadIdx.x;
+        for (int i = k - 1; i >= 0; i--) {
+            double s = 0.0;
+            for (int l = i + 1 + lane; l < k; l += 32) s += H[(int64_t)l * (m + 1) + i] * y[l];
+            s = warp_sum_d(s);
+            if (lane == 0) y[i] = (g[i] - s) / H[(int64_t)i * (m + 1) + i];
+            __syncwarp();
+        }
+    }
+}
+
+// End of an iteration: when the cycle is done, x += M^-1 V y (KIND 0: 3x3
+// block-Jacobi per node, KIND 1: diagonal) or x += Z y (KIND 2); if the solve
+// continues (restart), V_0 = V Q^T (g_k e_k) and a new cycle starts. Sets the
+// loop condition.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kThreads) k_cycle_end(T *__restrict__ V, const T *__restrict__ Z, T *__restrict__ x,
+                                                        const T *__restrict__ prec, int64_t n, const double *y,
+                                                        const double *cs, const double *sn, double *g,
+                                                        unsigned *counter, LevelState *st,
+                                                        cudaGraphConditionalHandle h) {
+    if (!st->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(h, 1u);
+        return;
+    }
+    if (st->stop == 2) return;  // already finalized (host-driven replays)
+    const int k = st->k, stop = st->stop;
+    __shared__ T ys[kMaxK];
+    __shared__ T cr[kMaxK + 1];
+    const bool usable = st->yok && k > 0;
+    for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = usable ? (T)y[l] : (T)0;
+    if (!stop && threadIdx.x == 0) {
+        // c = G_0^T G_1^T ... G_{k-1}^T (g_k e_k); G_i^T maps (a_i, a_{i+1}) to
+        // (cs a_i - sn a_{i+1}, sn a_i + cs a_{i+1}), and a_i = 0 when it is applied
+        double carry = g[k];
+        for (int i = k - 1; i >= 0; i--) {
+            cr[i + 1] = (T)(cs[i] * carry);
+            carry = -sn[i] * carry;
+        }
+        cr[0] = (T)carry;
+    }
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (usable) {
+        if (KIND == 0) {
+            const int64_t N3 = n / 3;
+            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N3; i += stride) {
+                T u0 = 0, u1 = 0, u2 = 0;
+                for (int l = 0; l < k; l++) {
+                    const T *Vl = V + (int64_t)l * n + 3 * i;
+                    u0 = fma(Vl[0], ys[l], u0);
+                    u1 = fma(Vl[1], ys[l], u1);
+                    u2 = fma(Vl[2], ys[l], u2);
+                }
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+                    x[3 * i + r] += prec[(3 * r) * N3 + i] * u0 + prec[(3 * r + 1) * N3 + i] * u1 +
+                                    prec[(3 * r + 2) * N3 + i] * u2;
+            }
+        } else {
+            const T *B = KIND == 2 ? Z : V;
+            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+                T u = 0;
+                for (int l = 0; l < k; l++) u = fma(B[(int64_t)l * n + i], ys[l], u);
+                if (KIND == 1) u *= prec[i];
+                x[i] += u;
+            }
+        }
+    }
+    if (!stop) {
+        // restart vector (unnormalised) into V_0; element-wise, in place
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            T r = 0;
+            for (int l = 0; l <= k; l++) r = fma(V[(int64_t)l * n + i], cr[l], r);
+            V[i] = r;
+        }
+    }
+    if (!last_block(counter)) return;
+    if (threadIdx.x == 0) {
+        if (stop) {
+            st->its += st->total;
+            st->solves += 1;
+            st->status_any |= st->flags | ((!st->converged && !st->flags) ? 4 : 0);
+            st->stop = 2;
+            set_cond(h, 0u);
+        } else {
+            const double beta = fabs(g[k]);
+            st->k = 0;
+            st->done = 0;
+            st->cycles += 1;
+            st->beta = beta;
+            st->res = beta;
+            st->inv_scale = beta > 0.0 ? 1.0 / beta : 0.0;
+            g[0] = beta;
+            for (int l = 1; l <= st->m; l++) g[l] = 0.0;
+            set_cond(h, 1u);
+        }
         *counter = 0u;
     }
 }
 
-// y = R^-1 g over the first k = st->k columns (one warp).
-__global__ void k_backsolve(const double *H, const double *g, double *y, const GmState *st, int m) {
-    const int k = st->k;
-    const int lane = threadIdx.x;
-    for (int i = k - 1; i >= 0; i--) {
-        double s = 0.0;
-        for (int l = i + 1 + lane; l < k; l += 32) s += H[(int64_t)l * (m + 1) + i] * y[l];
-        s = warp_sum_d(s);
-        if (lane == 0) y[i] = (g[i] - s) / H[(int64_t)i * (m + 1) + i];
-        __syncwarp();
-    }
-}
-
-// x (+)= jac * (sum_l V_l y_l) per node (GMRES on A with block-Jacobi).
+// v_k *= inv_scale; z = jac v_k  (block-Jacobi, per node)
 template <typename T>
-__global__ void k_update_bjac(const T *__restrict__ V, int64_t ld, const double *__restrict__ y,
-                              const T *__restrict__ jac, T *__restrict__ x, int64_t N, const GmState *st, int accumulate) {
-    __shared__ T ys[kMaxK];
-    const int k = st->k;
-    for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = (T)y[l];
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    T u0 = 0, u1 = 0, u2 = 0;
-    for (int l = 0; l < k; l++) {
-        const T *Vl = V + (int64_t)l * ld + 3 * i;
-        u0 = fma(Vl[0], ys[l], u0);
-        u1 = fma(Vl[1], ys[l], u1);
-        u2 = fma(Vl[2], ys[l], u2);
-    }
-    T z[3];
-#pragma unroll
-    for (int r = 0; r < 3; r++) z[r] = jac[(3 * r) * N + i] * u0 + jac[(3 * r + 1) * N + i] * u1 + jac[(3 * r + 2) * N + i] * u2;
-#pragma unroll
-    for (int r = 0; r < 3; r++) x[3 * i + r] = (accumulate ? x[3 * i + r] : (T)0) + z[r];
-}
-
-// x (+)= diag * (sum_l V_l y_l) (point Jacobi) or x (+)= sum_l Z_l y_l (diag == nullptr).
-template <typename T>
-__global__ void k_update_diag(const T *__restrict__ V, int64_t ld, const double *__restrict__ y,
-                              const T *__restrict__ diag, T *__restrict__ x, int64_t n, const GmState *st, int accumulate) {
-    __shared__ T ys[kMaxK];
-    const int k = st->k;
-    for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = (T)y[l];
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T u = 0;
-    for (int l = 0; l < k; l++) u = fma(V[(int64_t)l * ld + i], ys[l], u);
-    if (diag) u *= diag[i];
-    x[i] = (accumulate ? x[i] : (T)0) + u;
-}
-
-// v_j *= inv_scale; z = jac v_j  (block-Jacobi, per node)
-template <typename T>
-__global__ void k_scale_bjac(T *__restrict__ v, T *__restrict__ z, const T *__restrict__ jac, int64_t N, const GmState *st) {
+__global__ void k_scale_bjac(T *__restrict__ V, T *__restrict__ z, const T *__restrict__ jac, int64_t N,
+                             const LevelState *st) {
     if (st->done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    T *v = V + (int64_t)st->k * 3 * N;
     const T s = (T)st->inv_scale;
     const T v0 = v[3 * i] * s, v1 = v[3 * i + 1] * s, v2 = v[3 * i + 2] * s;
     v[3 * i] = v0;
     v[3 * i + 1] = v1;
     v[3 * i + 2] = v2;
 #pragma unroll
-    for (int r = 0; r < 3; r++) z[3 * i + r] = jac[(3 * r) * N + i] * v0 + jac[(3 * r + 1) * N + i] * v1 + jac[(3 * r + 2) * N + i] * v2;
+    for (int r = 0; r < 3; r++)
+        z[3 * i + r] = jac[(3 * r) * N + i] * v0 + jac[(3 * r + 1) * N + i] * v1 + jac[(3 * r + 2) * N + i] * v2;
 }
 
-// v_j *= inv_scale; z = diag .* v_j (diag == nullptr: scale only)
+// v_k *= inv_scale; z = diag .* v_k (diag == nullptr: scale only, z unused)
 template <typename T>
-__global__ void k_scale_diag(T *__restrict__ v, T *__restrict__ z, const T *__restrict__ diag, int64_t n, const GmState *st) {
+__global__ void k_scale_diag(T *__restrict__ V, T *__restrict__ z, const T *__restrict__ diag, int64_t n,
+                             const LevelState *st) {
     if (st->done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const T s = (T)st->inv_scale;
-    const T vi = v[i] * s;
+    T *v = V + (int64_t)st->k * n;
+    const T vi = v[i] * (T)st->inv_scale;
     v[i] = vi;
     if (diag) z[i] = diag[i] * vi;
+}
+
+// dst = (Tout) src with src/dst offset by (k + ofs) * stride when indexed by a level state
+template <typename Tin, typename Tout>
+__global__ void k_copy_ind(const Tin *__restrict__ src, Tout *__restrict__ dst, int64_t n, const LevelState *st,
+                           int64_t src_stride, int64_t dst_stride) {
+    if (st && st->done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = st ? st->k : 0;
+    dst[(int64_t)k * dst_stride + i] = (Tout)src[(int64_t)k * src_stride + i];
 }
 
 template <typename T>
@@ -326,180 +474,100 @@ __global__ void k_sub(const T *__restrict__ b, T *__restrict__ r, int64_t n) {  
     if (i < n) r[i] = b[i] - r[i];
 }
 
-template <typename Tin, typename Tout>
-__global__ void k_cast(const Tin *__restrict__ a, Tout *__restrict__ b, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (Tout)a[i];
-}
-
 __global__ void k_mul(const double *__restrict__ a, const double *__restrict__ w, double *__restrict__ b, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = a[i] * w[i];
 }
 
-// ------------------------------------------------------------ host driver
+// sum of squares into out (fixed grid, last block sums)
+__global__ void __launch_bounds__(kThreads) k_sumsq(const double *__restrict__ r, int64_t n, double *partial,
+                                                    unsigned *counter, double *out) {
+    __shared__ double red[kThreads / 32];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double ss = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) ss = fma(r[i], r[i], ss);
+    const double t = block_sum(ss, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    if (!last_block(counter)) return;
+    sum_partials(partial, 1, 1, out);
+    if (threadIdx.x == 0) *counter = 0u;
+}
 
-struct Level {
-    int64_t its = 0;
-    int32_t solves = 0;
-};
+// ------------------------------------------------------------ recording
 
-template <typename T>
-struct Gmres {
+// Records kernel sequences either as direct launches driven by a host loop or
+// into a CUDA graph with while-conditional nodes.
+struct Rec {
     Ctx *c = nullptr;
-    int64_t n = 0;
-    int m = 0;
-    bool flexible = false;
-    T *V = nullptr, *Z = nullptr, *z = nullptr;
-    double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h2 = nullptr;
-    double *partial = nullptr;
-    unsigned *counter = nullptr;
-    GmState *st = nullptr;
-    GmState *hst = nullptr;
-    int grid = 0;
-    std::vector<void *> mem;
+    bool graph = false;
+    int check_every = 1;
+    std::vector<cudaStream_t> *streams = nullptr;  // capture streams by depth
+    int depth = 0;
+    // kernel-node bookkeeping for launch counting: per level state, kernels
+    // per iteration and per solve
+    struct Site {
+        LevelState *st;
+        int body_nodes;
+        int init_nodes;
+    };
+    std::vector<Site> *sites = nullptr;
+    int *capture_count = nullptr;
 
-    void *alloc(size_t bytes) {
-        void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, bytes);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            fail(HYEL_ENOMEM, "solver workspace: cudaMalloc failed");
+    // run body() while the level is not stopped; init(h) starts the solve
+    void loop(LevelState *st, int every, const std::function<void(cudaGraphConditionalHandle)> &init,
+              const std::function<void(cudaGraphConditionalHandle)> &body) {
+        if (!graph) {
+            LevelState hs;
+            init(0);
+            for (;;) {
+                HYEL_CK(cudaMemcpyAsync(&hs, st, sizeof(LevelState), cudaMemcpyDeviceToHost, c->stream));
+                HYEL_CK(cudaStreamSynchronize(c->stream));
+                if (hs.stop) break;
+                for (int r = 0; r < every; r++) body(0);
+            }
+            return;
         }
-        mem.push_back(p);
-        c->bytes_held += bytes;
-        return p;
-    }
-    void init(Ctx *ctx, int64_t n_, int m_, bool flex) {
-        c = ctx;
-        n = n_;
-        m = m_;
-        flexible = flex;
-        grid = (int)std::max<int64_t>(1, std::min<int64_t>(2 * c->num_sms, (n + 4 * kThreads - 1) / (4 * kThreads)));
-        V = (T *)alloc(sizeof(T) * (size_t)(m + 1) * n);
-        if (flexible)
-            Z = (T *)alloc(sizeof(T) * (size_t)m * n);
-        else
-            z = (T *)alloc(sizeof(T) * (size_t)n);
-        H = (double *)alloc(sizeof(double) * (size_t)(m + 1) * m);
-        cs = (double *)alloc(sizeof(double) * m);
-        sn = (double *)alloc(sizeof(double) * m);
-        g = (double *)alloc(sizeof(double) * (m + 1));
-        y = (double *)alloc(sizeof(double) * m);
-        h2 = (double *)alloc(sizeof(double) * (m + 1));
-        partial = (double *)alloc(sizeof(double) * (size_t)grid * (m + 1));
-        counter = (unsigned *)alloc(sizeof(unsigned) * 4);
-        st = (GmState *)alloc(sizeof(GmState));
-        HYEL_CK(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, c->stream));
-        HYEL_CK(cudaMemsetAsync(st, 0, sizeof(GmState), c->stream));
-        HYEL_CK(cudaMallocHost(&hst, sizeof(GmState)));
-    }
-    void release() {
-        for (void *p : mem) cudaFree(p);
-        mem.clear();
-        if (hst) cudaFreeHost(hst);
-        hst = nullptr;
-    }
-    void read_state() {
-        HYEL_CK(cudaMemcpyAsync(hst, st, sizeof(GmState), cudaMemcpyDeviceToHost, c->stream));
-        HYEL_CK(cudaStreamSynchronize(c->stream));
-    }
-    T *Vcol(int j) { return V + (size_t)j * n; }
-
-    // Solve Op M^-1 u = b, x = M^-1 u (or FGMRES with Z). kind: 0 = block-Jacobi
-    // (n = 3N), 1 = point-diagonal, 2 = flexible (prec callback).
-    // Returns status; its accumulates iterations.
-    int solve(const T *b, T *x, const hyel_krylov_level &L, int kind, const T *pdata,
-              const std::function<void(const T *, T *, const int *)> &op,
-              const std::function<void(const T *, T *)> &prec, int check_every, int64_t &its) {
-        if (L.restart > m) fail(HYEL_EINVAL, "gmres: restart larger than workspace");
-        const int mm = std::min(L.restart, m);
-        const int64_t N3 = n / 3;
-        HYEL_CK(cudaMemcpyAsync(Vcol(0), b, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream));
-        (k_multidot<T><<<grid, kThreads, 0, c->stream>>>(V, n, 1, Vcol(0), n, partial, counter, nullptr, st,
-                                                        MD_INIT_FIRST, g, mm, L.rtol, L.atol), ::hyel::count_launch());
-        HYEL_CK(cudaGetLastError());
-        int64_t total = 0;
-        bool first = true;
-        int status = HYEL_OK;
-        for (;;) {
-            read_state();
-            if (hst->done) {
-                if (hst->flags & 1) return HYEL_ENAN;
-                if (first) HYEL_CK(cudaMemsetAsync(x, 0, sizeof(T) * n, c->stream));
-                break;
-            }
-            int j = 0;
-            for (; j < mm && total + j < L.maxit; j++) {
-                T *vj = Vcol(j);
-                T *w = Vcol(j + 1);
-                T *zj = flexible ? Z + (size_t)j * n : z;
-                if (kind == 0) {
-                    (k_scale_bjac<T><<<blocks_for(N3, 128), 128, 0, c->stream>>>(vj, zj, pdata, N3, st), ::hyel::count_launch());
-                } else if (kind == 1) {
-                    (k_scale_diag<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(vj, zj, pdata, n, st), ::hyel::count_launch());
-                } else {
-                    (k_scale_diag<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(vj, zj, (const T *)nullptr, n, st), ::hyel::count_launch());
-                    prec(vj, zj);
-                }
-                op(zj, w, &st->done);
-                (k_multidot<T><<<grid, kThreads, 0, c->stream>>>(V, n, j + 1, w, n, partial, counter,
-                                                                H + (size_t)j * (mm + 1), st, MD_STORE, g, mm, 0, 0), ::hyel::count_launch());
-                (k_multiaxpy<T><<<grid, kThreads, 0, c->stream>>>(V, n, j + 1, H + (size_t)j * (mm + 1), w, n, st), ::hyel::count_launch());
-                (k_multidot<T><<<grid, kThreads, 0, c->stream>>>(V, n, j + 1, w, n, partial, counter, h2, st, MD_STORE,
-                                                                g, mm, 0, 0), ::hyel::count_launch());
-                (k_axpy_norm_givens<T><<<grid, kThreads, 0, c->stream>>>(V, n, j, h2, w, n, partial, counter, H, cs, sn,
-                                                                        g, st, mm), ::hyel::count_launch());
-                HYEL_CK(cudaGetLastError());
-                const bool last_it = (j + 1 == mm) || (total + j + 1 >= L.maxit);
-                if (kind == 2 || last_it || ((j + 1) % std::max(1, check_every)) == 0) {
-                    read_state();
-                    if (hst->done) break;
-                }
-            }
-            read_state();
-            const int k = hst->k;
-            if (k > 0) {
-                (k_backsolve<<<1, 32, 0, c->stream>>>(H, g, y, st, mm), ::hyel::count_launch());
-                const int acc = first ? 0 : 1;
-                if (kind == 0)
-                    (k_update_bjac<T><<<blocks_for(N3, 128), 128, 0, c->stream>>>(V, n, y, pdata, x, N3, st, acc), ::hyel::count_launch());
-                else if (kind == 1)
-                    (k_update_diag<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(V, n, y, pdata, x, n, st, acc), ::hyel::count_launch());
-                else
-                    (k_update_diag<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(Z, n, y, (const T *)nullptr, x, n, st,
-                                                                               acc), ::hyel::count_launch());
-                HYEL_CK(cudaGetLastError());
-            } else if (first) {
-                HYEL_CK(cudaMemsetAsync(x, 0, sizeof(T) * n, c->stream));
-            }
-            first = false;
-            total += k;
-            if (hst->flags & 1) {
-                status = HYEL_ENAN;
-                break;
-            }
-            if (hst->converged) break;
-            if (hst->flags & 2) {
-                status = HYEL_EBREAKDOWN;
-                break;
-            }
-            if (total >= L.maxit) {
-                status = HYEL_ENOCONV;
-                break;
-            }
-            // restart: r = b - Op(x)
-            op(x, Vcol(0), nullptr);
-            (k_sub<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(b, Vcol(0), n), ::hyel::count_launch());
-            (k_multidot<T><<<grid, kThreads, 0, c->stream>>>(V, n, 1, Vcol(0), n, partial, counter, nullptr, st,
-                                                            MD_INIT_RESTART, g, mm, 0, 0), ::hyel::count_launch());
-            HYEL_CK(cudaGetLastError());
-            if (kind == 0 || kind == 1) {
-                // the non-flexible update needs x only after the cycle; nothing else to do
-            }
+        cudaStream_t s = c->stream;
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t g;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        HYEL_CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &nd));
+        cudaGraphConditionalHandle h;
+        HYEL_CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        const int before_init = *capture_count;
+        init(h);
+        const int init_nodes = *capture_count - before_init;
+        HYEL_CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &nd));
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        HYEL_CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+        HYEL_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+        if ((int)streams->size() <= depth + 1) {
+            cudaStream_t ns;
+            HYEL_CK(cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking));
+            streams->push_back(ns);
         }
-        its += total;
-        return status;
+        cudaStream_t bs = (*streams)[depth + 1];
+        HYEL_CK(cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        c->stream = bs;
+        depth++;
+        const int before_body = *capture_count;
+        const size_t nsites = sites->size();
+        body(h);
+        // nodes of nested loops are accounted to their own sites
+        int nested = 0;
+        for (size_t q = nsites; q < sites->size(); q++) nested += (*sites)[q].body_nodes + (*sites)[q].init_nodes;
+        const int body_nodes = *capture_count - before_body - nested;
+        depth--;
+        c->stream = s;
+        cudaGraph_t outg;
+        HYEL_CK(cudaStreamEndCapture(bs, &outg));
+        sites->push_back({st, body_nodes, init_nodes});
     }
 };
 
@@ -507,23 +575,52 @@ struct Gmres {
 
 // ------------------------------------------------------------ workspace
 
+namespace {
+
+template <typename T>
+struct Level {
+    int64_t n = 0;
+    int m = 0;
+    int kind = 0;
+    T *V = nullptr, *Z = nullptr, *z = nullptr;
+    double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h2 = nullptr;
+    double *partial = nullptr;
+    unsigned *counter = nullptr;
+    int grid = 0;
+};
+
+}  // namespace
+
 struct Workspace {
     int m_outer = 0, m_a = 0, m_s = 0, prec = -1;
-    Gmres<double> outer;
-    Gmres<double> a64, s64;
-    Gmres<float> a32, s32;
-    // vectors (sized 4N each), typed views
+    Level<double> outer;
+    Level<double> a64, s64;
+    Level<float> a32, s32;
+    LevelState *states = nullptr;  // [5]: outer, a1, a2, s, inner
+    LevelState *h_states = nullptr;
     double *d = nullptr;  // 12 x 4N doubles
     float *f = nullptr;   // 12 x 4N floats
     std::vector<void *> mem;
+    // cached graph
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    hyel_solver_params key;
+    bool have_key = false;
+    std::vector<cudaStream_t> streams;
+    std::vector<Rec::Site> sites;
+    int top_nodes = 0;
+
     void release() {
-        outer.release();
-        a64.release();
-        s64.release();
-        a32.release();
-        s32.release();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        for (cudaStream_t s : streams) cudaStreamDestroy(s);
+        streams.clear();
         for (void *p : mem) cudaFree(p);
         mem.clear();
+        if (h_states) cudaFreeHost(h_states);
+        h_states = nullptr;
     }
 };
 
@@ -537,6 +634,37 @@ void free_workspace(Ctx &c) {
 
 namespace {
 
+void *walloc(Ctx &c, Workspace &w, size_t bytes) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        fail(HYEL_ENOMEM, "solver workspace: cudaMalloc failed");
+    }
+    w.mem.push_back(p);
+    c.bytes_held += bytes;
+    return p;
+}
+
+template <typename T>
+void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
+    L.n = n;
+    L.m = m;
+    L.kind = kind;
+    L.grid = (int)std::max<int64_t>(1, std::min<int64_t>(2 * c.num_sms, (n + 4 * kThreads - 1) / (4 * kThreads)));
+    L.V = (T *)walloc(c, w, sizeof(T) * (size_t)(m + 1) * n);
+    if (kind == 2) L.Z = (T *)walloc(c, w, sizeof(T) * (size_t)m * n);
+    L.z = (T *)walloc(c, w, sizeof(T) * (size_t)n);
+    L.H = (double *)walloc(c, w, sizeof(double) * (size_t)(m + 1) * m);
+    L.cs = (double *)walloc(c, w, sizeof(double) * m);
+    L.sn = (double *)walloc(c, w, sizeof(double) * m);
+    L.g = (double *)walloc(c, w, sizeof(double) * (m + 1));
+    L.y = (double *)walloc(c, w, sizeof(double) * m);
+    L.h2 = (double *)walloc(c, w, sizeof(double) * (m + 1));
+    L.partial = (double *)walloc(c, w, sizeof(double) * (size_t)L.grid * (m + 1));
+    L.counter = (unsigned *)walloc(c, w, sizeof(unsigned) * 4);
+    HYEL_CK(cudaMemsetAsync(L.counter, 0, sizeof(unsigned) * 4, c.stream));
+}
+
 Workspace &workspace(Ctx &c, const hyel_solver_params &p) {
     const int mo = p.outer.restart, ma = std::max(p.a.restart, p.inner.restart), ms = p.s.restart;
     Workspace *w = c.ws;
@@ -549,24 +677,19 @@ Workspace &workspace(Ctx &c, const hyel_solver_params &p) {
     w->m_a = ma;
     w->m_s = ms;
     w->prec = p.precision;
-    w->outer.init(&c, 4 * N, mo, true);
+    level_init(c, *w, w->outer, 4 * N, mo, 2);
     if (p.precision == HYEL_PREC_FP64) {
-        w->a64.init(&c, 3 * N, ma, false);
-        w->s64.init(&c, N, ms, false);
+        level_init(c, *w, w->a64, 3 * N, ma, 0);
+        level_init(c, *w, w->s64, N, ms, 1);
     } else {
-        w->a32.init(&c, 3 * N, ma, false);
-        w->s32.init(&c, N, ms, false);
+        level_init(c, *w, w->a32, 3 * N, ma, 0);
+        level_init(c, *w, w->s32, N, ms, 1);
     }
-    void *pd = nullptr, *pf = nullptr;
-    if (cudaMalloc(&pd, sizeof(double) * 12 * 4 * (size_t)N) != cudaSuccess ||
-        cudaMalloc(&pf, sizeof(float) * 12 * 4 * (size_t)N) != cudaSuccess) {
-        (void)cudaGetLastError();
-        fail(HYEL_ENOMEM, "solver workspace: cudaMalloc failed");
-    }
-    w->mem.push_back(pd);
-    w->mem.push_back(pf);
-    w->d = (double *)pd;
-    w->f = (float *)pf;
+    w->states = (LevelState *)walloc(c, *w, sizeof(LevelState) * 5);
+    HYEL_CK(cudaMemsetAsync(w->states, 0, sizeof(LevelState) * 5, c.stream));
+    HYEL_CK(cudaMallocHost(&w->h_states, sizeof(LevelState) * 5));
+    w->d = (double *)walloc(c, *w, sizeof(double) * 12 * 4 * (size_t)N);
+    w->f = (float *)walloc(c, *w, sizeof(float) * 12 * 4 * (size_t)N);
     return *w;
 }
 
@@ -578,9 +701,14 @@ void check_params(const hyel_solver_params &p) {
         if (!(l->rtol >= 0) || !(l->atol >= 0)) fail(HYEL_EINVAL, "solver params: tolerances must be >= 0");
     }
     if (p.precision != HYEL_PREC_FP64 && p.precision != HYEL_PREC_FP32) fail(HYEL_EINVAL, "solver params: bad precision");
+    if (p.check_every < 1) fail(HYEL_EINVAL, "solver params: check_every must be >= 1");
 }
 
-// Typed view of the scaled matrix and the level solvers for precision T.
+bool same_params(const hyel_solver_params &a, const hyel_solver_params &b) {
+    return std::memcmp(&a, &b, sizeof a) == 0;
+}
+
+// Typed view of the scaled matrix and the levels for precision T.
 template <typename T>
 struct Sys;
 template <>
@@ -591,8 +719,8 @@ struct Sys<double> {
     static const double *D(Ctx &c) { return c.mat.Ds; }
     static const double *jac(Ctx &c) { return c.mat.jac64; }
     static const double *shat(Ctx &c) { return c.mat.shat64; }
-    static Gmres<double> &ga(Workspace &w) { return w.a64; }
-    static Gmres<double> &gs(Workspace &w) { return w.s64; }
+    static Level<double> &la(Workspace &w) { return w.a64; }
+    static Level<double> &ls(Workspace &w) { return w.s64; }
     static double *vec(Workspace &w, int k, int64_t N) { return w.d + (size_t)k * 4 * N; }
 };
 template <>
@@ -603,66 +731,189 @@ struct Sys<float> {
     static const float *D(Ctx &c) { return c.mat.Df; }
     static const float *jac(Ctx &c) { return c.mat.jac32; }
     static const float *shat(Ctx &c) { return c.mat.shat32; }
-    static Gmres<float> &ga(Workspace &w) { return w.a32; }
-    static Gmres<float> &gs(Workspace &w) { return w.s32; }
+    static Level<float> &la(Workspace &w) { return w.a32; }
+    static Level<float> &ls(Workspace &w) { return w.s32; }
     static float *vec(Workspace &w, int k, int64_t N) { return w.f + (size_t)k * 4 * N; }
 };
 
-struct Counters {
-    Level a, s, inner;
-    int status = HYEL_OK;
-    void note(int st) {
-        if (status == HYEL_OK && st != HYEL_OK && st != HYEL_ENOCONV) status = st;
-    }
-};
+enum { ST_OUTER = 0, ST_A1 = 1, ST_A2 = 2, ST_S = 3, ST_INNER = 4 };
 
-// A-solve: x = A^-1 b with the given level controls.
-template <typename T>
-void a_solve(Ctx &c, Workspace &w, const hyel_solver_params &p, const hyel_krylov_level &L, const T *b, T *x,
-             Level &lv, Counters &cnt) {
-    Gmres<T> &g = Sys<T>::ga(w);
-    auto op = [&c](const T *in, T *out, const int *done) { spmv_A<T>(c, Sys<T>::A(c), in, out, done); };
-    int st = g.solve(b, x, L, 0, Sys<T>::jac(c), op, nullptr, p.check_every, lv.its);
-    lv.solves++;
-    cnt.note(st);
+#define LAUNCH(...) ((__VA_ARGS__), ::hyel::count_launch())
+
+// One GMRES/FGMRES solve of level L: the init kernel, then the iteration
+// loop. prec_flex (KIND 2) maps V_k to Z_k; op maps the preconditioned vector
+// (z, or Z_k for KIND 2) to V_{k+1}.
+template <typename T, int KIND>
+void gm_solve(Rec &R, Level<T> &L, LevelState *st, const hyel_krylov_level &P, const T *b, T *x, const T *prec,
+              const std::function<void()> &prec_flex, const std::function<void()> &op) {
+    Ctx &c = *R.c;
+    const int m = std::min(P.restart, L.m);
+    // host-driven mode may run several cheap A-level iterations between checks
+    // (the kernels of an iteration after the stop do nothing); levels whose
+    // operator is itself a solve are checked every iteration
+    R.loop(
+        st, KIND == 0 ? R.check_every : 1,
+        [&](cudaGraphConditionalHandle h) {
+            LAUNCH(k_init<T><<<L.grid, kThreads, 0, c.stream>>>(b, L.V, x, L.n, L.partial, L.counter, st, L.g, m,
+                                                               P.rtol, P.atol, P.maxit, h));
+        },
+        [&](cudaGraphConditionalHandle h) {
+            if (KIND == 0)
+                LAUNCH(k_scale_bjac<T><<<blocks_for(L.n / 3, 128), 128, 0, c.stream>>>(L.V, L.z, prec, L.n / 3, st));
+            else if (KIND == 1)
+                LAUNCH(k_scale_diag<T><<<blocks_for(L.n, 256), 256, 0, c.stream>>>(L.V, L.z, prec, L.n, st));
+            else {
+                LAUNCH(k_scale_diag<T><<<blocks_for(L.n, 256), 256, 0, c.stream>>>(L.V, (T *)nullptr, (const T *)nullptr,
+                                                                                  L.n, st));
+                prec_flex();
+            }
+            op();
+            LAUNCH(k_multidot<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.partial, L.counter, L.H, L.h2, st, 1));
+            LAUNCH(k_multiaxpy<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.H, st));
+            LAUNCH(k_multidot<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.partial, L.counter, L.H, L.h2, st, 2));
+            LAUNCH(k_axpy_norm_givens<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.h2, L.partial, L.counter, L.H,
+                                                                            L.cs, L.sn, L.g, L.y, st));
+            LAUNCH(k_cycle_end<T, KIND><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.Z, x, prec, L.n, L.y, L.cs, L.sn, L.g,
+                                                                          L.counter, st, h));
+        });
 }
 
-// Algorithm 2: y = D x - C A^-1 (B x)
+// A-solve x = A^-1 b
 template <typename T>
-void schur_op(Ctx &c, Workspace &w, const hyel_solver_params &p, const T *x, T *y, Counters &cnt) {
+void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, const T *b, T *x) {
+    Ctx &c = *R.c;
+    Level<T> &L = Sys<T>::la(w);
+    gm_solve<T, 0>(R, L, st, P, b, x, Sys<T>::jac(c), nullptr, [&]() {
+        spmv_A_ind<T>(c, Sys<T>::A(c), L.z, L.V, L.n, &st->k);
+    });
+}
+
+// Algorithm 2: y = D x - C A^-1 (B x), y indexed by the S-level state
+template <typename T>
+void schur_op(Rec &R, Workspace &w, const hyel_solver_params &p, const T *x, T *y, const int *yk, int64_t ystride) {
+    Ctx &c = *R.c;
     const int64_t N = c.mesh.N;
     T *xbar = Sys<T>::vec(w, 4, N);
     T *xtil = Sys<T>::vec(w, 5, N);
-    spmv_B<T>(c, Sys<T>::B(c), x, xbar, nullptr, nullptr);
-    a_solve<T>(c, w, p, p.inner, xbar, xtil, cnt.inner, cnt);
-    spmv_DC<T>(c, Sys<T>::D(c), Sys<T>::C(c), x, xtil, y, nullptr);
+    spmv_B<T>(c, Sys<T>::B(c), x, xbar, nullptr);
+    a_solve<T>(R, w, w.states + ST_INNER, p.inner, xbar, xtil);
+    spmv_DC_ind<T>(c, Sys<T>::D(c), Sys<T>::C(c), x, xtil, y, ystride, yk);
 }
 
 // Algorithm 1 (SCR) as the preconditioner: (rv, rp) -> (xv, xp)
 template <typename T>
-void pscr(Ctx &c, Workspace &w, const hyel_solver_params &p, const T *rv, const T *rp, T *xv, T *xp, Counters &cnt) {
+void pscr(Rec &R, Workspace &w, const hyel_solver_params &p, const T *rv, const T *rp, T *xv, T *xp) {
+    Ctx &c = *R.c;
     const int64_t N = c.mesh.N;
     T *xhat = Sys<T>::vec(w, 0, N);
     T *rp2 = Sys<T>::vec(w, 1, N);
     T *rv2 = Sys<T>::vec(w, 2, N);
     // 1: A xhat = r_v
-    a_solve<T>(c, w, p, p.a, rv, xhat, cnt.a, cnt);
+    a_solve<T>(R, w, w.states + ST_A1, p.a, rv, xhat);
     // 2: r_p <- r_p - C xhat
-    spmv_C<T>(c, Sys<T>::C(c), xhat, rp2, rp, nullptr);
+    spmv_C<T>(c, Sys<T>::C(c), xhat, rp2, rp);
     // 3: S x_p = r_p, right-preconditioned by diag(S^)^-1
-    Gmres<T> &gs = Sys<T>::gs(w);
-    auto sop = [&](const T *in, T *out, const int *) { schur_op<T>(c, w, p, in, out, cnt); };
-    int st = gs.solve(rp2, xp, p.s, 1, Sys<T>::shat(c), sop, nullptr, 1, cnt.s.its);
-    cnt.s.solves++;
-    cnt.note(st);
+    Level<T> &Ls = Sys<T>::ls(w);
+    LevelState *sst = w.states + ST_S;
+    gm_solve<T, 1>(R, Ls, sst, p.s, rp2, xp, Sys<T>::shat(c), nullptr,
+                   [&]() { schur_op<T>(R, w, p, Ls.z, Ls.V, &sst->k, Ls.n); });
     // 4: r_v <- r_v - B x_p
-    spmv_B<T>(c, Sys<T>::B(c), xp, rv2, rv, nullptr);
+    spmv_B<T>(c, Sys<T>::B(c), xp, rv2, rv);
     // 5: A x_v = r_v
-    a_solve<T>(c, w, p, p.a, rv2, xv, cnt.a, cnt);
+    a_solve<T>(R, w, w.states + ST_A2, p.a, rv2, xv);
+}
+
+// The outer FGMRES on the scaled system: b -> xs (both FP64, fixed buffers).
+void outer_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const double *b, double *xs) {
+    Ctx &c = *R.c;
+    const int64_t N = c.mesh.N, n = 4 * N;
+    Level<double> &L = w.outer;
+    LevelState *st = w.states + ST_OUTER;
+    auto prec = [&]() {
+        if (p.precision == HYEL_PREC_FP64) {
+            double *vin = Sys<double>::vec(w, 6, N), *zout = Sys<double>::vec(w, 7, N);
+            LAUNCH(k_copy_ind<double, double><<<blocks_for(n, 256), 256, 0, c.stream>>>(L.V, vin, n, st, n, 0));
+            pscr<double>(R, w, p, vin, vin + 3 * N, zout, zout + 3 * N);
+            LAUNCH(k_copy_ind<double, double><<<blocks_for(n, 256), 256, 0, c.stream>>>(zout, L.Z, n, st, 0, n));
+        } else {
+            float *vf = Sys<float>::vec(w, 6, N), *zf = Sys<float>::vec(w, 7, N);
+            LAUNCH(k_copy_ind<double, float><<<blocks_for(n, 256), 256, 0, c.stream>>>(L.V, vf, n, st, n, 0));
+            pscr<float>(R, w, p, vf, vf + 3 * N, zf, zf + 3 * N);
+            LAUNCH(k_copy_ind<float, double><<<blocks_for(n, 256), 256, 0, c.stream>>>(zf, L.Z, n, st, 0, n));
+        }
+    };
+    auto op = [&]() { spmv_full64_ind(c, c.mat.As, c.mat.Bs, c.mat.Cs, c.mat.Ds, L.Z, L.V, n, &st->k); };
+    gm_solve<double, 2>(R, L, st, p.outer, b, xs, nullptr, prec, op);
 }
 
 double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+struct CaptureScope {
+    int count = 0;
+    int *saved;
+    CaptureScope() : saved(g_capture_count) { g_capture_count = &count; }
+    ~CaptureScope() { g_capture_count = saved; }
+};
+
+// Build (or reuse) the graph of the nested solve for these parameters.
+void ensure_graph(Ctx &c, Workspace &w, const hyel_solver_params &p) {
+    if (w.exec && w.have_key && same_params(w.key, p)) return;
+    if (w.exec) cudaGraphExecDestroy(w.exec);
+    if (w.graph) cudaGraphDestroy(w.graph);
+    w.exec = nullptr;
+    w.graph = nullptr;
+    w.sites.clear();
+    if (w.streams.empty()) {
+        cudaStream_t s;
+        HYEL_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        w.streams.push_back(s);
+    }
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    const int64_t N = c.mesh.N;
+    cudaStream_t user = c.stream;
+    c.stream = w.streams[0];
+    CaptureScope scope;
+    Rec R;
+    R.c = &c;
+    R.graph = true;
+    R.streams = &w.streams;
+    R.sites = &w.sites;
+    R.capture_count = &scope.count;
+    cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        c.stream = user;
+        check_cuda(e, "cudaStreamBeginCapture");
+    }
+    try {
+        outer_solve(R, w, p, Sys<double>::vec(w, 8, N), Sys<double>::vec(w, 9, N));
+    } catch (...) {
+        cudaGraph_t g;
+        cudaStreamEndCapture(c.stream, &g);
+        if (g) cudaGraphDestroy(g);
+        c.stream = user;
+        throw;
+    }
+    e = cudaStreamEndCapture(c.stream, &w.graph);
+    c.stream = user;
+    check_cuda(e, "cudaStreamEndCapture");
+    int nested = 0;
+    for (auto &s : w.sites) nested += s.body_nodes + s.init_nodes;
+    w.top_nodes = scope.count - nested;
+    check_cuda(cudaGraphInstantiate(&w.exec, w.graph, 0), "cudaGraphInstantiate");
+    w.key = p;
+    w.have_key = true;
+}
+
+// Kernel executions of the last solve from the level statistics.
+int64_t executed_kernels(Workspace &w) {
+    int64_t total = w.top_nodes;
+    for (auto &s : w.sites) {
+        const LevelState &hs = w.h_states[s.st - w.states];
+        total += (int64_t)s.body_nodes * hs.its + (int64_t)s.init_nodes * hs.solves;
+    }
+    return total;
 }
 
 }  // namespace
@@ -673,6 +924,7 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
     auto t0 = std::chrono::steady_clock::now();
     solve_setup(c);
     Workspace &w = workspace(c, p);
+    if (p.graph) ensure_graph(c, w, p);
     HYEL_CK(cudaStreamSynchronize(c.stream));
     const double ms_setup = 1e3 * seconds_since(t0);
     auto t1 = std::chrono::steady_clock::now();
@@ -680,54 +932,58 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
     double *b = Sys<double>::vec(w, 8, N);
     double *xs = Sys<double>::vec(w, 9, N);
     double *r = Sys<double>::vec(w, 10, N);
+    HYEL_CK(cudaMemsetAsync(w.states, 0, sizeof(LevelState) * 5, c.stream));
     // r* = W r
-    (k_mul<<<blocks_for(n, 256), 256, 0, c.stream>>>(rhs, c.mat.w, b, n), ::hyel::count_launch());
-    Counters cnt;
-    auto op = [&c](const double *in, double *o, const int *done) {
-        spmv_full64(c, c.mat.As, c.mat.Bs, c.mat.Cs, c.mat.Ds, in, o, done);
-    };
-    std::function<void(const double *, double *)> prec;
-    if (p.precision == HYEL_PREC_FP64) {
-        prec = [&](const double *v, double *z) { pscr<double>(c, w, p, v, v + 3 * N, z, z + 3 * N, cnt); };
+    LAUNCH(k_mul<<<blocks_for(n, 256), 256, 0, c.stream>>>(rhs, c.mat.w, b, n));
+    if (p.graph) {
+        HYEL_CK(cudaGraphLaunch(w.exec, c.stream));
     } else {
-        prec = [&](const double *v, double *z) {
-            float *vf = Sys<float>::vec(w, 6, N), *zf = Sys<float>::vec(w, 7, N);
-            (k_cast<double, float><<<blocks_for(n, 256), 256, 0, c.stream>>>(v, vf, n), ::hyel::count_launch());
-            pscr<float>(c, w, p, vf, vf + 3 * N, zf, zf + 3 * N, cnt);
-            (k_cast<float, double><<<blocks_for(n, 256), 256, 0, c.stream>>>(zf, z, n), ::hyel::count_launch());
-        };
+        Rec R;
+        R.c = &c;
+        R.graph = false;
+        R.check_every = p.check_every;
+        outer_solve(R, w, p, b, xs);
     }
-    int64_t outer_its = 0;
-    int st = w.outer.solve(b, xs, p.outer, 2, nullptr, op, prec, 1, outer_its);
     // true residual of the scaled system and unscaling x = W x*
-    op(xs, r, nullptr);
-    (k_sub<double><<<blocks_for(n, 256), 256, 0, c.stream>>>(b, r, n), ::hyel::count_launch());
-    (k_multidot<double><<<w.outer.grid, kThreads, 0, c.stream>>>(r, n, 1, r, n, w.outer.partial, w.outer.counter,
-                                                                c.red + 8, nullptr, MD_DOT, nullptr, 0, 0, 0), ::hyel::count_launch());
-    (k_mul<<<blocks_for(n, 256), 256, 0, c.stream>>>(xs, c.mat.w, x, n), ::hyel::count_launch());
+    spmv_full64_ind(c, c.mat.As, c.mat.Bs, c.mat.Cs, c.mat.Ds, xs, r, 0, nullptr);
+    LAUNCH(k_sub<double><<<blocks_for(n, 256), 256, 0, c.stream>>>(b, r, n));
+    LAUNCH(k_sumsq<<<w.outer.grid, kThreads, 0, c.stream>>>(r, n, w.outer.partial, w.outer.counter, c.red + 8));
+    LAUNCH(k_mul<<<blocks_for(n, 256), 256, 0, c.stream>>>(xs, c.mat.w, x, n));
     HYEL_CK(cudaGetLastError());
     HYEL_CK(cudaMemcpyAsync(c.h_red + 8, c.red + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    w.outer.read_state();
-    const double bn = w.outer.hst->bnorm;
+    HYEL_CK(cudaMemcpyAsync(w.h_states, w.states, sizeof(LevelState) * 5, cudaMemcpyDeviceToHost, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    if (p.graph) {
+        const int64_t k = executed_kernels(w);
+        for (int64_t q = 0; q < k; q++) count_launch();
+    }
+    const LevelState *hs = w.h_states;
+    const double bn = hs[ST_OUTER].bnorm;
     const double rel = bn > 0 ? std::sqrt(c.h_red[8]) / bn : std::sqrt(c.h_red[8]);
+    int st = HYEL_OK;
+    if (hs[ST_OUTER].status_any & 1) st = HYEL_ENAN;
+    else if (hs[ST_OUTER].status_any & 2) st = HYEL_EBREAKDOWN;
+    else if (!hs[ST_OUTER].converged) st = HYEL_ENOCONV;
+    for (int q = 1; q < 5 && st == HYEL_OK; q++) {
+        if (hs[q].status_any & 1) st = HYEL_ENAN;
+    }
+    if (!std::isfinite(rel)) st = HYEL_ENAN;
     if (out) {
         out->status = st;
-        out->outer_its = (int32_t)outer_its;
-        out->a_its = cnt.a.its;
-        out->s_its = cnt.s.its;
-        out->inner_its = cnt.inner.its;
-        out->a_solves = cnt.a.solves;
-        out->s_solves = cnt.s.solves;
-        out->inner_solves = cnt.inner.solves;
+        out->outer_its = (int32_t)hs[ST_OUTER].its;
+        out->a_its = hs[ST_A1].its + hs[ST_A2].its;
+        out->s_its = hs[ST_S].its;
+        out->inner_its = hs[ST_INNER].its;
+        out->a_solves = hs[ST_A1].solves + hs[ST_A2].solves;
+        out->s_solves = hs[ST_S].solves;
+        out->inner_solves = hs[ST_INNER].solves;
         out->rel_residual = rel;
         out->ms_setup = ms_setup;
         out->ms_solve = 1e3 * seconds_since(t1);
     }
-    if (cnt.status != HYEL_OK && st == HYEL_OK) st = cnt.status;
-    if (!std::isfinite(rel)) st = HYEL_ENAN;
     if (st != HYEL_OK) {
-        const char *what = st == HYEL_ENOCONV ? "outer FGMRES reached its iteration cap"
-                           : st == HYEL_ENAN  ? "NaN or Inf in the solve"
+        const char *what = st == HYEL_ENOCONV   ? "outer FGMRES reached its iteration cap"
+                           : st == HYEL_ENAN    ? "NaN or Inf in the solve"
                            : st == HYEL_EBREAKDOWN ? "GMRES breakdown without convergence"
                                                    : "solve failed";
         fail(st, std::string("solve_nested: ") + what);
@@ -740,22 +996,27 @@ void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y
     solve_setup(c);
     Workspace &w = workspace(c, p);
     const int64_t N = c.mesh.N;
-    Counters cnt;
+    HYEL_CK(cudaMemsetAsync(w.states, 0, sizeof(LevelState) * 5, c.stream));
+    Rec R;
+    R.c = &c;
+    R.graph = false;
+    R.check_every = p.check_every;
     if (p.precision == HYEL_PREC_FP64) {
-        schur_op<double>(c, w, p, x, y, cnt);
+        schur_op<double>(R, w, p, x, y, nullptr, 0);
     } else {
         float *xf = Sys<float>::vec(w, 6, N), *yf = Sys<float>::vec(w, 7, N);
-        (k_cast<double, float><<<blocks_for(N, 256), 256, 0, c.stream>>>(x, xf, N), ::hyel::count_launch());
-        schur_op<float>(c, w, p, xf, yf, cnt);
-        (k_cast<float, double><<<blocks_for(N, 256), 256, 0, c.stream>>>(yf, y, N), ::hyel::count_launch());
+        LAUNCH(k_copy_ind<double, float><<<blocks_for(N, 256), 256, 0, c.stream>>>(x, xf, N, nullptr, 0, 0));
+        schur_op<float>(R, w, p, xf, yf, nullptr, 0);
+        LAUNCH(k_copy_ind<float, double><<<blocks_for(N, 256), 256, 0, c.stream>>>(yf, y, N, nullptr, 0, 0));
     }
     HYEL_CK(cudaGetLastError());
+    HYEL_CK(cudaMemcpyAsync(w.h_states, w.states, sizeof(LevelState) * 5, cudaMemcpyDeviceToHost, c.stream));
     HYEL_CK(cudaStreamSynchronize(c.stream));
     if (out) {
         *out = hyel_solve_stats{};
-        out->status = cnt.status;
-        out->inner_its = cnt.inner.its;
-        out->inner_solves = cnt.inner.solves;
+        out->status = (w.h_states[ST_INNER].status_any & 1) ? HYEL_ENAN : HYEL_OK;
+        out->inner_its = w.h_states[ST_INNER].its;
+        out->inner_solves = w.h_states[ST_INNER].solves;
     }
 }
 

@@ -156,8 +156,13 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_spmv_A(const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ row_len,
                                                 const int32_t *__restrict__ col, const T *__restrict__ A,
                                                 const T *__restrict__ x, T *__restrict__ y, int64_t N,
-                                                const int *done) {
-    if (done && *done) return;
+                                                const int *kd, int64_t ystride) {
+    // kd = (k, done) of a Krylov level: output column k+1 of a basis with
+    // column stride ystride; nothing to do once the level is done
+    if (kd) {
+        if (kd[1]) return;
+        y += (int64_t)(kd[0] + 1) * ystride;
+    }
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
     const int t = (int)(r & 31);
@@ -190,8 +195,14 @@ __global__ void __launch_bounds__(128) k_spmv_full64(const int32_t *__restrict__
                                                      const int32_t *__restrict__ col, const double *__restrict__ A,
                                                      const double *__restrict__ B, const double *__restrict__ C,
                                                      const double *__restrict__ D, const double *__restrict__ x,
-                                                     double *__restrict__ y, int64_t N, const int *done) {
-    if (done && *done) return;
+                                                     double *__restrict__ y, int64_t N, const int *kd,
+                                                     int64_t stride) {
+    // kd = (k, done): input column k, output column k+1 (FGMRES Z_k -> V_{k+1})
+    if (kd) {
+        if (kd[1]) return;
+        x += (int64_t)kd[0] * stride;
+        y += (int64_t)(kd[0] + 1) * stride;
+    }
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
     const int t = (int)(r & 31);
@@ -290,8 +301,11 @@ template <typename T>
 __global__ void k_spmv_DC(const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ row_len,
                           const int32_t *__restrict__ col, const T *__restrict__ D, const T *__restrict__ C,
                           const T *__restrict__ xp, const T *__restrict__ xv, T *__restrict__ yp, int64_t N,
-                          const int *done) {
-    if (done && *done) return;
+                          const int *kd, int64_t ystride) {
+    if (kd) {  // output column k+1 of a Krylov basis (see k_spmv_A)
+        if (kd[1]) return;
+        yp += (int64_t)(kd[0] + 1) * ystride;
+    }
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
     const int t = (int)(r & 31);
@@ -365,54 +379,69 @@ void solve_setup(Ctx &c) {
 }
 
 template <typename T>
-void spmv_A(Ctx &c, const T *Av, const T *x, T *y, const int *done) {
+void spmv_A_ind(Ctx &c, const T *Av, const T *x, T *y, int64_t ystride, const int *kd) {
     const DeviceMesh &m = c.mesh;
     const int cls = sizeof(T) == 8 ? HYEL_K_SPMV_A64 : HYEL_K_SPMV_A32;
     cudaEvent_t ev;
     prof_begin(c, cls, &ev);
-    (k_spmv_A<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, done), ::hyel::count_launch());
+    (k_spmv_A<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, kd,
+                                                            ystride), ::hyel::count_launch());
     // algorithmic bytes: 9 values + 1 column index per block, x and y once
     prof_end(c, cls, ev, (double)m.nnzb * (9.0 * sizeof(T) + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * sizeof(T));
 }
-template void spmv_A<double>(Ctx &, const double *, const double *, double *, const int *);
-template void spmv_A<float>(Ctx &, const float *, const float *, float *, const int *);
+template <typename T>
+void spmv_A(Ctx &c, const T *Av, const T *x, T *y) {
+    spmv_A_ind<T>(c, Av, x, y, 0, nullptr);
+}
+template void spmv_A<double>(Ctx &, const double *, const double *, double *);
+template void spmv_A<float>(Ctx &, const float *, const float *, float *);
+template void spmv_A_ind<double>(Ctx &, const double *, const double *, double *, int64_t, const int *);
+template void spmv_A_ind<float>(Ctx &, const float *, const float *, float *, int64_t, const int *);
 
-void spmv_full64(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x, double *y,
-                 const int *done) {
+void spmv_full64_ind(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,
+                     double *y, int64_t stride, const int *kd) {
     const DeviceMesh &m = c.mesh;
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_SPMV_FULL64, &ev);
     (k_spmv_full64<<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, A, B, C, D, x, y, m.N,
-                                                              done), ::hyel::count_launch());
+                                                              kd, stride), ::hyel::count_launch());
     prof_end(c, HYEL_K_SPMV_FULL64, ev, (double)m.nnzb * (16.0 * 8 + 4.0) + 4.0 * (m.N + 1) + 2.0 * 4 * m.N * 8);
+}
+void spmv_full64(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,
+                 double *y) {
+    spmv_full64_ind(c, A, B, C, D, x, y, 0, nullptr);
 }
 
 template <typename T>
-void spmv_B(Ctx &c, const T *B, const T *xp, T *yv, const T *r, const int *done) {
+void spmv_B(Ctx &c, const T *B, const T *xp, T *yv, const T *r) {
     const DeviceMesh &m = c.mesh;
-    (k_spmv_B<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, B, xp, yv, r, m.N, done), ::hyel::count_launch());
+    (k_spmv_B<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, B, xp, yv, r, m.N,
+                                                            nullptr), ::hyel::count_launch());
 }
 template <typename T>
-void spmv_C(Ctx &c, const T *C, const T *xv, T *yp, const T *r, const int *done) {
+void spmv_C(Ctx &c, const T *C, const T *xv, T *yp, const T *r) {
     const DeviceMesh &m = c.mesh;
-    (k_spmv_C<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, C, xv, yp, r, m.N, done), ::hyel::count_launch());
+    (k_spmv_C<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, C, xv, yp, r, m.N,
+                                                            nullptr), ::hyel::count_launch());
 }
 template <typename T>
-void spmv_D(Ctx &c, const T *D, const T *xp, T *yp, const int *done) {
+void spmv_D(Ctx &c, const T *D, const T *xp, T *yp) {
     const DeviceMesh &m = c.mesh;
     (k_spmv_DC<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, D, (const T *)nullptr, xp,
-                                                             (const T *)nullptr, yp, m.N, done), ::hyel::count_launch());
+                                                             (const T *)nullptr, yp, m.N, nullptr, 0),
+     ::hyel::count_launch());
 }
 template <typename T>
-void spmv_DC(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp, const int *done) {
+void spmv_DC_ind(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp, int64_t ystride, const int *kd) {
     const DeviceMesh &m = c.mesh;
-    (k_spmv_DC<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, D, C, xp, xv, yp, m.N, done), ::hyel::count_launch());
+    (k_spmv_DC<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, D, C, xp, xv, yp, m.N, kd,
+                                                             ystride), ::hyel::count_launch());
 }
-#define HYEL_INST(T)                                                                         \
-    template void spmv_B<T>(Ctx &, const T *, const T *, T *, const T *, const int *);       \
-    template void spmv_C<T>(Ctx &, const T *, const T *, T *, const T *, const int *);       \
-    template void spmv_D<T>(Ctx &, const T *, const T *, T *, const int *);                  \
-    template void spmv_DC<T>(Ctx &, const T *, const T *, const T *, const T *, T *, const int *);
+#define HYEL_INST(T)                                                                              \
+    template void spmv_B<T>(Ctx &, const T *, const T *, T *, const T *);                         \
+    template void spmv_C<T>(Ctx &, const T *, const T *, T *, const T *);                         \
+    template void spmv_D<T>(Ctx &, const T *, const T *, T *);                                    \
+    template void spmv_DC_ind<T>(Ctx &, const T *, const T *, const T *, const T *, T *, int64_t, const int *);
 HYEL_INST(double)
 HYEL_INST(float)
 #undef HYEL_INST

@@ -66,7 +66,8 @@ class HyelKrylovLevel(C.Structure):
 
 class HyelSolverParams(C.Structure):
     _fields_ = [("outer", HyelKrylovLevel), ("a", HyelKrylovLevel), ("s", HyelKrylovLevel),
-                ("inner", HyelKrylovLevel), ("precision", C.c_int32), ("check_every", C.c_int32)]
+                ("inner", HyelKrylovLevel), ("precision", C.c_int32), ("check_every", C.c_int32),
+                ("graph", C.c_int32)]
 
 
 class HyelSolveStats(C.Structure):
@@ -262,12 +263,12 @@ def level(rtol, maxit, restart, atol=1e-50):
 
 
 def solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=HYEL_PREC_FP64, outer=(200, 200),
-                  a=(500, 500), s=(200, 200), inner=(500, 500), check_every=4, inner_rtol=None):
+                  a=(500, 500), s=(200, 200), inner=(500, 500), check_every=4, inner_rtol=None, graph=1):
     """Solver controls with the paper's defaults (§5: FGMRES(200), A: GMRES(500),
     S: GMRES(200), inner GMRES(500), absolute tolerances 1e-50)."""
     ir = sub_rtol if inner_rtol is None else inner_rtol
     return HyelSolverParams(level(outer_rtol, *outer), level(sub_rtol, *a), level(sub_rtol, *s),
-                            level(ir, *inner), precision, check_every)
+                            level(ir, *inner), precision, check_every, graph)
 
 
 def time_params(dt=1e-3, t_n=0.0, rho_inf=0.5, tol_r=1e-6, tol_a=1e-6, l_max=20, rhs_literal=0):

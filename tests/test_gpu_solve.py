@@ -134,3 +134,19 @@ def test_iteration_cap_and_nan(cube):
     # still usable afterwards
     st, rc = H.hyel_solve_nested(gp.ctx, H.solver_params(), cube["rhs"].data_ptr(), x.data_ptr())
     assert rc == H.HYEL_OK
+
+
+@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
+def test_graph_and_host_driven_loops_agree_bitwise(cube, precision):
+    """The CUDA-graph solve (device-driven while loops) and the host-driven
+    replay run the same kernels in the same order: identical iterates."""
+    gp, N = cube["gp"], cube["N"]
+    out = []
+    for graph, every in ((1, 1), (0, 3), (1, 1)):
+        x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+        params = H.solver_params(outer_rtol=1e-12, precision=precision, graph=graph, check_every=every)
+        st, rc = H.hyel_solve_nested(gp.ctx, params, cube["rhs"].data_ptr(), x.data_ptr())
+        out.append((x.cpu().numpy(), st.outer_its, st.a_its, st.s_its, st.inner_its))
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0])
+        assert o[1:] == out[0][1:]
