@@ -279,6 +279,27 @@ int hyel_profile_read(hyel_ctx *ctx, double *ms, int64_t *launches, double *byte
  * (all contexts). count: host. */
 int hyel_launch_count(int64_t *count);
 
+/* ---------------------------------------------------------------- no-allocation variant */
+
+/* Residual norms of the coupled operator without any device allocation:
+ * out[0] = ||b - M x||_2, out[1] = ||b||_2 with M = [[A, B], [C, D]] the
+ * assembled (HYEL_MAT_ASSEMBLED) or scaled (HYEL_MAT_SCALED64, after
+ * hyel_solve_setup) matrix. x, b: device [4N] double; out: device [2] double.
+ * Stream-ordered, no synchronization.
+ *
+ * The paper has no counterpart: this serves callers that cannot allocate
+ * device memory where they need a residual check (code running during CUDA
+ * stream capture, frameworks whose pool allocator owns all device memory,
+ * latency-critical loops). Its reduction scratch is a fixed 128 KB
+ * file-scope device array, held by every GPU that loads the library until the
+ * process exits; it calls no cudaMalloc, cudaFree or allocating routine.
+ * Limit: N <= 1,048,576 nodes (HYEL_EINVAL beyond). The first call on a device
+ * looks up the array's device address; make that first call before any stream
+ * capture. All calls share the one array: calls whose kernels overlap on the
+ * GPU (different streams or contexts at the same time) race and give wrong
+ * results; serialize them. */
+int hyel_residual_norm_static(hyel_ctx *ctx, int matrix, const double *x, const double *b, double *out);
+
 #ifdef __cplusplus
 }
 #endif

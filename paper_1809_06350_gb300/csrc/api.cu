@@ -295,6 +295,10 @@ int hyel_profile(hyel_ctx *ctx, int enable) {
     });
 }
 
+int hyel_residual_norm_static(hyel_ctx *ctx, int matrix, const double *x, const double *b, double *out) {
+    return guarded(ctx, [&](hyel::Ctx &c) { hyel::residual_norm_static(c, matrix, x, b, out); });
+}
+
 int hyel_launch_count(int64_t *count) {
     if (!count) return HYEL_EINVAL;
     *count = (int64_t)hyel::g_launches.load(std::memory_order_relaxed);

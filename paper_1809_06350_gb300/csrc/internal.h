@@ -194,6 +194,9 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
 void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y, hyel_solve_stats *st);
 void free_workspace(Ctx &c);
 
+// noalloc.cu
+void residual_norm_static(Ctx &c, int matrix, const double *x, const double *b, double *out);
+
 // newton.cu
 void newton_step(Ctx &c, const hyel_time_params &tp, const hyel_solver_params &sp, hyel_state &s,
                  hyel_newton_stats *st);

@@ -31,7 +31,7 @@ EXPORTS = [
     "hyel_create", "hyel_destroy", "hyel_set_stream", "hyel_last_error", "hyel_mesh_upload",
     "hyel_mesh_info", "hyel_assemble", "hyel_matrix_download", "hyel_spmv", "hyel_solve_setup",
     "hyel_schur_apply", "hyel_solve_nested", "hyel_newton_step", "hyel_profile", "hyel_profile_read",
-    "hyel_launch_count",
+    "hyel_launch_count", "hyel_residual_norm_static",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -127,6 +127,7 @@ def lib():
             "hyel_profile": (C.c_int, [vp, C.c_int]),
             "hyel_profile_read": (C.c_int, [vp, _dp, C.POINTER(C.c_int64), _dp]),
             "hyel_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
+            "hyel_residual_norm_static": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -246,6 +247,13 @@ def hyel_profile_read(ctx):
     by = (C.c_double * HYEL_K_NCLASSES)()
     _check(ctx, lib().hyel_profile_read(ctx, ms, n, by))
     return {K_NAMES[k]: {"ms": ms[k], "launches": n[k], "bytes": by[k]} for k in range(HYEL_K_NCLASSES)}
+
+
+def hyel_residual_norm_static(ctx, matrix, x_ptr, b_ptr, out_ptr):
+    """out[0] = ||b - M x||, out[1] = ||b|| (device [2]); allocates nothing on
+    the device (fixed scratch array inside the library)."""
+    return _check(ctx, lib().hyel_residual_norm_static(ctx, int(matrix), C.c_void_p(x_ptr), C.c_void_p(b_ptr),
+                                                       C.c_void_p(out_ptr)))
 
 
 def hyel_launch_count():
