@@ -192,6 +192,18 @@ def assemble_matrix(prob, st, ga):
     return K
 
 
+def assemble_rows(prob, st, ga, nodes):
+    """The reduced tangent restricted to the elements that touch ``nodes``:
+    the block rows of those nodes are complete, all other rows are partial.
+    For sampled parity checks on meshes too large to assemble whole."""
+    elems = np.unique(np.nonzero(np.isin(prob.tets, nodes))[0])
+    geo, me, tau = prob.subset(elems)
+    sub = Problem.__new__(Problem)
+    sub.__dict__.update(prob.__dict__)
+    sub.tets, sub.geo, sub.me, sub.tau, sub.E = prob.tets[elems], geo, me, tau, len(elems)
+    return assemble_matrix(sub, st, ga)
+
+
 def newton_rhs(prob, st, t_alpha, ga, exact=True):
     """Right-hand side of the reduced system.
 
