@@ -225,12 +225,16 @@ int hyel_matrix_download(hyel_ctx *ctx, int32_t *row_ptr, int32_t *col,
 /* ---------------------------------------------------------------- operators */
 
 enum { HYEL_OP_FULL = 0, HYEL_OP_A = 1, HYEL_OP_B = 2, HYEL_OP_C = 3, HYEL_OP_D = 4 };
-enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2 };
+enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYEL_MAT_TRANSPOSED = 3 };
 
 /* y = op(M) x on device vectors. FULL: [4N] -> [4N]; A: [3N] -> [3N];
  * B: [N] -> [3N]; C: [3N] -> [N]; D: [N] -> [N]. x, y are double for the
  * FP64 matrices and float for HYEL_MAT_SCALED32. Scaled matrices exist after
- * hyel_solve_setup (or a solve) on the current assembly. */
+ * hyel_solve_setup (or a solve) on the current assembly.
+ * HYEL_MAT_TRANSPOSED (FULL only): y = [[A^T, C^T], [B^T, D^T]] x, the
+ * transpose of the assembled operator, built on first use after each
+ * assembly (the block pattern is symmetric; block (i, c) of the transpose is
+ * taken from block (c, i)). */
 int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y);
 
 /* Prepare the scaled system for the current assembly (§4.1): W_ii =
@@ -260,6 +264,41 @@ int hyel_solve_nested(hyel_ctx *ctx, const hyel_solver_params *params,
 int hyel_newton_step(hyel_ctx *ctx, const hyel_time_params *tp,
                      const hyel_solver_params *sp, hyel_state *state,
                      hyel_newton_stats *stats);
+
+/* ---------------------------------------------------------------- adjoint */
+
+/* Replace the moduli of the uploaded mesh (mu, kappa, k1, k2; global or per
+ * element) and recompute tau_M; geometry, models, rho0, c_m, body force and
+ * fibre directions are kept. Invalidates the current assembly. */
+int hyel_update_material(hyel_ctx *ctx, const hyel_material *mat);
+
+/* Solve A^T x = rhs for the last assembled matrix: the nested solver of
+ * hyel_solve_nested applied to the transposed blocks [[A^T, C^T], [B^T, D^T]]
+ * (same scaling W; S^T = D^T - B^T A^-T C^T applied matrix-free). rhs, x:
+ * device [4N], ordered [x_v ; x_p] as in hyel_solve_nested. */
+int hyel_solve_nested_transpose(hyel_ctx *ctx, const hyel_solver_params *params,
+                                const double *rhs, double *x, hyel_solve_stats *stats);
+
+/* grad[e][k] -= sum over element e of lambda . dF_e/dtheta_k for the element
+ * parameters theta = (mu, kappa, k1, k2), F = [R_k bar ; R_p ; R_m] the residual
+ * of Appendix A at the stage state (R_k bar does not depend on theta).
+ * lambda: device [7N] ordered [lam_k 3N | lam_p N | lam_m 3N] (Dirichlet
+ * components are ignored); grad: device [E][4], accumulated. Synchronizes. */
+int hyel_param_sensitivity(hyel_ctx *ctx, const hyel_state *stage, const double *lambda, double *grad);
+
+/* One reverse step of the discrete adjoint of the generalized-alpha Newton
+ * step (§3.2, §3.3) for an objective of the final state. state_n holds y_n,
+ * ydot_n and state_np1 the converged y_{n+1}, ydot_{n+1} (device, read only).
+ * ybar, ydotbar: device [7N] ([u|p|v] and [udot|pdot|vdot]), dJ/dy_{n+1} and
+ * dJ/dydot_{n+1} on entry, dJ/dy_n and dJ/dydot_n on return. grad: device
+ * [E][4] or NULL, accumulates dJ/dtheta. lambda_out: device [7N] or NULL, the
+ * step's adjoint [lam_k | lam_p | lam_m]. The transposed linear system is
+ * solved with `sp` (stats: that solve). Dirichlet constraints must be
+ * homogeneous; their components carry zero adjoint. Leaves the context
+ * without a valid assembly. */
+int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solver_params *sp,
+                      const hyel_state *state_n, const hyel_state *state_np1, double *ybar,
+                      double *ydotbar, double *grad, double *lambda_out, hyel_solve_stats *stats);
 
 /* ---------------------------------------------------------------- profiling */
 

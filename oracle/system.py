@@ -109,8 +109,8 @@ def kinematic_residual(st):
 def assemble_residual(prob, st, t_alpha):
     """Global R_m [N,3] (with the traction term) and R_p [N] at a stage state."""
     Rm_e, Rp_e = el.element_residual(prob.geo, prob.me, prob.tau, el.gather(prob.tets, st))
-    Rm = np.zeros((prob.N, 3))
-    Rp = np.zeros(prob.N)
+    Rm = np.zeros((prob.N, 3), dtype=Rm_e.dtype)
+    Rp = np.zeros(prob.N, dtype=Rp_e.dtype)
     for a in range(4):
         np.add.at(Rm, prob.tets[:, a], Rm_e[:, a])
         np.add.at(Rp, prob.tets[:, a], Rp_e[:, a])

@@ -210,8 +210,14 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "spmv: null vector");
         if (op < HYEL_OP_FULL || op > HYEL_OP_D) hyel::fail(HYEL_EINVAL, "spmv: bad op");
-        if (matrix < HYEL_MAT_ASSEMBLED || matrix > HYEL_MAT_SCALED32) hyel::fail(HYEL_EINVAL, "spmv: bad matrix");
+        if (matrix < HYEL_MAT_ASSEMBLED || matrix > HYEL_MAT_TRANSPOSED) hyel::fail(HYEL_EINVAL, "spmv: bad matrix");
         if (!c.mat.assembled) hyel::fail(HYEL_ESTATE, "spmv: nothing assembled");
+        if (matrix == HYEL_MAT_TRANSPOSED) {
+            if (op != HYEL_OP_FULL) hyel::fail(HYEL_EINVAL, "spmv: the transposed matrix supports HYEL_OP_FULL only");
+            hyel::spmv_transpose(c, (const double *)x, (double *)y);
+            HYEL_CK(cudaGetLastError());
+            return;
+        }
         if (matrix != HYEL_MAT_ASSEMBLED && !c.mat.scaled) hyel::fail(HYEL_ESTATE, "spmv: call hyel_solve_setup first");
         hyel::DeviceMatrix &M = c.mat;
         if (matrix == HYEL_MAT_SCALED32) {
@@ -292,6 +298,38 @@ int hyel_profile(hyel_ctx *ctx, int enable) {
             c.prof.bytes[k] = 0;
         }
         c.prof.on = enable != 0;
+    });
+}
+
+int hyel_update_material(hyel_ctx *ctx, const hyel_material *mat) {
+    return guarded(ctx, [&](hyel::Ctx &c) { hyel::update_material(c, mat); });
+}
+
+int hyel_solve_nested_transpose(hyel_ctx *ctx, const hyel_solver_params *params, const double *rhs, double *x,
+                                hyel_solve_stats *stats) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!params || !rhs || !x) hyel::fail(HYEL_EINVAL, "solve_nested_transpose: null argument");
+        hyel::solve_nested_transpose(c, *params, rhs, x, stats);
+    });
+}
+
+int hyel_param_sensitivity(hyel_ctx *ctx, const hyel_state *stage, const double *lambda, double *grad) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!stage || !lambda || !grad || !stage->u || !stage->p || !stage->v || !stage->udot || !stage->pdot ||
+            !stage->vdot)
+            hyel::fail(HYEL_EINVAL, "param_sensitivity: null argument");
+        hyel::param_sensitivity(c, *stage, lambda, grad);
+        HYEL_CK(cudaStreamSynchronize(c.stream));
+    });
+}
+
+int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solver_params *sp,
+                      const hyel_state *state_n, const hyel_state *state_np1, double *ybar, double *ydotbar,
+                      double *grad, double *lambda_out, hyel_solve_stats *stats) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!tp || !sp || !state_n || !state_np1 || !ybar || !ydotbar)
+            hyel::fail(HYEL_EINVAL, "adjoint_step: null argument");
+        hyel::adjoint_step(c, *tp, *sp, *state_n, *state_np1, ybar, ydotbar, grad, lambda_out, stats);
     });
 }
 

@@ -616,6 +616,7 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     HYEL_CK(cudaGetLastError());
     c.mat.assembled = true;
     c.mat.scaled = false;
+    c.mat.transposed = false;
     HYEL_CK(cudaMemcpyAsync(c.h_red, c.red, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     HYEL_CK(cudaMemcpyAsync(c.h_err, c.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
     HYEL_CK(cudaStreamSynchronize(c.stream));

@@ -76,6 +76,8 @@ struct DeviceMesh {
     // host copies for downloads
     std::vector<int32_t> h_row_ptr, h_col;  // block CSR
     std::vector<int64_t> h_csr_slot;        // CSR position -> slot
+    std::vector<double> h_hmax;             // longest reference edge per element (tau_M updates)
+    double c_m = 1e-3;
 };
 
 struct DeviceMatrix {
@@ -87,8 +89,12 @@ struct DeviceMatrix {
     float *jac32 = nullptr;
     double *shat64 = nullptr;   // [N] 1 / diag(S^) of the scaled system
     float *shat32 = nullptr;
+    // transposed operator [[A^T, C^T], [B^T, D^T]] in the same pattern: block
+    // (i, c) holds A(c, i)^T, C(c, i), B(c, i), D(c, i)
+    double *At = nullptr, *Bt = nullptr, *Ct = nullptr, *Dt = nullptr;
     bool assembled = false;
     bool scaled = false;
+    bool transposed = false;  // At..Dt hold the transpose of the current assembly
 };
 
 struct GmState {
@@ -168,6 +174,7 @@ void matrix_download(Ctx &c, int32_t *row_ptr, int32_t *col, double *A, double *
 
 // sparse.cu
 void solve_setup(Ctx &c);
+void transpose_assembled(Ctx &c);  // fills At..Dt from A..D (mirror slots)
 // SpMVs. The *_ind forms take kd = (k, done) of a Krylov level (the first two
 // ints of its device state): they write basis column k+1 (column stride given)
 // and do nothing once the level is done; kd == nullptr means plain pointers.
@@ -193,6 +200,16 @@ void spmv_DC_ind(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp
 void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double *x, hyel_solve_stats *st);
 void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y, hyel_solve_stats *st);
 void free_workspace(Ctx &c);
+
+// adjoint.cu
+void solve_nested_transpose(Ctx &c, const hyel_solver_params &p, const double *rhs, double *x,
+                            hyel_solve_stats *st);
+void spmv_transpose(Ctx &c, const double *x, double *y);
+void param_sensitivity(Ctx &c, const hyel_state &st, const double *lam, double *grad);
+void adjoint_step(Ctx &c, const hyel_time_params &tp, const hyel_solver_params &sp, const hyel_state &sn,
+                  const hyel_state &s1, double *ybar, double *ydbar, double *grad, double *lam_out,
+                  hyel_solve_stats *stats);
+void update_material(Ctx &c, const hyel_material *mat);
 
 // noalloc.cu
 void residual_norm_static(Ctx &c, int matrix, const double *x, const double *b, double *out);

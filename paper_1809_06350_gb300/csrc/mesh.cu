@@ -69,6 +69,7 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     std::vector<int32_t> tets(tets_in, tets_in + 4 * E);
     std::vector<double> geo(14 * (size_t)E);
     std::vector<double> mat4(4 * (size_t)E);
+    std::vector<double> hmax_all((size_t)E);
     for (int64_t e = 0; e < E; e++) {
         int32_t *t = &tets[4 * e];
         for (int a = 0; a < 4; a++)
@@ -125,6 +126,7 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
         double cw = mat->vol_model == HYEL_VOL_GIBBS ? std::sqrt((kappa + 4.0 * mu / 3.0) / mat->rho0)
                                                       : std::sqrt(mu / mat->rho0);
         geo[13 * E + e] = mat->c_m * hmax / (cw * mat->rho0);
+        hmax_all[e] = hmax;
         mat4[0 * E + e] = mu;
         mat4[1 * E + e] = kappa;
         mat4[2 * E + e] = k1;
@@ -291,6 +293,8 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     m.h_row_ptr = row_ptr;
     m.h_col = cols;
     m.h_csr_slot = csr_slot;
+    m.h_hmax = std::move(hmax_all);
+    m.c_m = mat->c_m;
 
     // ---- matrices, staging and scratch
     size_t ns = (size_t)m.nslots;
@@ -317,6 +321,14 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     HYEL_CK(cudaMemsetAsync(M.B, 0, 3 * ns * sizeof(double), c.stream));
     HYEL_CK(cudaMemsetAsync(M.C, 0, 3 * ns * sizeof(double), c.stream));
     HYEL_CK(cudaMemsetAsync(M.D, 0, ns * sizeof(double), c.stream));
+    M.At = dalloc_n<double>(c, 9 * ns);
+    M.Bt = dalloc_n<double>(c, 3 * ns);
+    M.Ct = dalloc_n<double>(c, 3 * ns);
+    M.Dt = dalloc_n<double>(c, ns);
+    HYEL_CK(cudaMemsetAsync(M.At, 0, 9 * ns * sizeof(double), c.stream));
+    HYEL_CK(cudaMemsetAsync(M.Bt, 0, 3 * ns * sizeof(double), c.stream));
+    HYEL_CK(cudaMemsetAsync(M.Ct, 0, 3 * ns * sizeof(double), c.stream));
+    HYEL_CK(cudaMemsetAsync(M.Dt, 0, ns * sizeof(double), c.stream));
     size_t nblk32 = ((size_t)E + 31) / 32;
     c.stage = dalloc_n<double>(c, nblk32 * 32 * kRecords * kRecordDoubles);
     c.vec = dalloc_n<double>(c, 56 * (size_t)N);  // Newton states, stage values, rhs, increment
@@ -326,6 +338,38 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     HYEL_CK(cudaMemsetAsync(c.counter, 0, 64 * sizeof(unsigned), c.stream));
     HYEL_CK(cudaMemsetAsync(c.err, 0, 4 * sizeof(unsigned), c.stream));
     HYEL_CK(cudaStreamSynchronize(c.stream));
+}
+
+// New moduli on the uploaded mesh (mu, kappa, k1, k2, global or per element):
+// material arrays and tau_M = c_m h / (c rho0) are recomputed; geometry, model
+// choice, rho0, c_m, body force and fibre directions stay as uploaded.
+void update_material(Ctx &c, const hyel_material *mat) {
+    DeviceMesh &m = c.mesh;
+    if (m.N == 0) fail(HYEL_ESTATE, "update_material: no mesh uploaded");
+    if (!mat) fail(HYEL_EINVAL, "update_material: null material");
+    if (mat->vol_model != m.vol_model || mat->n_fibres != m.n_fibres)
+        fail(HYEL_EINVAL, "update_material: model or fibre count differs from the uploaded material");
+    const int64_t E = m.E;
+    std::vector<double> mat4(4 * (size_t)E), tau((size_t)E);
+    for (int64_t e = 0; e < E; e++) {
+        const double mu = mat->mu_e ? mat->mu_e[e] : mat->mu;
+        const double kappa = mat->kappa_e ? mat->kappa_e[e] : mat->kappa;
+        const double k1 = mat->k1_e ? mat->k1_e[e] : mat->k1;
+        const double k2 = mat->k2_e ? mat->k2_e[e] : mat->k2;
+        if (!(mu > 0)) fail(HYEL_EINVAL, "update_material: mu must be > 0");
+        if (m.vol_model == HYEL_VOL_GIBBS && !(kappa > 0)) fail(HYEL_EINVAL, "update_material: kappa must be > 0");
+        const double cw = m.vol_model == HYEL_VOL_GIBBS ? std::sqrt((kappa + 4.0 * mu / 3.0) / m.rho0)
+                                                         : std::sqrt(mu / m.rho0);
+        tau[e] = m.c_m * m.h_hmax[e] / (cw * m.rho0);
+        mat4[0 * E + e] = mu;
+        mat4[1 * E + e] = kappa;
+        mat4[2 * E + e] = k1;
+        mat4[3 * E + e] = k2;
+    }
+    HYEL_CK(cudaMemcpyAsync(m.mat, mat4.data(), mat4.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    HYEL_CK(cudaMemcpyAsync(m.geo + 13 * E, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    c.mat.assembled = false;
 }
 
 void mesh_upload(Ctx &c, int64_t N, const double *X, int64_t E, const int32_t *tets, const hyel_bc *bc,

@@ -152,6 +152,35 @@ __global__ void k_schur_hat(ScaleArgs a) {
     a.shat32[i] = (float)inv;
 }
 
+// Transposed operator in the same pattern (the pattern is symmetric): block
+// (i, c) of [[A^T, C^T], [B^T, D^T]] takes A(c, i)^T, C(c, i), B(c, i) and
+// D(c, i) from the mirror slot of (i, c).
+__global__ void k_transpose(const int32_t *__restrict__ col_slice, const int32_t *__restrict__ slice_ptr,
+                            const int32_t *__restrict__ row_len, const int32_t *__restrict__ mirror,
+                            const double *__restrict__ A, const double *__restrict__ B,
+                            const double *__restrict__ C, const double *__restrict__ D, double *__restrict__ At,
+                            double *__restrict__ Bt, double *__restrict__ Ct, double *__restrict__ Dt, int64_t N,
+                            int64_t nslots) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nslots) return;
+    const int64_t b = q >> 5;
+    const int t = (int)(q & 31);
+    const int s = col_slice[b];
+    const int64_t r = (int64_t)s * 32 + t;
+    if (r >= N || b - slice_ptr[s] >= row_len[r]) return;  // padding stays zero
+    const int64_t mq = mirror[q], mb = mq >> 5, mt = mq & 31;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) At[(b * 9 + 3 * i + j) * 32 + t] = A[(mb * 9 + 3 * j + i) * 32 + mt];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        Bt[(b * 3 + i) * 32 + t] = C[(mb * 3 + i) * 32 + mt];
+        Ct[(b * 3 + i) * 32 + t] = B[(mb * 3 + i) * 32 + mt];
+    }
+    Dt[b * 32 + t] = D[mb * 32 + mt];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_spmv_A(const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ row_len,
                                                 const int32_t *__restrict__ col, const T *__restrict__ A,
@@ -376,6 +405,19 @@ void solve_setup(Ctx &c) {
     HYEL_CK(cudaStreamSynchronize(c.stream));
     if (*c.h_err & ERR_SINGULAR) fail(HYEL_ESINGULAR, "solve_setup: a 3x3 diagonal block of A is singular");
     c.mat.scaled = true;
+}
+
+void transpose_assembled(Ctx &c) {
+    if (!c.mat.assembled) fail(HYEL_ESTATE, "transpose: nothing assembled");
+    if (c.mat.transposed) return;
+    const DeviceMesh &m = c.mesh;
+    DeviceMatrix &M = c.mat;
+    (k_transpose<<<blocks_for(m.nslots, 256), 256, 0, c.stream>>>(m.col_slice, m.slice_ptr, m.row_len, m.mirror, M.A,
+                                                                  M.B, M.C, M.D, M.At, M.Bt, M.Ct, M.Dt, m.N,
+                                                                  m.nslots),
+     ::hyel::count_launch());
+    HYEL_CK(cudaGetLastError());
+    M.transposed = true;
 }
 
 template <typename T>

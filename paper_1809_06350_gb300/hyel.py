@@ -21,7 +21,7 @@ HYEL_EBREAKDOWN, HYEL_ENAN, HYEL_EINVERTED, HYEL_ESINGULAR, HYEL_ESTATE = -5, -6
 HYEL_VOL_GIBBS, HYEL_VOL_INCOMPRESSIBLE = 0, 1
 HYEL_PREC_FP64, HYEL_PREC_FP32 = 0, 1
 HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D = 0, 1, 2, 3, 4
-HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32 = 0, 1, 2
+HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32, HYEL_MAT_TRANSPOSED = 0, 1, 2, 3
 HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER = range(5)
 HYEL_K_NCLASSES = 5
 K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather"]
@@ -31,7 +31,8 @@ EXPORTS = [
     "hyel_create", "hyel_destroy", "hyel_set_stream", "hyel_last_error", "hyel_mesh_upload",
     "hyel_mesh_info", "hyel_assemble", "hyel_matrix_download", "hyel_spmv", "hyel_solve_setup",
     "hyel_schur_apply", "hyel_solve_nested", "hyel_newton_step", "hyel_profile", "hyel_profile_read",
-    "hyel_launch_count", "hyel_residual_norm_static",
+    "hyel_launch_count", "hyel_residual_norm_static", "hyel_update_material",
+    "hyel_solve_nested_transpose", "hyel_param_sensitivity", "hyel_adjoint_step",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -128,6 +129,13 @@ def lib():
             "hyel_profile_read": (C.c_int, [vp, _dp, C.POINTER(C.c_int64), _dp]),
             "hyel_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
             "hyel_residual_norm_static": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+            "hyel_update_material": (C.c_int, [vp, C.POINTER(HyelMaterial)]),
+            "hyel_solve_nested_transpose": (C.c_int, [vp, C.POINTER(HyelSolverParams), vp, vp,
+                                                      C.POINTER(HyelSolveStats)]),
+            "hyel_param_sensitivity": (C.c_int, [vp, C.POINTER(HyelState), vp, vp]),
+            "hyel_adjoint_step": (C.c_int, [vp, C.POINTER(HyelTimeParams), C.POINTER(HyelSolverParams),
+                                            C.POINTER(HyelState), C.POINTER(HyelState), vp, vp, vp, vp,
+                                            C.POINTER(HyelSolveStats)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -249,6 +257,31 @@ def hyel_profile_read(ctx):
     return {K_NAMES[k]: {"ms": ms[k], "launches": n[k], "bytes": by[k]} for k in range(HYEL_K_NCLASSES)}
 
 
+def hyel_update_material(ctx, mat):
+    return _check(ctx, lib().hyel_update_material(ctx, C.byref(mat)))
+
+
+def hyel_solve_nested_transpose(ctx, params, rhs_ptr, x_ptr, raise_on_error=True):
+    st = HyelSolveStats()
+    rc = lib().hyel_solve_nested_transpose(ctx, C.byref(params), C.c_void_p(rhs_ptr), C.c_void_p(x_ptr),
+                                           C.byref(st))
+    if raise_on_error:
+        _check(ctx, rc)
+    return st, rc
+
+
+def hyel_param_sensitivity(ctx, stage, lam_ptr, grad_ptr):
+    return _check(ctx, lib().hyel_param_sensitivity(ctx, C.byref(stage), C.c_void_p(lam_ptr), C.c_void_p(grad_ptr)))
+
+
+def hyel_adjoint_step(ctx, tp, sp, state_n, state_np1, ybar_ptr, ydbar_ptr, grad_ptr=0, lam_ptr=0):
+    st = HyelSolveStats()
+    _check(ctx, lib().hyel_adjoint_step(ctx, C.byref(tp), C.byref(sp), C.byref(state_n), C.byref(state_np1),
+                                        C.c_void_p(ybar_ptr), C.c_void_p(ydbar_ptr), C.c_void_p(grad_ptr or 0),
+                                        C.c_void_p(lam_ptr or 0), C.byref(st)))
+    return st
+
+
 def hyel_residual_norm_static(ctx, matrix, x_ptr, b_ptr, out_ptr):
     """out[0] = ||b - M x||, out[1] = ||b|| (device [2]); allocates nothing on
     the device (fixed scratch array inside the library)."""
@@ -283,6 +316,32 @@ def time_params(dt=1e-3, t_n=0.0, rho_inf=0.5, tol_r=1e-6, tol_a=1e-6, l_max=20,
     return HyelTimeParams(rho_inf, dt, t_n, tol_r, tol_a, l_max, rhs_literal)
 
 
+def material_struct(mat, fields=None, mesh=None):
+    """HyelMaterial for a material dict (and optional per-element fields);
+    returns (struct, keepalive) -- keep the second alive while the struct is used."""
+    fields = fields or {}
+    keep = {}
+
+    def opt(name):
+        if name in fields:
+            a = _arr(fields[name], np.float64)
+            keep[name] = a
+            return _ptr(a, C.c_double)
+        return None
+
+    fa1 = fa2 = None
+    if mat["fibres"]:
+        keep["a1"] = _arr(mesh["fibre_a1"], np.float64)
+        keep["a2"] = _arr(mesh["fibre_a2"], np.float64)
+        fa1 = _ptr(keep["a1"], C.c_double)
+        fa2 = _ptr(keep["a2"], C.c_double)
+    vol = HYEL_VOL_INCOMPRESSIBLE if mat["vol"] == "incompressible" else HYEL_VOL_GIBBS
+    m = HyelMaterial(vol, int(mat["fibres"]), mat["rho0"], mat["mu"], mat["kappa"], mat["k1"],
+                     mat["k2"], mat["kd"], mat["c_m"], (C.c_double * 3)(*mat["body"]),
+                     opt("mu_e"), opt("kappa_e"), opt("k1_e"), opt("k2_e"), fa1, fa2)
+    return m, keep
+
+
 class MeshInputs:
     """Keeps the host arrays that the C structs point to alive."""
 
@@ -300,25 +359,7 @@ class MeshInputs:
                          _ptr(self.dir_val, C.c_double), self.tris.shape[0], _ptr(self.tris, C.c_int32),
                          (C.c_double * 3)(*np.asarray(mesh["traction_dir"], dtype=np.float64)),
                          float(load["p_max"]), float(load["t_ramp"]))
-        self.keep = {}
-
-        def opt(name):
-            if name in fields:
-                a = _arr(fields[name], np.float64)
-                self.keep[name] = a
-                return _ptr(a, C.c_double)
-            return None
-
-        fa1 = fa2 = None
-        if mat["fibres"]:
-            self.keep["a1"] = _arr(mesh["fibre_a1"], np.float64)
-            self.keep["a2"] = _arr(mesh["fibre_a2"], np.float64)
-            fa1 = _ptr(self.keep["a1"], C.c_double)
-            fa2 = _ptr(self.keep["a2"], C.c_double)
-        vol = HYEL_VOL_INCOMPRESSIBLE if mat["vol"] == "incompressible" else HYEL_VOL_GIBBS
-        self.mat = HyelMaterial(vol, int(mat["fibres"]), mat["rho0"], mat["mu"], mat["kappa"], mat["k1"],
-                                mat["k2"], mat["kd"], mat["c_m"], (C.c_double * 3)(*mat["body"]),
-                                opt("mu_e"), opt("kappa_e"), opt("k1_e"), opt("k2_e"), fa1, fa2)
+        self.mat, self.keep = material_struct(mat, fields, mesh)
 
 
 def state_struct(u, p, v, udot, pdot, vdot):
