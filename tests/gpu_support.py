@@ -84,3 +84,15 @@ def row_scaled_error(gpu, orc, rows, nrows):
 
 def gen_alpha(rho_inf):
     return S.gen_alpha(rho_inf)
+
+
+def oracle_blocks_sparse(K, N, rows, cols):
+    """Blocks (rows[k], cols[k]) of a sparse oracle 4N x 4N matrix, vectorized."""
+    K = K.tocsr()
+    r3 = (3 * rows[:, None] + np.arange(3)).astype(np.int64)
+    c3 = (3 * cols[:, None] + np.arange(3)).astype(np.int64)
+    A = np.asarray(K[np.repeat(r3, 3, axis=1).ravel(), np.tile(c3, (1, 3)).ravel()]).reshape(-1, 3, 3)
+    B = np.asarray(K[r3.ravel(), np.repeat(3 * N + cols, 3)]).reshape(-1, 3)
+    C = np.asarray(K[np.repeat(3 * N + rows, 3), c3.ravel()]).reshape(-1, 3)
+    D = np.asarray(K[3 * N + rows, 3 * N + cols]).ravel()
+    return A, B, C, D
