@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark: Newton linear-solve throughput of the nested block-preconditioned
-Newton step on one GB300 (FP64, and FP32 preconditioner levels), plus BSR SpMV
-bandwidth.
+Newton step on one GB300 (FP64; FP32 preconditioner levels; FP32 levels with
+A read as BF16 entries times a per-block FP32 scale), plus BSR SpMV bandwidth.
 
 Workload (one bench step = one generalized-alpha time step, every part of the
 hot path: stage values, element assembly, Dirichlet elimination, diagonal
@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--host-loops", action="store_true",
                    help="drive the Krylov loops from the host (for per-kernel ncu launch lists)")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16s"],
+                   help="preconditioner-level precision of the main timed run (fp64 is the headline; "
+                        "the mixed forms are also timed beside it unless --no-mixed)")
     return p.parse_args()
 
 
@@ -63,7 +66,8 @@ def workload(args):
 
 def config_dict(args, mesh):
     N = mesh["X"].shape[0]
-    return {"workload": f"cube{args.n}^3 compression, nu={args.nu}", "tets": int(mesh["tets"].shape[0]),
+    return {"workload": f"cube{args.n}^3 compression, nu={args.nu}", "levels": args.precision,
+            "tets": int(mesh["tets"].shape[0]),
             "nodes": int(N), "unknowns": int(4 * N), "dt": 1e-3, "rho_inf": 0.5, "outer_rtol": 1e-10,
             "sub_rtol": 1e-2, "steps_per_run": "t = 0..K-1 from rest, load ramp over 10 steps",
             "l2": "working set larger than L2 (FP64 blocks 218 MB, Krylov bases > 1 GB); no flush",
@@ -293,31 +297,40 @@ def run_hyel(args, rank, world, local_rank):
         return ms, its, its_total, launches, prof
 
     graph = 0 if args.host_loops else 1
-    sp64 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP64, graph=graph)
+    main_prec = {"fp64": H.HYEL_PREC_FP64, "fp32": H.HYEL_PREC_FP32, "bf16s": H.HYEL_PREC_BF16S}[args.precision]
+    sp64 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=graph)
     sp32 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, graph=graph)
+    sp16 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_BF16S, graph=graph)
     # warm-up (also builds the Krylov workspaces)
     reset()
     run_steps(args.warmup, sp64)
-    if not args.no_mixed:
-        reset()
-        run_steps(1, sp32)
+    if not args.no_mixed and args.precision == "fp64":
+        for spm in (sp32, sp16):
+            reset()
+            run_steps(1, spm)
     torch.cuda.synchronize()
 
     clocks = Clocks(local_rank)
     clocks.start()
     acc["ms_solve"] = acc["ms_assemble"] = 0.0
-    ms, its, its_total, launches, prof = timed(args.steps, sp64, profile=True)
+    ms, its, its_total, launches, _ = timed(args.steps, sp64)
     ck = clocks.stop()
     solve_ms = acc["ms_solve"] / max(1, its)
     asm_ms = acc["ms_assemble"] / max(1, its + args.steps)
 
-    mixed = None
-    if not args.no_mixed:
-        msm, itsm, itsm_total, _, profm = timed(args.steps, sp32, profile=True)
-        mixed = {"value": n_unk * itsm_total / (msm / 1e3), "unit": UNIT, "ms_per_step": msm / args.steps,
-                 "newton_solves": itsm, "speedup_vs_fp64": ms / msm,
-                 "spmv_A32_gbs": (profm["spmv_A32"]["bytes"] / (profm["spmv_A32"]["ms"] / 1e3) / 1e9
-                                  if profm["spmv_A32"]["ms"] > 0 else None)}
+    final64 = torch.cat([dev[k] for k in names])
+
+    def mixed_run(spm, cls):
+        msm, itsm, itsm_total, _, _ = timed(args.steps, spm)
+        fin = torch.cat([dev[k] for k in names])
+        return {"value": n_unk * itsm_total / (msm / 1e3), "unit": UNIT, "ms_per_step": msm / args.steps,
+                "newton_solves": itsm, "speedup_vs_fp64": ms / msm,
+                "state_rel_diff_vs_fp64": float(torch.linalg.norm(fin - final64) / torch.linalg.norm(final64))}
+
+    mixed = mixed16 = None
+    if not args.no_mixed and args.precision == "fp64":
+        mixed = mixed_run(sp32, "spmv_A32")
+        mixed16 = mixed_run(sp16, "spmv_A16")
     e2e = None
     if not args.no_e2e:
         host = {k: torch.zeros(sizes[k], dtype=torch.float64, pin_memory=True) for k in names}
@@ -345,20 +358,42 @@ def run_hyel(args, rank, world, local_rank):
         by = pr["bytes"] / pr["launches"]
         return by / (us * 1e-6) / 1e9, us, by
 
+    # per-launch CUDA events need host-launched kernels: replay the same K
+    # steps with host-driven Krylov loops (same kernels, same order, same
+    # iterates) and time every launch of the profiled classes on the stream
+    sp_prof = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=0)
+    _, _, _, _, prof_host = timed(args.steps, sp_prof, profile=True)
+    main_cls = {"fp64": "spmv_A64", "fp32": "spmv_A32", "bf16s": "spmv_A16"}[args.precision]
+    pl = prof_host[main_cls]
+    us_live = 1e3 * pl["ms"] / max(1, pl["launches"])
+    by_live = pl["bytes"] / max(1, pl["launches"])
+    gbs_live = by_live / (us_live * 1e-6) / 1e9 if pl["launches"] else None
+
     H.hyel_solve_setup(ctx)
     gbs64, us64, by64 = spmv_timed(H.HYEL_MAT_SCALED64, torch.float64, "spmv_A64")
     gbs32, us32, by32 = spmv_timed(H.HYEL_MAT_SCALED32, torch.float32, "spmv_A32")
-    roof = {"kernel": "k_spmv_A<double> (3x3 BSR SpMV of A, FP64, SELL-32), timed alone, L2 flushed",
-            "bound": "hbm", "achieved": gbs64, "peak": peak, "unit": "GB/s", "frac": gbs64 / peak,
-            "traffic": profile_traffic("spmv_A64_cube48"),
+    gbs16, us16, by16 = spmv_timed(H.HYEL_MAT_SCALED_BF16S, torch.float32, "spmv_A16")
+    kname = {"spmv_A64": "k_spmv_A<double> (3x3 BSR SpMV of A, FP64, SELL-32)",
+             "spmv_A32": "k_spmv_A<float> (3x3 BSR SpMV of A, FP32, SELL-32)",
+             "spmv_A16": "k_spmv_A16 (3x3 BSR SpMV of A, BF16 entries x FP32 block scale, FP32 accumulation)"}
+    roof = {"kernel": kname[main_cls], "bound": "hbm", "achieved": gbs_live, "peak": peak, "unit": "GB/s",
+            "frac": gbs_live / peak if gbs_live else None,
+            "traffic": profile_traffic("spmv_A64_cube48") if main_cls == "spmv_A64" else None,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy burst)" if peak_kind == "measured"
             else "fallback 6.8 TB/s",
-            "bytes_per_launch": by64, "avg_launch_us": us64,
+            "bytes_per_launch": by_live, "avg_launch_us": us_live, "launches": pl["launches"],
+            "measured": "CUDA events around every launch on the library stream, in a host-driven replay of the "
+                        "timed K steps (the graph-mode run has no per-kernel events)",
             "fp64_pipe_note": "9 DFMA per 76-byte block: GB300's 1.2 TFLOP/s FP64 pipe caps this kernel near 5.1 TB/s",
-            "fp32_variant": {"kernel": "k_spmv_A<float>", "achieved": gbs32, "frac": gbs32 / peak,
-                             "bytes_per_launch": by32, "avg_launch_us": us32}}
+            "alone_l2_flushed": {
+                "note": "one launch between two events after a 256 MB L2 flush; includes launch latency",
+                "spmv_A64": {"achieved": gbs64, "frac": gbs64 / peak, "bytes_per_launch": by64, "avg_launch_us": us64},
+                "spmv_A32": {"achieved": gbs32, "frac": gbs32 / peak, "bytes_per_launch": by32, "avg_launch_us": us32},
+                "spmv_A16": {"achieved": gbs16, "frac": gbs16 / peak, "bytes_per_launch": by16,
+                             "avg_launch_us": us16}}}
     kclass = {k: {"ms": v["ms"], "launches": v["launches"],
-                  "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None)} for k, v in prof.items()}
+                  "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None)}
+              for k, v in prof_host.items()}
     H.hyel_destroy(ctx)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -367,11 +402,13 @@ def run_hyel(args, rank, world, local_rank):
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jittered cube, no dataset)",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64 outer / f32 levels",
+                                             "bf16s": "f64 outer / f32 levels, bf16 A"}[args.precision], "data": "synthetic (seeded jittered cube, no dataset)",
             "config": config_dict(args, mesh), "clocks": ck, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "cpu_baseline": cpu,
             "newton_solves": its, "solve_ms_per_newton_it": solve_ms, "assembly_ms_per_pass": asm_ms,
-            "mixed_fp32_preconditioner": mixed, "kernel_classes": kclass}
+            "mixed_fp32_preconditioner": mixed, "mixed_bf16s_preconditioner": mixed16,
+            "kernel_classes_host_replay": kclass}
     print(json.dumps(line), flush=True)
 
 

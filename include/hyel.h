@@ -123,8 +123,12 @@ typedef struct {
 
 /* Precision of the preconditioner levels (intermediate and inner solvers,
  * their SpMVs and Gram-Schmidt). The outer FGMRES, its Gram-Schmidt and
- * Givens, the residual assembly and the Newton update are always FP64. */
-enum { HYEL_PREC_FP64 = 0, HYEL_PREC_FP32 = 1 };
+ * Givens, the residual assembly and the Newton update are always FP64.
+ * HYEL_PREC_BF16S: as HYEL_PREC_FP32, except that the A-SpMVs of the A-solves
+ * read each scaled 3x3 block of A as nine BF16 values times one FP32 scale
+ * (s = max |entry|, stored entries = bf16_rn(float(a) / s)), accumulating in
+ * FP32. B, C, D, the block-Jacobi inverses and diag(S^) stay FP32. */
+enum { HYEL_PREC_FP64 = 0, HYEL_PREC_FP32 = 1, HYEL_PREC_BF16S = 2 };
 
 /* One Krylov level: stop when ||r|| <= max(rtol ||b||, atol) or after maxit
  * iterations; restart every `restart` iterations. Zero initial guess. */
@@ -225,7 +229,8 @@ int hyel_matrix_download(hyel_ctx *ctx, int32_t *row_ptr, int32_t *col,
 /* ---------------------------------------------------------------- operators */
 
 enum { HYEL_OP_FULL = 0, HYEL_OP_A = 1, HYEL_OP_B = 2, HYEL_OP_C = 3, HYEL_OP_D = 4 };
-enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYEL_MAT_TRANSPOSED = 3 };
+enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYEL_MAT_TRANSPOSED = 3,
+       HYEL_MAT_SCALED_BF16S = 4 };
 
 /* y = op(M) x on device vectors. FULL: [4N] -> [4N]; A: [3N] -> [3N];
  * B: [N] -> [3N]; C: [3N] -> [N]; D: [N] -> [N]. x, y are double for the
@@ -234,11 +239,14 @@ enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYE
  * HYEL_MAT_TRANSPOSED (FULL only): y = [[A^T, C^T], [B^T, D^T]] x, the
  * transpose of the assembled operator, built on first use after each
  * assembly (the block pattern is symmetric; block (i, c) of the transpose is
- * taken from block (c, i)). */
+ * taken from block (c, i)).
+ * HYEL_MAT_SCALED_BF16S (A only, float x and y): the BF16-with-block-scale
+ * copy of the scaled A described at HYEL_PREC_BF16S. */
 int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y);
 
 /* Prepare the scaled system for the current assembly (§4.1): W_ii =
- * |A_ii|^-1/2 (1 if |A_ii| < 1e-15), scaled FP64 and FP32 blocks, 3x3
+ * |A_ii|^-1/2 (1 if |A_ii| < 1e-15), scaled FP64 and FP32 blocks, the
+ * BF16-with-block-scale copy of the scaled A, 3x3
  * block-Jacobi inverses of A and diag(S^). w_out: device [4N] or NULL. */
 int hyel_solve_setup(hyel_ctx *ctx, double *w_out);
 
@@ -304,7 +312,7 @@ int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solv
 
 /* Kernel classes timed with CUDA events on the context's stream when enabled. */
 enum { HYEL_K_SPMV_A64 = 0, HYEL_K_SPMV_A32 = 1, HYEL_K_SPMV_FULL64 = 2,
-       HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_NCLASSES = 5 };
+       HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_SPMV_A16 = 5, HYEL_K_NCLASSES = 6 };
 
 /* enable != 0 starts event timing of the kernel classes (and clears the
  * totals); 0 stops it. */

@@ -210,7 +210,7 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "spmv: null vector");
         if (op < HYEL_OP_FULL || op > HYEL_OP_D) hyel::fail(HYEL_EINVAL, "spmv: bad op");
-        if (matrix < HYEL_MAT_ASSEMBLED || matrix > HYEL_MAT_TRANSPOSED) hyel::fail(HYEL_EINVAL, "spmv: bad matrix");
+        if (matrix < HYEL_MAT_ASSEMBLED || matrix > HYEL_MAT_SCALED_BF16S) hyel::fail(HYEL_EINVAL, "spmv: bad matrix");
         if (!c.mat.assembled) hyel::fail(HYEL_ESTATE, "spmv: nothing assembled");
         if (matrix == HYEL_MAT_TRANSPOSED) {
             if (op != HYEL_OP_FULL) hyel::fail(HYEL_EINVAL, "spmv: the transposed matrix supports HYEL_OP_FULL only");
@@ -220,7 +220,10 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
         }
         if (matrix != HYEL_MAT_ASSEMBLED && !c.mat.scaled) hyel::fail(HYEL_ESTATE, "spmv: call hyel_solve_setup first");
         hyel::DeviceMatrix &M = c.mat;
-        if (matrix == HYEL_MAT_SCALED32) {
+        if (matrix == HYEL_MAT_SCALED_BF16S) {
+            if (op != HYEL_OP_A) hyel::fail(HYEL_EINVAL, "spmv: the BF16 copy holds A only");
+            hyel::spmv_A16_ind(c, (const float *)x, (float *)y, 0, nullptr);
+        } else if (matrix == HYEL_MAT_SCALED32) {
             const float *xf = (const float *)x;
             float *yf = (float *)y;
             switch (op) {

@@ -84,6 +84,12 @@ struct DeviceMatrix {
     double *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr;      // assembled
     double *As = nullptr, *Bs = nullptr, *Cs = nullptr, *Ds = nullptr;  // scaled FP64
     float *Af = nullptr, *Bf = nullptr, *Cf = nullptr, *Df = nullptr;   // scaled FP32
+    // scaled A as BF16 x per-block FP32 scale, one record per slot q:
+    // Ah8[q] = entries 0..7 (row-major, two per 32-bit word), Ah1[q] = entry 8,
+    // Ahs[q] = scale s = max |entry| (0 for padding)
+    uint4 *Ah8 = nullptr;
+    uint16_t *Ah1 = nullptr;
+    float *Ahs = nullptr;
     double *w = nullptr;        // [4N] scaling
     double *jac64 = nullptr;    // [9][N] inverses of scaled diagonal blocks of A
     float *jac32 = nullptr;
@@ -182,6 +188,8 @@ template <typename T>
 void spmv_A(Ctx &c, const T *Av, const T *x, T *y);
 template <typename T>
 void spmv_A_ind(Ctx &c, const T *Av, const T *x, T *y, int64_t ystride, const int *kd);
+// A-SpMV on the BF16-with-block-scale copy of the scaled A (see HYEL_PREC_BF16S)
+void spmv_A16_ind(Ctx &c, const float *x, float *y, int64_t ystride, const int *kd);
 void spmv_full64(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,
                  double *y);
 void spmv_full64_ind(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,

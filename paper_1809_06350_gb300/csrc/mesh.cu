@@ -311,6 +311,9 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     M.Bf = dalloc_n<float>(c, 3 * ns);
     M.Cf = dalloc_n<float>(c, 3 * ns);
     M.Df = dalloc_n<float>(c, ns);
+    M.Ah8 = dalloc_n<uint4>(c, ns);
+    M.Ah1 = dalloc_n<uint16_t>(c, ns);
+    M.Ahs = dalloc_n<float>(c, ns);
     M.w = dalloc_n<double>(c, 4 * (size_t)N);
     M.jac64 = dalloc_n<double>(c, 9 * (size_t)N);
     M.jac32 = dalloc_n<float>(c, 9 * (size_t)N);

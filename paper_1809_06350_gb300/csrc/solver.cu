@@ -15,7 +15,9 @@
 // * Precision: the intermediate and inner levels (A-, S- and inner solves,
 //   their SpMVs and Gram-Schmidt) run in T = double or float; the outer
 //   FGMRES, its Gram-Schmidt and Givens stay FP64 and its flexible basis Z is
-//   FP64, so the outer iteration acts as iterative refinement.
+//   FP64, so the outer iteration acts as iterative refinement. The BF16S
+//   variant runs the float levels with A read from its BF16-with-block-scale
+//   copy in the A-solves.
 //
 // Control flow: every Krylov level keeps its state (iteration index, norms,
 // flags) in device memory and every kernel reads it there. The whole nested
@@ -33,6 +35,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -700,7 +703,8 @@ void check_params(const hyel_solver_params &p) {
         if (l->maxit < 1) fail(HYEL_EINVAL, "solver params: maxit must be >= 1");
         if (!(l->rtol >= 0) || !(l->atol >= 0)) fail(HYEL_EINVAL, "solver params: tolerances must be >= 0");
     }
-    if (p.precision != HYEL_PREC_FP64 && p.precision != HYEL_PREC_FP32) fail(HYEL_EINVAL, "solver params: bad precision");
+    if (p.precision != HYEL_PREC_FP64 && p.precision != HYEL_PREC_FP32 && p.precision != HYEL_PREC_BF16S)
+        fail(HYEL_EINVAL, "solver params: bad precision");
     if (p.check_every < 1) fail(HYEL_EINVAL, "solver params: check_every must be >= 1");
 }
 
@@ -784,6 +788,12 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
     Ctx &c = *R.c;
     Level<T> &L = Sys<T>::la(w);
     gm_solve<T, 0>(R, L, st, P, b, x, Sys<T>::jac(c), nullptr, [&]() {
+        if constexpr (std::is_same<T, float>::value) {
+            if (w.prec == HYEL_PREC_BF16S) {
+                spmv_A16_ind(c, L.z, L.V, L.n, &st->k);
+                return;
+            }
+        }
         spmv_A_ind<T>(c, Sys<T>::A(c), L.z, L.V, L.n, &st->k);
     });
 }

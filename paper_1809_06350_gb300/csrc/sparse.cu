@@ -7,6 +7,8 @@
 // x is gathered by column (three consecutive values per node). Accumulation
 // is in the value type (FP64, or FP32 for the single-precision copies), in a
 // fixed order: results are bitwise reproducible.
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include "internal.h"
@@ -20,6 +22,9 @@ struct ScaleArgs {
     const double *A, *B, *C, *D;
     double *As, *Bs, *Cs, *Ds;
     float *Af, *Bf, *Cf, *Df;
+    uint4 *Ah8;
+    uint16_t *Ah1;
+    float *Ahs;
     double *w;  // [4N]
     double *jac64;
     float *jac32;
@@ -60,15 +65,27 @@ __global__ void k_scale_values(ScaleArgs a) {
         wpr = a.w[3 * a.N + r];
         wpc = a.w[3 * a.N + c];
     }
+    double v[9], amax = 0.0;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             const int64_t o = (b * 9 + 3 * i + j) * 32 + t;
-            const double v = a.A[o] * wr[i] * wc[j];
-            a.As[o] = v;
-            a.Af[o] = (float)v;
+            v[3 * i + j] = a.A[o] * wr[i] * wc[j];
+            a.As[o] = v[3 * i + j];
+            a.Af[o] = (float)v[3 * i + j];
+            amax = fmax(amax, fabs(v[3 * i + j]));
         }
+    // BF16 copy with one FP32 scale per block: e_k = bf16_rn(float(v_k) / s)
+    const float sc = (float)amax;
+    unsigned short h[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++)
+        h[k] = sc > 0.0f ? __bfloat16_as_ushort(__float2bfloat16_rn(__fdiv_rn((float)v[k], sc))) : (unsigned short)0;
+    a.Ah8[q] = make_uint4(h[0] | ((unsigned)h[1] << 16), h[2] | ((unsigned)h[3] << 16), h[4] | ((unsigned)h[5] << 16),
+                          h[6] | ((unsigned)h[7] << 16));
+    a.Ah1[q] = h[8];
+    a.Ahs[q] = sc;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         const int64_t o = (b * 3 + i) * 32 + t;
@@ -213,6 +230,51 @@ __global__ void __launch_bounds__(128) k_spmv_A(const int32_t *__restrict__ slic
         a2 = fma(__ldg(Ab + 192), x0, a2);
         a2 = fma(__ldg(Ab + 224), x1, a2);
         a2 = fma(__ldg(Ab + 256), x2, a2);
+    }
+    y[3 * r] = a0;
+    y[3 * r + 1] = a1;
+    y[3 * r + 2] = a2;
+}
+
+// A-SpMV on the BF16-with-block-scale copy, FP32 accumulation: per block,
+// t_i = sum_j e_ij x_j, y_i += s t_i. Entry 2k of a block sits in the low half
+// of word k of its 16-byte record, entry 2k+1 in the high half; a BF16 value
+// widens to FP32 by a 16-bit shift.
+__global__ void __launch_bounds__(128) k_spmv_A16(const int32_t *__restrict__ slice_ptr,
+                                                  const int32_t *__restrict__ row_len, const int32_t *__restrict__ col,
+                                                  const uint4 *__restrict__ Ah8, const uint16_t *__restrict__ Ah1,
+                                                  const float *__restrict__ Ahs, const float *__restrict__ x,
+                                                  float *__restrict__ y, int64_t N, const int *kd, int64_t ystride) {
+    if (kd) {
+        if (kd[1]) return;
+        y += (int64_t)(kd[0] + 1) * ystride;
+    }
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const int t = (int)(r & 31);
+    const int64_t b0 = slice_ptr[r >> 5];
+    const int len = row_len[r];
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < len; j++) {
+        const int64_t q = (b0 + j) * 32 + t;
+        const int64_t c = __ldg(col + q);
+        const uint4 w = __ldg(Ah8 + q);
+        const unsigned e8 = __ldg(Ah1 + q);
+        const float s = __ldg(Ahs + q);
+        const float x0 = __ldg(x + 3 * c), x1 = __ldg(x + 3 * c + 1), x2 = __ldg(x + 3 * c + 2);
+        float t0 = __uint_as_float(w.x << 16) * x0;
+        t0 = fmaf(__uint_as_float(w.x & 0xffff0000u), x1, t0);
+        t0 = fmaf(__uint_as_float(w.y << 16), x2, t0);
+        float t1 = __uint_as_float(w.y & 0xffff0000u) * x0;
+        t1 = fmaf(__uint_as_float(w.z << 16), x1, t1);
+        t1 = fmaf(__uint_as_float(w.z & 0xffff0000u), x2, t1);
+        float t2 = __uint_as_float(w.w << 16) * x0;
+        t2 = fmaf(__uint_as_float(w.w & 0xffff0000u), x1, t2);
+        t2 = fmaf(__uint_as_float(e8 << 16), x2, t2);
+        a0 = fmaf(s, t0, a0);
+        a1 = fmaf(s, t1, a1);
+        a2 = fmaf(s, t2, a2);
     }
     y[3 * r] = a0;
     y[3 * r + 1] = a1;
@@ -377,6 +439,9 @@ ScaleArgs scale_args(Ctx &c) {
     a.Bf = M.Bf;
     a.Cf = M.Cf;
     a.Df = M.Df;
+    a.Ah8 = M.Ah8;
+    a.Ah1 = M.Ah1;
+    a.Ahs = M.Ahs;
     a.w = M.w;
     a.jac64 = M.jac64;
     a.jac32 = M.jac32;
@@ -426,7 +491,9 @@ void spmv_A_ind(Ctx &c, const T *Av, const T *x, T *y, int64_t ystride, const in
     const int cls = sizeof(T) == 8 ? HYEL_K_SPMV_A64 : HYEL_K_SPMV_A32;
     cudaEvent_t ev;
     prof_begin(c, cls, &ev);
-    (k_spmv_A<T><<<blocks_for(m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, kd,
+    // one-warp blocks: with one thread per row the grid is too small to fill
+    // the SMs, and single-slice blocks spread it evenly over them
+    (k_spmv_A<T><<<blocks_for(m.N, 32), 32, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, kd,
                                                             ystride), ::hyel::count_launch());
     // algorithmic bytes: 9 values + 1 column index per block, x and y once
     prof_end(c, cls, ev, (double)m.nnzb * (9.0 * sizeof(T) + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * sizeof(T));
@@ -439,6 +506,17 @@ template void spmv_A<double>(Ctx &, const double *, const double *, double *);
 template void spmv_A<float>(Ctx &, const float *, const float *, float *);
 template void spmv_A_ind<double>(Ctx &, const double *, const double *, double *, int64_t, const int *);
 template void spmv_A_ind<float>(Ctx &, const float *, const float *, float *, int64_t, const int *);
+
+void spmv_A16_ind(Ctx &c, const float *x, float *y, int64_t ystride, const int *kd) {
+    const DeviceMesh &m = c.mesh;
+    const DeviceMatrix &M = c.mat;
+    cudaEvent_t ev;
+    prof_begin(c, HYEL_K_SPMV_A16, &ev);
+    (k_spmv_A16<<<blocks_for(m.N, 32), 32, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, M.Ah8, M.Ah1, M.Ahs, x, y,
+                                                            m.N, kd, ystride), ::hyel::count_launch());
+    // algorithmic bytes: 9 BF16 values + 1 FP32 scale + 1 column index per block, x and y once
+    prof_end(c, HYEL_K_SPMV_A16, ev, (double)m.nnzb * (18.0 + 4.0 + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * 4);
+}
 
 void spmv_full64_ind(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,
                      double *y, int64_t stride, const int *kd) {

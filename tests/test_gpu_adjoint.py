@@ -48,7 +48,7 @@ def test_transposed_spmv_and_solve():
     assert np.all(np.abs(y.cpu().numpy() - KT @ x) <= 1e-13 * (abs(KT) @ np.abs(x)) + 1e-300)
     r = inputs.random_vector(4 * N, seed=6) * np.concatenate([~prob.dir_mask.ravel(), np.ones(N, bool)])
     xo = S.direct_solve(KT, r)
-    for prec in (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32):
+    for prec in (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S):
         xg = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
         stt, rc = H.hyel_solve_nested_transpose(gp.ctx, H.solver_params(outer_rtol=1e-13, precision=prec),
                                                 _dev(r).data_ptr(), xg.data_ptr())

@@ -8,7 +8,8 @@ solver, FP64 and FP32 preconditioner levels).
 * Residual: the whole R_m, R_p vector against the oracle (real arithmetic).
 * Newton step: the oracle's residual at the GPU's converged state satisfies
   the stopping test ||R||/||R_(0)|| <= tol_R (a property any correct step has,
-  at any size); FP32 preconditioner levels reach the FP64 state to 1e-9.
+  at any size); FP32 preconditioner levels, and FP32 levels with the BF16 A,
+  reach the FP64 state to 1e-9.
 """
 import numpy as np
 import pytest
@@ -90,7 +91,7 @@ def test_fullsize_newton_step_fp64_and_fp32(big):
     ydz = {k: z[k] for k in ("udot", "pdot", "vdot")}
     norm0 = _oracle_norm(prob, yz, ydz, yz, ydz, 0.0)  # predictor from rest: y1 = 0, ydot1 = 0
     finals = {}
-    for prec in (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32):
+    for prec in (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S):
         dev = {k: gp.dev(z[k]) for k in z}
         state = H.state_struct(dev["u"], dev["p"], dev["v"], dev["udot"], dev["pdot"], dev["vdot"])
         sp_ = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=prec, graph=1)
@@ -104,5 +105,6 @@ def test_fullsize_newton_step_fp64_and_fp32(big):
         assert abs(nrm - st.res_norm) <= 1e-12 * norm0
         finals[prec] = np.concatenate([y1[k].ravel() for k in ("u", "p", "v")] +
                                       [yd1[k].ravel() for k in ("udot", "pdot", "vdot")])
-    f64, f32 = finals[H.HYEL_PREC_FP64], finals[H.HYEL_PREC_FP32]
-    assert np.linalg.norm(f32 - f64) / np.linalg.norm(f64) <= 1e-9
+    f64 = finals[H.HYEL_PREC_FP64]
+    for prec in (H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S):
+        assert np.linalg.norm(finals[prec] - f64) / np.linalg.norm(f64) <= 1e-9, prec

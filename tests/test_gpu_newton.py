@@ -22,7 +22,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
+@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S])
 def test_two_newton_steps_match_oracle(precision):
     m = inputs.cube_mesh(8)
     mat = inputs.material_nh(1e5, 1e6, 1e3)

@@ -1,11 +1,14 @@
 """GPU parity of the linear-algebra path against the oracle (config-1 cube).
 
 * block SpMVs (FP64 assembled/scaled, FP32 scaled) vs the oracle matrix;
+* the BF16-with-block-scale A-SpMV vs the same quantization applied to the
+  oracle's scaled A, and within the quantization bound of the exact product;
 * the symmetric diagonal scaling W (§4.1) vs its definition;
 * the matrix-free Schur product (Algorithm 2) with a tight inner solve vs the
   explicit dense S = D - C A^-1 B of the scaled system;
 * the nested FGMRES solve vs the oracle's direct solve: relative error <= 1e-9
-  at outer tolerance 1e-13, in FP64 and with FP32 preconditioner levels;
+  at outer tolerance 1e-13, in FP64, with FP32 preconditioner levels and with
+  the BF16 A in the FP32 levels;
 * tight intermediate/inner tolerances give convergence in <= 2 outer
   iterations (exact LDU preconditioner, §4.4);
 * status codes: iteration cap, NaN right-hand side.
@@ -83,6 +86,48 @@ def test_scaling_and_fp32_spmv(cube):
     assert np.all(np.abs(y64.cpu().numpy() - As @ x) <= 1e-13 * (abs(As) @ np.abs(x)))
 
 
+def _bf16_rn(f):
+    """float32 -> nearest bfloat16 (ties to even), returned as float32."""
+    u = np.asarray(f, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) & 0xFFFF
+    return (r << 16).astype(np.uint32).view(np.float32)
+
+
+def test_bf16_rounding_helper():
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: even mantissa (1) wins
+    assert _bf16_rn(np.float32(1 + 2.0 ** -8)) == 1.0
+    assert _bf16_rn(np.float32(1 + 3 * 2.0 ** -8)) == np.float32(1 + 2.0 ** -6)
+    assert _bf16_rn(np.float32(-(1 + 2.0 ** -8 + 2.0 ** -20))) == np.float32(-(1 + 2.0 ** -7))
+
+
+def test_bf16s_spmv(cube):
+    """y = A x with each scaled 3x3 block read as s * e, s = float32(max|a|),
+    e = bf16_rn(float32(a) / s): equal, up to FP32 accumulation, to the same
+    quantization applied to the oracle's scaled A; within 2^-9 |A||x| (plus
+    FP32 accumulation) of the exact product; and visibly quantized."""
+    gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
+    H.hyel_solve_setup(gp.ctx)
+    wo = S.diag_scaling(Kd)
+    As = S.split_blocks(sp.diags(wo) @ Kd @ sp.diags(wo), N)[0]
+    bsr = sp.bsr_matrix(As, blocksize=(3, 3))
+    blk = bsr.data
+    s = np.abs(blk).max(axis=(1, 2)).astype(np.float32)
+    safe = np.where(s > 0, s, np.float32(1))
+    e = _bf16_rn(blk.astype(np.float32) / safe[:, None, None])
+    Q = sp.bsr_matrix((e.astype(np.float64) * s[:, None, None].astype(np.float64), bsr.indices, bsr.indptr),
+                      shape=As.shape)
+    x32 = inputs.random_vector(3 * N, seed=19).astype(np.float32)
+    x = x32.astype(np.float64)
+    y = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
+    H.hyel_spmv(gp.ctx, H.HYEL_OP_A, H.HYEL_MAT_SCALED_BF16S, _dev(x32, torch.float32).data_ptr(), y.data_ptr())
+    yg = y.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(yg - Q @ x) <= 2e-6 * (abs(Q) @ np.abs(x)))
+    bound = abs(As) @ np.abs(x)
+    dev_exact = np.abs(yg - As @ x)
+    assert np.all(dev_exact <= (2.0 ** -9 + 4e-6) * bound)
+    assert np.max(dev_exact / bound) > 2.0 ** -14
+
+
 @pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
 def test_schur_product_algorithm2(cube, precision):
     gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
@@ -100,7 +145,7 @@ def test_schur_product_algorithm2(cube, precision):
     assert err <= (1e-9 if precision == H.HYEL_PREC_FP64 else 1e-4), err
 
 
-@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
+@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S])
 def test_nested_solve_matches_direct(cube, precision):
     gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
     xo = S.direct_solve(Kd, cube["rhs_o"])
@@ -136,7 +181,7 @@ def test_iteration_cap_and_nan(cube):
     assert rc == H.HYEL_OK
 
 
-@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
+@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S])
 def test_graph_and_host_driven_loops_agree_bitwise(cube, precision):
     """The CUDA-graph solve (device-driven while loops) and the host-driven
     replay run the same kernels in the same order: identical iterates."""
