@@ -136,12 +136,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel; else None."""
+def profile_traffic(kernel, source="sparse.cu", field="dram_bytes_per_launch_full_size"):
+    """DRAM bytes (per launch, or per unit named by `field`) from the committed
+    ncu summary, if it was taken on the current source of the kernel; else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel}.md")
-    src = os.path.join(ROOT, "paper_1809_06350_gb300", "csrc", "sparse.cu")
+    src = os.path.join(ROOT, "paper_1809_06350_gb300", "csrc", source)
     try:
         text = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -149,7 +149,7 @@ def profile_traffic(kernel):
         fields = {k.strip("- ").strip(): v.strip() for k, v in fields.items()}
         if fields.get("source_sha256_16") != sha:
             return None
-        return float(fields["dram_bytes_per_launch_full_size"])
+        return float(fields[field])
     except Exception:
         return None
 
@@ -363,8 +363,7 @@ def run_hyel(args, rank, world, local_rank):
     # iterates) and time every launch of the profiled classes on the stream
     sp_prof = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=0)
     _, _, _, _, prof_host = timed(args.steps, sp_prof, profile=True)
-    main_cls = {"fp64": "spmv_A64", "fp32": "spmv_A32", "bf16s": "spmv_A16"}[args.precision]
-    pl = prof_host[main_cls]
+    pl = prof_host["gmres_A"]
     us_live = 1e3 * pl["ms"] / max(1, pl["launches"])
     by_live = pl["bytes"] / max(1, pl["launches"])
     gbs_live = by_live / (us_live * 1e-6) / 1e9 if pl["launches"] else None
@@ -373,18 +372,23 @@ def run_hyel(args, rank, world, local_rank):
     gbs64, us64, by64 = spmv_timed(H.HYEL_MAT_SCALED64, torch.float64, "spmv_A64")
     gbs32, us32, by32 = spmv_timed(H.HYEL_MAT_SCALED32, torch.float32, "spmv_A32")
     gbs16, us16, by16 = spmv_timed(H.HYEL_MAT_SCALED_BF16S, torch.float32, "spmv_A16")
-    kname = {"spmv_A64": "k_spmv_A<double> (3x3 BSR SpMV of A, FP64, SELL-32)",
-             "spmv_A32": "k_spmv_A<float> (3x3 BSR SpMV of A, FP32, SELL-32)",
-             "spmv_A16": "k_spmv_A16 (3x3 BSR SpMV of A, BF16 entries x FP32 block scale, FP32 accumulation)"}
-    roof = {"kernel": kname[main_cls], "bound": "hbm", "achieved": gbs_live, "peak": peak, "unit": "GB/s",
+    kname = {"fp64": "k_gmres_a<double>", "fp32": "k_gmres_a<float>", "bf16s": "k_gmres_a<float, bf16>"}
+    traffic_ratio = profile_traffic("gmres_a_cube48", "solver.cu", "dram_over_algorithmic")
+    roof = {"kernel": kname[args.precision] + " (persistent A-solve, one cooperative launch per A-solve: SELL-32 "
+                                              "SpMV of A M^-1, CGS2, Givens, solution update)",
+            "bound": "hbm", "achieved": gbs_live, "peak": peak, "unit": "GB/s",
             "frac": gbs_live / peak if gbs_live else None,
-            "traffic": profile_traffic("spmv_A64_cube48") if main_cls == "spmv_A64" else None,
+            "traffic": (traffic_ratio * by_live if traffic_ratio is not None and args.precision == "fp64"
+                        else None),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy burst)" if peak_kind == "measured"
             else "fallback 6.8 TB/s",
             "bytes_per_launch": by_live, "avg_launch_us": us_live, "launches": pl["launches"],
+            "algorithmic_bytes": "per iteration j: A M^-1 values + indices + 4(N+1), and 4(j+1)+9 passes over "
+                                 "3N-vectors (counted on the device, summed over the launch's iterations)",
             "measured": "CUDA events around every launch on the library stream, in a host-driven replay of the "
                         "timed K steps (the graph-mode run has no per-kernel events)",
-            "fp64_pipe_note": "9 DFMA per 76-byte block: GB300's 1.2 TFLOP/s FP64 pipe caps this kernel near 5.1 TB/s",
+            "fp64_pipe_note": "9 DFMA per 76-byte block: GB300's 1.2 TFLOP/s FP64 pipe caps the SpMV phase near "
+                              "5.1 TB/s",
             "alone_l2_flushed": {
                 "note": "one launch between two events after a 256 MB L2 flush; includes launch latency",
                 "spmv_A64": {"achieved": gbs64, "frac": gbs64 / peak, "bytes_per_launch": by64, "avg_launch_us": us64},

@@ -147,9 +147,11 @@ typedef struct {
  * graph = 1 (default): the whole nested solve is one CUDA graph whose Krylov
  * loops are device-driven `while` conditional nodes (no host round trip until
  * the solve ends); the graph is built once per context and parameter set.
- * graph = 0: the host drives the loops, checking convergence every
- * `check_every` (>= 1) iterations. Both run the same kernels and give the
- * same iterates. */
+ * graph = 0: the host drives the outer and S loops, reading the level state
+ * after every iteration. Both run the same kernels and give the same
+ * iterates. Every A-solve (intermediate and inner) is one cooperative launch
+ * of a persistent GMRES kernel on A M^-1 (M the 3x3 block diagonal of A) in
+ * both modes. check_every (>= 1) is validated and otherwise unused. */
 typedef struct {
     hyel_krylov_level outer, a, s, inner;
     int32_t precision;      /* HYEL_PREC_* */
@@ -228,7 +230,7 @@ int hyel_matrix_download(hyel_ctx *ctx, int32_t *row_ptr, int32_t *col,
 
 /* ---------------------------------------------------------------- operators */
 
-enum { HYEL_OP_FULL = 0, HYEL_OP_A = 1, HYEL_OP_B = 2, HYEL_OP_C = 3, HYEL_OP_D = 4 };
+enum { HYEL_OP_FULL = 0, HYEL_OP_A = 1, HYEL_OP_B = 2, HYEL_OP_C = 3, HYEL_OP_D = 4, HYEL_OP_AM = 5 };
 enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYEL_MAT_TRANSPOSED = 3,
        HYEL_MAT_SCALED_BF16S = 4 };
 
@@ -240,8 +242,11 @@ enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYE
  * transpose of the assembled operator, built on first use after each
  * assembly (the block pattern is symmetric; block (i, c) of the transpose is
  * taken from block (c, i)).
- * HYEL_MAT_SCALED_BF16S (A only, float x and y): the BF16-with-block-scale
- * copy of the scaled A described at HYEL_PREC_BF16S. */
+ * HYEL_MAT_SCALED_BF16S (A and AM only, float x and y): the BF16-with-block-
+ * scale copies described at HYEL_PREC_BF16S.
+ * AM ([3N] -> [3N], scaled matrices only): y = A M^-1 x with M the 3x3 block
+ * diagonal of the scaled A, i.e. A right-preconditioned by block-Jacobi; the
+ * A-solves iterate on this operator (stored block by block as A_(r,c) M_c^-1). */
 int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y);
 
 /* Prepare the scaled system for the current assembly (§4.1): W_ii =
@@ -310,9 +315,15 @@ int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solv
 
 /* ---------------------------------------------------------------- profiling */
 
-/* Kernel classes timed with CUDA events on the context's stream when enabled. */
+/* Kernel classes timed with CUDA events on the context's stream when enabled
+ * (launches made while a solve runs as a CUDA graph are not timed).
+ * HYEL_K_GMRES_A is the persistent A-solve kernel (one launch per A-solve);
+ * its algorithmic bytes are counted per iteration j as the A M^-1 values and
+ * indices plus 4 (j+1) + 9 passes over 3N-vectors, and are added when the
+ * solve that launched it returns. */
 enum { HYEL_K_SPMV_A64 = 0, HYEL_K_SPMV_A32 = 1, HYEL_K_SPMV_FULL64 = 2,
-       HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_SPMV_A16 = 5, HYEL_K_NCLASSES = 6 };
+       HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_SPMV_A16 = 5, HYEL_K_GMRES_A = 6,
+       HYEL_K_NCLASSES = 7 };
 
 /* enable != 0 starts event timing of the kernel classes (and clears the
  * totals); 0 stops it. */

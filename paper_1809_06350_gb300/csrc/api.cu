@@ -209,7 +209,9 @@ int hyel_matrix_download(hyel_ctx *ctx, int32_t *row_ptr, int32_t *col, double *
 int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "spmv: null vector");
-        if (op < HYEL_OP_FULL || op > HYEL_OP_D) hyel::fail(HYEL_EINVAL, "spmv: bad op");
+        if (op < HYEL_OP_FULL || op > HYEL_OP_AM) hyel::fail(HYEL_EINVAL, "spmv: bad op");
+        if (op == HYEL_OP_AM && (matrix == HYEL_MAT_ASSEMBLED || matrix == HYEL_MAT_TRANSPOSED))
+            hyel::fail(HYEL_EINVAL, "spmv: A M^-1 exists for the scaled matrices only");
         if (matrix < HYEL_MAT_ASSEMBLED || matrix > HYEL_MAT_SCALED_BF16S) hyel::fail(HYEL_EINVAL, "spmv: bad matrix");
         if (!c.mat.assembled) hyel::fail(HYEL_ESTATE, "spmv: nothing assembled");
         if (matrix == HYEL_MAT_TRANSPOSED) {
@@ -221,13 +223,18 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
         if (matrix != HYEL_MAT_ASSEMBLED && !c.mat.scaled) hyel::fail(HYEL_ESTATE, "spmv: call hyel_solve_setup first");
         hyel::DeviceMatrix &M = c.mat;
         if (matrix == HYEL_MAT_SCALED_BF16S) {
-            if (op != HYEL_OP_A) hyel::fail(HYEL_EINVAL, "spmv: the BF16 copy holds A only");
-            hyel::spmv_A16_ind(c, (const float *)x, (float *)y, 0, nullptr);
+            if (op == HYEL_OP_A)
+                hyel::spmv_A16_ind(c, M.Ah8, M.Ah1, M.Ahs, (const float *)x, (float *)y, 0, nullptr);
+            else if (op == HYEL_OP_AM)
+                hyel::spmv_A16_ind(c, M.Amh8, M.Amh1, M.Amhs, (const float *)x, (float *)y, 0, nullptr);
+            else
+                hyel::fail(HYEL_EINVAL, "spmv: the BF16 copies hold A and A M^-1 only");
         } else if (matrix == HYEL_MAT_SCALED32) {
             const float *xf = (const float *)x;
             float *yf = (float *)y;
             switch (op) {
                 case HYEL_OP_A: hyel::spmv_A<float>(c, M.Af, xf, yf); break;
+                case HYEL_OP_AM: hyel::spmv_A<float>(c, M.Amf, xf, yf); break;
                 case HYEL_OP_B: hyel::spmv_B<float>(c, M.Bf, xf, yf, nullptr); break;
                 case HYEL_OP_C: hyel::spmv_C<float>(c, M.Cf, xf, yf, nullptr); break;
                 case HYEL_OP_D: hyel::spmv_D<float>(c, M.Df, xf, yf); break;
@@ -243,6 +250,7 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
             switch (op) {
                 case HYEL_OP_FULL: hyel::spmv_full64(c, Av, Bv, Cv, Dv, xd, yd); break;
                 case HYEL_OP_A: hyel::spmv_A<double>(c, Av, xd, yd); break;
+                case HYEL_OP_AM: hyel::spmv_A<double>(c, M.Ams, xd, yd); break;
                 case HYEL_OP_B: hyel::spmv_B<double>(c, Bv, xd, yd, nullptr); break;
                 case HYEL_OP_C: hyel::spmv_C<double>(c, Cv, xd, yd, nullptr); break;
                 case HYEL_OP_D: hyel::spmv_D<double>(c, Dv, xd, yd); break;

@@ -90,6 +90,14 @@ struct DeviceMatrix {
     uint4 *Ah8 = nullptr;
     uint16_t *Ah1 = nullptr;
     float *Ahs = nullptr;
+    // right-preconditioned operator of the A-solves, A~ = A M^-1 with M the
+    // 3x3 block diagonal of the scaled A: FP64, FP32 and BF16-with-scale copies
+    // in the layouts of As, Af and Ah8/Ah1/Ahs
+    double *Ams = nullptr;
+    float *Amf = nullptr;
+    uint4 *Amh8 = nullptr;
+    uint16_t *Amh1 = nullptr;
+    float *Amhs = nullptr;
     double *w = nullptr;        // [4N] scaling
     double *jac64 = nullptr;    // [9][N] inverses of scaled diagonal blocks of A
     float *jac32 = nullptr;
@@ -188,8 +196,9 @@ template <typename T>
 void spmv_A(Ctx &c, const T *Av, const T *x, T *y);
 template <typename T>
 void spmv_A_ind(Ctx &c, const T *Av, const T *x, T *y, int64_t ystride, const int *kd);
-// A-SpMV on the BF16-with-block-scale copy of the scaled A (see HYEL_PREC_BF16S)
-void spmv_A16_ind(Ctx &c, const float *x, float *y, int64_t ystride, const int *kd);
+// A-SpMV on a BF16-with-block-scale copy (see HYEL_PREC_BF16S)
+void spmv_A16_ind(Ctx &c, const uint4 *h8, const uint16_t *h1, const float *hs, const float *x, float *y,
+                  int64_t ystride, const int *kd);
 void spmv_full64(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,
                  double *y);
 void spmv_full64_ind(Ctx &c, const double *A, const double *B, const double *C, const double *D, const double *x,

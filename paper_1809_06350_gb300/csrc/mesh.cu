@@ -314,6 +314,11 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     M.Ah8 = dalloc_n<uint4>(c, ns);
     M.Ah1 = dalloc_n<uint16_t>(c, ns);
     M.Ahs = dalloc_n<float>(c, ns);
+    M.Ams = dalloc_n<double>(c, 9 * ns);
+    M.Amf = dalloc_n<float>(c, 9 * ns);
+    M.Amh8 = dalloc_n<uint4>(c, ns);
+    M.Amh1 = dalloc_n<uint16_t>(c, ns);
+    M.Amhs = dalloc_n<float>(c, ns);
     M.w = dalloc_n<double>(c, 4 * (size_t)N);
     M.jac64 = dalloc_n<double>(c, 9 * (size_t)N);
     M.jac32 = dalloc_n<float>(c, 9 * (size_t)N);

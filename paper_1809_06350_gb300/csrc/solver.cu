@@ -61,6 +61,7 @@ struct LevelState {
     int status_any;    // OR of flags over solves since reset (1 nan, 2 breakdown, 4 cap reached)
     int yok;           // y = R^-1 g was formed for the finished cycle
     double beta, bnorm, tol, res, inv_scale;
+    double alg_bytes;  // algorithmic bytes of the persistent A-solve iterations since reset
 };
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -339,8 +340,8 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm_givens(T *__restrict__ V
     }
 }
 
-// End of an iteration: when the cycle is done, x += M^-1 V y (KIND 0: 3x3
-// block-Jacobi per node, KIND 1: diagonal) or x += Z y (KIND 2); if the solve
+// End of an iteration: when the cycle is done, x += M^-1 V y (KIND 1:
+// diagonal M^-1) or x += Z y (KIND 2); if the solve
 // continues (restart), V_0 = V Q^T (g_k e_k) and a new cycle starts. Sets the
 // loop condition.
 template <typename T, int KIND>
@@ -368,33 +369,18 @@ __global__ void __launch_bounds__(kThreads) k_cycle_end(T *__restrict__ V, const
             carry = -sn[i] * carry;
         }
         cr[0] = (T)carry;
+        // V_k still holds w = h_{k,k-1} v_k (its scaling is applied lazily)
+        cr[k] = (T)(cs[k - 1] * g[k] * st->inv_scale);
     }
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (usable) {
-        if (KIND == 0) {
-            const int64_t N3 = n / 3;
-            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N3; i += stride) {
-                T u0 = 0, u1 = 0, u2 = 0;
-                for (int l = 0; l < k; l++) {
-                    const T *Vl = V + (int64_t)l * n + 3 * i;
-                    u0 = fma(Vl[0], ys[l], u0);
-                    u1 = fma(Vl[1], ys[l], u1);
-                    u2 = fma(Vl[2], ys[l], u2);
-                }
-#pragma unroll
-                for (int r = 0; r < 3; r++)
-                    x[3 * i + r] += prec[(3 * r) * N3 + i] * u0 + prec[(3 * r + 1) * N3 + i] * u1 +
-                                    prec[(3 * r + 2) * N3 + i] * u2;
-            }
-        } else {
-            const T *B = KIND == 2 ? Z : V;
-            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-                T u = 0;
-                for (int l = 0; l < k; l++) u = fma(B[(int64_t)l * n + i], ys[l], u);
-                if (KIND == 1) u *= prec[i];
-                x[i] += u;
-            }
+        const T *B = KIND == 2 ? Z : V;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            T u = 0;
+            for (int l = 0; l < k; l++) u = fma(B[(int64_t)l * n + i], ys[l], u);
+            if (KIND == 1) u *= prec[i];
+            x[i] += u;
         }
     }
     if (!stop) {
@@ -427,24 +413,6 @@ __global__ void __launch_bounds__(kThreads) k_cycle_end(T *__restrict__ V, const
         }
         *counter = 0u;
     }
-}
-
-// v_k *= inv_scale; z = jac v_k  (block-Jacobi, per node)
-template <typename T>
-__global__ void k_scale_bjac(T *__restrict__ V, T *__restrict__ z, const T *__restrict__ jac, int64_t N,
-                             const LevelState *st) {
-    if (st->done) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    T *v = V + (int64_t)st->k * 3 * N;
-    const T s = (T)st->inv_scale;
-    const T v0 = v[3 * i] * s, v1 = v[3 * i + 1] * s, v2 = v[3 * i + 2] * s;
-    v[3 * i] = v0;
-    v[3 * i + 1] = v1;
-    v[3 * i + 2] = v2;
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-        z[3 * i + r] = jac[(3 * r) * N + i] * v0 + jac[(3 * r + 1) * N + i] * v1 + jac[(3 * r + 2) * N + i] * v2;
 }
 
 // v_k *= inv_scale; z = diag .* v_k (diag == nullptr: scale only, z unused)
@@ -494,6 +462,549 @@ __global__ void __launch_bounds__(kThreads) k_sumsq(const double *__restrict__ r
     if (!last_block(counter)) return;
     sum_partials(partial, 1, 1, out);
     if (threadIdx.x == 0) *counter = 0u;
+}
+
+// ------------------------------------------------------------ persistent A-solve
+//
+// One A-solve (GMRES(m) on A~ = A M^-1, M the 3x3 block diagonal of A, then
+// x = M^-1 V y) as a single cooperative kernel: every block owns the nodes
+// gid, gid + G*B, ... for the whole solve and the phases of an iteration are
+// separated by grid barriers instead of kernel boundaries. Per iteration j:
+//   P1  v_j = s u (s = 1/||u||, applied lazily), w = s A~ u (SELL-32 SpMV,
+//       gathering u), partial dots V_l . w            -> barrier, h1 = sum
+//   P2  w -= V h1, partial dots V_l . w                -> barrier, h2 = sum
+//   P3  w -= V h2, partial ||w||^2                     -> barrier: Givens,
+//       stopping test and, at the end of a cycle, y = R^-1 g and the
+//       restart combination (all by the last block to arrive)
+// The last block to reach a barrier sums the per-block partials in block
+// order before releasing the others, so every result is reproducible bit for
+// bit. Row-local vectors (V, w, x) are only touched by the thread that owns
+// the node; values written by other blocks are read after a barrier.
+// Every barrier wait is bounded (1 s): a block that runs out of time sets the
+// abort word, every block then leaves, and the level state reports flag 8.
+
+constexpr int kPgThreads = 512;
+constexpr unsigned long long kBarrierNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T>
+struct PgArgs {
+    const int32_t *slice_ptr, *row_len, *col;
+    const T *Am;                              // A~ values (nullptr: BF16 records)
+    const uint4 *Am8;
+    const uint16_t *Am1;
+    const float *Ams;
+    const T *jac;                             // [9][N] M^-1
+    int64_t N;                                // nodes (vectors have 3N entries)
+    const T *b;
+    T *x, *V, *U0, *U1;
+    double *H, *cs, *sn, *g, *y, *cr, *tot;   // tot: [m + 3] sums and scalars
+    double *partial;                          // [m + 1][grid]
+    unsigned *bar;                            // barrier words (arrivals, generation, abort)
+    LevelState *st;
+    int m, maxit;
+    double rtol, atol;
+    double it_fixed, it_unit;  // algorithmic bytes per iteration: fixed + (4 (j+1) + 9) unit
+};
+
+// Barrier words, each on its own 128-byte line: arrivals, generation, abort.
+constexpr int kBarArrive = 0, kBarGen = 32, kBarAbort = 64, kBarWords = 96;
+
+// Grid barrier; red() runs in the last block to arrive, before the release.
+// false: a wait ran out of time or another block gave up. The fence after
+// the wait makes the other blocks' writes visible to ordinary loads of every
+// thread of the block once it passes the closing __syncthreads.
+template <typename F>
+__device__ bool grid_step(unsigned *bw, unsigned &gen, F &&red) {
+    __shared__ int s_last, s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&bw[kBarArrive], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        if (threadIdx.x == 0) __threadfence();
+        __syncthreads();
+        red();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_ok = ((volatile unsigned *)bw)[kBarAbort] == 0u;
+            atomicExch(&bw[kBarArrive], 0u);
+            __threadfence();
+            atomicAdd(&bw[kBarGen], 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        volatile unsigned *vb = bw;
+        const unsigned long long t0 = global_ns();
+        int ok = 1;
+        while (vb[kBarGen] == gen) {
+            __nanosleep(64);
+            if (vb[kBarAbort] != 0u || global_ns() - t0 > kBarrierNs) {
+                atomicExch(&bw[kBarAbort], 1u);
+                ok = 0;
+                break;
+            }
+        }
+        s_ok = ok;
+        __threadfence();
+    }
+    __syncthreads();
+    gen += 1;
+    return s_ok != 0;
+}
+
+// Sums over the grid's partials p[k * G + block] (k < nk) in block order,
+// one warp per column, lanes striding over the blocks (coalesced).
+__device__ __forceinline__ void pg_sum(const double *p, int nk, double *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int G = gridDim.x;
+    for (int k = warp; k < nk; k += nw) {
+        double s = 0.0;
+        for (int b = lane; b < G; b += 32) s += p[(int64_t)k * G + b];
+        s = warp_sum_d(s);
+        if (lane == 0) out[k] = s;
+    }
+}
+
+// Nodes owned by the calling thread: block b holds the contiguous 32-row
+// slices [S b / G, S (b+1) / G) (S slices, G blocks), its warps take them in
+// turn and lane t the row 32 s + t. Every phase uses this map, so row-local
+// data never cross threads, and with G a multiple of the SM count every SM
+// gets the same number of slices to within one per block.
+#define PG_FOR_OWN_NODES(N, i)                                                                   \
+    for (int64_t pg_s = ((((N) + 31) >> 5) * blockIdx.x) / gridDim.x + (threadIdx.x >> 5),       \
+                 pg_e = ((((N) + 31) >> 5) * (blockIdx.x + 1)) / gridDim.x;                      \
+         pg_s < pg_e; pg_s += (blockDim.x >> 5))                                                 \
+        for (int64_t i = pg_s * 32 + (threadIdx.x & 31); i < (N); i = (N))
+
+// Warp sums of eight values per lane by reduce-scatter (9 adds, 9 shuffles):
+// afterwards lane l holds, in v[0], the warp total of value (l >> 2) & 7.
+template <typename T>
+__device__ __forceinline__ void warp_reduce8(T v[8]) {
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const T keep = h16 ? v[4 + k] : v[k], send = h16 ? v[k] : v[4 + k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const T keep = h8 ? v[2 + k] : v[k], send = h8 ? v[k] : v[2 + k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const T keep = h4 ? v[1] : v[0], send = h4 ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Block sum of one value per thread: warp sums in T, then the warps' sums in
+// double (thread 0 gets the result).
+template <typename T>
+__device__ __forceinline__ double pg_block_sum(T v, double *red) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q];
+    __syncthreads();
+    return t;
+}
+
+// Partial dots V_l . w (l < nk) of this block's nodes into partial[l][block];
+// sums within a warp in T, across the block's warps in double.
+template <typename T>
+__device__ void pg_dots(const T *V, const T *w, int64_t N, int nk, double *partial) {
+    __shared__ double red[kPgThreads / 32][KC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n = 3 * N;
+    for (int k0 = 0; k0 < nk; k0 += KC) {
+        const int kc = min(KC, nk - k0);
+        T acc[KC];
+#pragma unroll
+        for (int c = 0; c < KC; c++) acc[c] = 0;
+        PG_FOR_OWN_NODES(N, i) {
+            const T w0 = w[3 * i], w1 = w[3 * i + 1], w2 = w[3 * i + 2];
+#pragma unroll
+            for (int c = 0; c < KC; c++)
+                if (c < kc) {
+                    const T *v = V + (int64_t)(k0 + c) * n + 3 * i;
+                    acc[c] = fma(v[0], w0, fma(v[1], w1, fma(v[2], w2, acc[c])));
+                }
+        }
+        if (kc == 1) {
+            const T s = warp_sum(acc[0]);
+            if (lane == 0) red[warp][0] = (double)s;
+        } else {
+            warp_reduce8<T>(acc);
+            if ((lane & 3) == 0) red[warp][lane >> 2] = (double)acc[0];
+        }
+        __syncthreads();
+        if (threadIdx.x < kc) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < kPgThreads / 32; q++) s += red[q][threadIdx.x];
+            partial[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// w -= V h (h in shared memory, l < nk) on this block's nodes; returns sum w^2
+// (accumulated in T per thread)
+template <typename T>
+__device__ T pg_axpy(const T *V, T *w, int64_t N, int nk, const T *h) {
+    const int64_t n = 3 * N;
+    T ss = 0;
+    PG_FOR_OWN_NODES(N, i) {
+        T w0 = w[3 * i], w1 = w[3 * i + 1], w2 = w[3 * i + 2];
+        for (int l = 0; l < nk; l++) {
+            const T *v = V + (int64_t)l * n + 3 * i;
+            const T hl = h[l];
+            w0 = fma(-v[0], hl, w0);
+            w1 = fma(-v[1], hl, w1);
+            w2 = fma(-v[2], hl, w2);
+        }
+        w[3 * i] = w0;
+        w[3 * i + 1] = w1;
+        w[3 * i + 2] = w2;
+        ss = fma(w0, w0, fma(w1, w1, fma(w2, w2, ss)));
+    }
+    return ss;
+}
+
+template <typename T, bool H16>
+__device__ __forceinline__ void pg_row(const PgArgs<T> &a, int64_t i, const T *u, T &y0, T &y1, T &y2) {
+    const int t = (int)(i & 31);
+    const int64_t b0 = a.slice_ptr[i >> 5];
+    const int len = a.row_len[i];
+    T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 4
+    for (int jb = 0; jb < len; jb++) {
+        const int64_t q = (b0 + jb) * 32 + t;
+        const int64_t c = __ldg(a.col + q);
+        const T x0 = u[3 * c], x1 = u[3 * c + 1], x2 = u[3 * c + 2];
+        if constexpr (H16) {
+            const uint4 w = __ldg(a.Am8 + q);
+            const unsigned e8 = __ldg(a.Am1 + q);
+            const float s = __ldg(a.Ams + q);
+            float t0 = __uint_as_float(w.x << 16) * x0;
+            t0 = fmaf(__uint_as_float(w.x & 0xffff0000u), x1, t0);
+            t0 = fmaf(__uint_as_float(w.y << 16), x2, t0);
+            float t1 = __uint_as_float(w.y & 0xffff0000u) * x0;
+            t1 = fmaf(__uint_as_float(w.z << 16), x1, t1);
+            t1 = fmaf(__uint_as_float(w.z & 0xffff0000u), x2, t1);
+            float t2 = __uint_as_float(w.w << 16) * x0;
+            t2 = fmaf(__uint_as_float(w.w & 0xffff0000u), x1, t2);
+            t2 = fmaf(__uint_as_float(e8 << 16), x2, t2);
+            a0 = fmaf(s, t0, a0);
+            a1 = fmaf(s, t1, a1);
+            a2 = fmaf(s, t2, a2);
+        } else {
+            const T *Ab = a.Am + (q >> 5) * 288 + t;
+            a0 = fma(__ldg(Ab + 0), x0, a0);
+            a0 = fma(__ldg(Ab + 32), x1, a0);
+            a0 = fma(__ldg(Ab + 64), x2, a0);
+            a1 = fma(__ldg(Ab + 96), x0, a1);
+            a1 = fma(__ldg(Ab + 128), x1, a1);
+            a1 = fma(__ldg(Ab + 160), x2, a1);
+            a2 = fma(__ldg(Ab + 192), x0, a2);
+            a2 = fma(__ldg(Ab + 224), x1, a2);
+            a2 = fma(__ldg(Ab + 256), x2, a2);
+        }
+    }
+    y0 = a0;
+    y1 = a1;
+    y2 = a2;
+}
+
+template <typename T, bool H16>
+__global__ void __launch_bounds__(kPgThreads) k_gmres_a(PgArgs<T> a) {
+    __shared__ T hs[kMaxK + 1];
+    __shared__ double s_sc[2];
+    const int64_t N = a.N, n = 3 * N;
+    const int m = a.m;
+    LevelState *st = a.st;
+    volatile LevelState *vst = st;
+    unsigned gen = 0u;  // the barrier words are cleared before every launch
+
+    auto abort_out = [&]() {
+        if (threadIdx.x == 0) {
+            atomicOr(&st->flags, 8);
+            atomicOr(&st->status_any, 8);
+            st->stop = 1;
+        }
+    };
+
+    // ---- start: x = 0, beta = ||b||
+    T ss = 0;
+    PG_FOR_OWN_NODES(N, i)
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            const T v = a.b[3 * i + r];
+            a.x[3 * i + r] = 0;
+            ss = fma(v, v, ss);
+        }
+    {
+        __shared__ double red1[kPgThreads / 32];
+        const double tb = pg_block_sum<T>(ss, red1);
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = tb;
+    }
+    bool ok = grid_step(a.bar, gen, [&]() {
+        __shared__ double tot0;
+        pg_sum(a.partial, 1, &tot0);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double beta = sqrt(tot0);
+            st->k = 0;
+            st->total = 0;
+            st->cycles = 0;
+            st->maxit = a.maxit;
+            st->m = m;
+            st->beta = beta;
+            st->bnorm = beta;
+            st->tol = fmax(a.rtol * beta, a.atol);
+            st->res = beta;
+            st->inv_scale = beta > 0.0 ? 1.0 / beta : 0.0;
+            const int nan = isfinite(beta) ? 0 : 1;
+            st->flags = nan;
+            st->converged = (!nan && beta <= st->tol) ? 1 : 0;
+            st->stop = (st->converged || nan) ? 1 : 0;
+            st->done = st->stop;
+            st->yok = 0;
+            if (st->stop) {
+                st->solves += 1;
+                st->status_any |= nan;
+                st->stop = 2;
+            }
+            a.g[0] = beta;
+            for (int l = 1; l <= m; l++) a.g[l] = 0.0;
+            a.tot[m + 1] = st->inv_scale;
+        }
+    });
+    if (!ok) return abort_out();
+    if (vst->stop) return;
+
+    const T *uin = a.b;
+    T *uout = a.U0;
+    T s = (T)a.tot[m + 1];
+    int j = 0;
+    for (;;) {
+        // ---- P1: v_j = s u; w = s A~ u; dots with V_0..V_j
+        T *Vj = a.V + (int64_t)j * n;
+        PG_FOR_OWN_NODES(N, i) {
+            Vj[3 * i] = uin[3 * i] * s;
+            Vj[3 * i + 1] = uin[3 * i + 1] * s;
+            Vj[3 * i + 2] = uin[3 * i + 2] * s;
+            T y0, y1, y2;
+            pg_row<T, H16>(a, i, uin, y0, y1, y2);
+            uout[3 * i] = y0 * s;
+            uout[3 * i + 1] = y1 * s;
+            uout[3 * i + 2] = y2 * s;
+        }
+        pg_dots<T>(a.V, uout, N, j + 1, a.partial);
+        ok = grid_step(a.bar, gen, [&]() {
+            pg_sum(a.partial, j + 1, a.tot);
+            __syncthreads();
+            for (int l = threadIdx.x; l <= j; l += blockDim.x) a.H[(int64_t)j * (m + 1) + l] = a.tot[l];
+        });
+        if (!ok) return abort_out();
+        // ---- P2: w -= V h1; dots again (second Gram-Schmidt pass)
+        for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = (T)a.tot[l];
+        __syncthreads();
+        pg_axpy<T>(a.V, uout, N, j + 1, hs);
+        pg_dots<T>(a.V, uout, N, j + 1, a.partial);
+        ok = grid_step(a.bar, gen, [&]() {
+            pg_sum(a.partial, j + 1, a.tot);
+            __syncthreads();
+            for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+                volatile double *Hc = a.H + (int64_t)j * (m + 1);
+                Hc[l] = Hc[l] + a.tot[l];
+            }
+        });
+        if (!ok) return abort_out();
+        // ---- P3: w -= V h2; ||w||
+        for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = (T)a.tot[l];
+        __syncthreads();
+        {
+            __shared__ double red1[kPgThreads / 32];
+            const double tb = pg_block_sum<T>(pg_axpy<T>(a.V, uout, N, j + 1, hs), red1);
+            if (threadIdx.x == 0) a.partial[blockIdx.x] = tb;
+        }
+        ok = grid_step(a.bar, gen, [&]() {
+            __shared__ double tot0;
+            __shared__ int s_yok;
+            pg_sum(a.partial, 1, &tot0);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                volatile double *Hc = a.H + (int64_t)j * (m + 1);
+                volatile double *cs = a.cs, *sn = a.sn, *g = a.g;
+                const double hn = sqrt(tot0);
+                for (int l = 0; l < j; l++) {
+                    const double a0 = Hc[l], a1 = Hc[l + 1];
+                    Hc[l] = cs[l] * a0 + sn[l] * a1;
+                    Hc[l + 1] = -sn[l] * a0 + cs[l] * a1;
+                }
+                const double al = Hc[j];
+                double c, s2, r;
+                if (hn == 0.0) {
+                    c = 1.0;
+                    s2 = 0.0;
+                    r = al;
+                } else {
+                    r = sqrt(al * al + hn * hn);
+                    c = al / r;
+                    s2 = hn / r;
+                }
+                cs[j] = c;
+                sn[j] = s2;
+                Hc[j] = r;
+                Hc[j + 1] = 0.0;
+                const double gj = g[j];
+                g[j] = c * gj;
+                g[j + 1] = -s2 * gj;
+                const double res = fabs(g[j + 1]);
+                st->k = j + 1;
+                st->total += 1;
+                st->res = res;
+                st->inv_scale = hn > 0.0 ? 1.0 / hn : 0.0;
+                st->alg_bytes += a.it_fixed + (4.0 * (j + 1) + 9.0) * a.it_unit;
+                int done = 0, stop = 0;
+                if (!isfinite(res) || !isfinite(hn)) {
+                    st->flags |= 1;
+                    done = stop = 1;
+                } else if (r == 0.0) {
+                    st->flags |= 2;
+                    done = stop = 1;
+                } else if (res <= st->tol) {
+                    st->converged = 1;
+                    done = stop = 1;
+                } else if (hn == 0.0) {
+                    st->flags |= 2;
+                    done = stop = 1;
+                } else if (st->total >= st->maxit) {
+                    done = stop = 1;
+                } else if (j + 1 == m) {
+                    done = 1;
+                }
+                st->done = done;
+                st->stop = stop;
+                s_yok = done && isfinite(res) && isfinite(hn) && r != 0.0;
+                st->yok = s_yok;
+                a.tot[m + 1] = st->inv_scale;  // scale of the next basis vector
+                a.tot[m + 2] = st->inv_scale;  // 1 / h_{j+1,j}
+            }
+            __syncthreads();
+            if (s_yok && threadIdx.x < 32) {  // y = R^-1 g over the k = j+1 columns (warp 0)
+                const int k = j + 1, lane = threadIdx.x;
+                volatile double *H = a.H, *yv = a.y, *g = a.g;
+                for (int i = k - 1; i >= 0; i--) {
+                    double sacc = 0.0;
+                    for (int l = i + 1 + lane; l < k; l += 32) sacc += H[(int64_t)l * (m + 1) + i] * yv[l];
+                    sacc = warp_sum_d(sacc);
+                    if (lane == 0) yv[i] = (g[i] - sacc) / H[(int64_t)i * (m + 1) + i];
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && st->done) {
+                if (st->stop) {
+                    st->its += st->total;
+                    st->solves += 1;
+                    st->status_any |= st->flags | ((!st->converged && !st->flags) ? 4 : 0);
+                    st->stop = 2;
+                } else {
+                    // restart: c = G_0^T ... G_{k-1}^T (g_k e_k); new residual norm |g_k|
+                    const int k = j + 1;
+                    volatile double *cs = a.cs, *sn = a.sn, *g = a.g, *cr = a.cr;
+                    double carry = g[k];
+                    for (int i = k - 1; i >= 0; i--) {
+                        cr[i + 1] = cs[i] * carry;
+                        carry = -sn[i] * carry;
+                    }
+                    cr[0] = carry;
+                    const double beta = fabs(g[k]);
+                    st->k = 0;
+                    st->done = 0;
+                    st->cycles += 1;
+                    st->beta = beta;
+                    st->res = beta;
+                    st->inv_scale = beta > 0.0 ? 1.0 / beta : 0.0;
+                    a.tot[m + 1] = st->inv_scale;
+                    g[0] = beta;
+                    for (int l = 1; l <= m; l++) g[l] = 0.0;
+                }
+            }
+        });
+        if (!ok) return abort_out();
+        if (threadIdx.x == 0) {
+            s_sc[0] = a.tot[m + 1];
+            s_sc[1] = a.tot[m + 2];
+        }
+        __syncthreads();
+        const int done = vst->done, stop = vst->stop, yok = vst->yok;
+        if (!done) {
+            // next iteration: u = w, scaled lazily by 1 / h_{j+1,j}
+            s = (T)s_sc[0];
+            uin = uout;
+            uout = (uout == a.U0) ? a.U1 : a.U0;
+            j += 1;
+            continue;
+        }
+        const int k = j + 1;
+        if (yok) {  // x += M^-1 V y
+            for (int l = threadIdx.x; l < k; l += blockDim.x) hs[l] = (T)a.y[l];
+            __syncthreads();
+            PG_FOR_OWN_NODES(N, i) {
+                T u0 = 0, u1 = 0, u2 = 0;
+                for (int l = 0; l < k; l++) {
+                    const T *v = a.V + (int64_t)l * n + 3 * i;
+                    u0 = fma(v[0], hs[l], u0);
+                    u1 = fma(v[1], hs[l], u1);
+                    u2 = fma(v[2], hs[l], u2);
+                }
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+                    a.x[3 * i + r] += __ldg(a.jac + (3 * r) * N + i) * u0 + __ldg(a.jac + (3 * r + 1) * N + i) * u1 +
+                                      __ldg(a.jac + (3 * r + 2) * N + i) * u2;
+            }
+            __syncthreads();
+        }
+        if (stop) return;
+        // restart vector r = sum_{l<k} c_l V_l + c_k (w / h_{k,k-1}), unnormalised
+        for (int l = threadIdx.x; l <= k; l += blockDim.x) hs[l] = (T)a.cr[l];
+        __syncthreads();
+        const T hinv = (T)s_sc[1];
+        T *unew = (uout == a.U0) ? a.U1 : a.U0;
+        PG_FOR_OWN_NODES(N, i) {
+            T r0 = uout[3 * i] * hinv * hs[k], r1 = uout[3 * i + 1] * hinv * hs[k], r2 = uout[3 * i + 2] * hinv * hs[k];
+            for (int l = 0; l < k; l++) {
+                const T *v = a.V + (int64_t)l * n + 3 * i;
+                r0 = fma(v[0], hs[l], r0);
+                r1 = fma(v[1], hs[l], r1);
+                r2 = fma(v[2], hs[l], r2);
+            }
+            unew[3 * i] = r0;
+            unew[3 * i + 1] = r1;
+            unew[3 * i + 2] = r2;
+        }
+        ok = grid_step(a.bar, gen, [&]() {});
+        if (!ok) return abort_out();
+        s = (T)a.tot[m + 1];
+        uin = unew;
+        uout = (unew == a.U0) ? a.U1 : a.U0;
+        j = 0;
+    }
 }
 
 // ------------------------------------------------------------ recording
@@ -590,6 +1101,12 @@ struct Level {
     double *partial = nullptr;
     unsigned *counter = nullptr;
     int grid = 0;
+    // persistent A-solve (kind 0): second work vector, reduced sums, restart
+    // coefficients, per-block partials, barrier words, cooperative grid sizes
+    T *z2 = nullptr;
+    double *tot = nullptr, *cr = nullptr, *pg_partial = nullptr;
+    unsigned *bar = nullptr;
+    int pg_grid = 0, pg_grid16 = 0;
 };
 
 }  // namespace
@@ -666,6 +1183,25 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
     L.partial = (double *)walloc(c, w, sizeof(double) * (size_t)L.grid * (m + 1));
     L.counter = (unsigned *)walloc(c, w, sizeof(unsigned) * 4);
     HYEL_CK(cudaMemsetAsync(L.counter, 0, sizeof(unsigned) * 4, c.stream));
+    if (kind == 0) {
+        // the persistent A-solve: a cooperative grid of all co-resident blocks
+        // (at most one thread per node)
+        L.z2 = (T *)walloc(c, w, sizeof(T) * (size_t)n);
+        L.tot = (double *)walloc(c, w, sizeof(double) * (m + 3));
+        L.cr = (double *)walloc(c, w, sizeof(double) * (m + 1));
+        L.bar = (unsigned *)walloc(c, w, sizeof(unsigned) * kBarWords);
+        const int64_t need = std::max<int64_t>(1, (n / 3 + 31) / 32);  // no block without a slice
+        int occ = 0, occ16 = 0;
+        HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_a<T, false>, kPgThreads, 0));
+        occ16 = occ;
+        if constexpr (std::is_same<T, float>::value)
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_a<float, true>, kPgThreads, 0));
+        if (occ < 1 || occ16 < 1) fail(HYEL_ECUDA, "persistent A-solve kernel does not fit on an SM");
+        L.pg_grid = (int)std::min<int64_t>((int64_t)occ * c.num_sms, need);
+        L.pg_grid16 = (int)std::min<int64_t>((int64_t)occ16 * c.num_sms, need);
+        L.pg_partial =
+            (double *)walloc(c, w, sizeof(double) * (size_t)std::max(L.pg_grid, L.pg_grid16) * (m + 1));
+    }
 }
 
 Workspace &workspace(Ctx &c, const hyel_solver_params &p) {
@@ -752,19 +1288,16 @@ void gm_solve(Rec &R, Level<T> &L, LevelState *st, const hyel_krylov_level &P, c
               const std::function<void()> &prec_flex, const std::function<void()> &op) {
     Ctx &c = *R.c;
     const int m = std::min(P.restart, L.m);
-    // host-driven mode may run several cheap A-level iterations between checks
-    // (the kernels of an iteration after the stop do nothing); levels whose
-    // operator is itself a solve are checked every iteration
+    // the operator of both looped levels is itself a solve: the host-driven
+    // mode checks them every iteration
     R.loop(
-        st, KIND == 0 ? R.check_every : 1,
+        st, 1,
         [&](cudaGraphConditionalHandle h) {
             LAUNCH(k_init<T><<<L.grid, kThreads, 0, c.stream>>>(b, L.V, x, L.n, L.partial, L.counter, st, L.g, m,
                                                                P.rtol, P.atol, P.maxit, h));
         },
         [&](cudaGraphConditionalHandle h) {
-            if (KIND == 0)
-                LAUNCH(k_scale_bjac<T><<<blocks_for(L.n / 3, 128), 128, 0, c.stream>>>(L.V, L.z, prec, L.n / 3, st));
-            else if (KIND == 1)
+            if (KIND == 1)
                 LAUNCH(k_scale_diag<T><<<blocks_for(L.n, 256), 256, 0, c.stream>>>(L.V, L.z, prec, L.n, st));
             else {
                 LAUNCH(k_scale_diag<T><<<blocks_for(L.n, 256), 256, 0, c.stream>>>(L.V, (T *)nullptr, (const T *)nullptr,
@@ -782,20 +1315,79 @@ void gm_solve(Rec &R, Level<T> &L, LevelState *st, const hyel_krylov_level &P, c
         });
 }
 
-// A-solve x = A^-1 b
+// A-solve x = A^-1 b: one cooperative launch of the persistent GMRES kernel
+// (its barrier words cleared just before), in host-driven mode and in the graph
 template <typename T>
 void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, const T *b, T *x) {
     Ctx &c = *R.c;
     Level<T> &L = Sys<T>::la(w);
-    gm_solve<T, 0>(R, L, st, P, b, x, Sys<T>::jac(c), nullptr, [&]() {
-        if constexpr (std::is_same<T, float>::value) {
-            if (w.prec == HYEL_PREC_BF16S) {
-                spmv_A16_ind(c, L.z, L.V, L.n, &st->k);
-                return;
-            }
+    const DeviceMesh &msh = c.mesh;
+    const DeviceMatrix &M = c.mat;
+    PgArgs<T> a;
+    a.slice_ptr = msh.slice_ptr;
+    a.row_len = msh.row_len;
+    a.col = msh.col;
+    a.Am = nullptr;
+    a.Am8 = M.Amh8;
+    a.Am1 = M.Amh1;
+    a.Ams = M.Amhs;
+    a.jac = Sys<T>::jac(c);
+    a.N = msh.N;
+    a.b = b;
+    a.x = x;
+    a.V = L.V;
+    a.U0 = L.z;
+    a.U1 = L.z2;
+    a.H = L.H;
+    a.cs = L.cs;
+    a.sn = L.sn;
+    a.g = L.g;
+    a.y = L.y;
+    a.cr = L.cr;
+    a.tot = L.tot;
+    a.partial = L.pg_partial;
+    a.bar = L.bar;
+    a.st = st;
+    a.m = std::min(P.restart, L.m);
+    a.maxit = P.maxit;
+    a.rtol = P.rtol;
+    a.atol = P.atol;
+    bool h16 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        h16 = w.prec == HYEL_PREC_BF16S;
+        a.Am = h16 ? nullptr : M.Amf;
+    } else {
+        a.Am = M.Ams;
+    }
+    // algorithmic bytes of one iteration (matrix once, each vector pass once):
+    // A~ values + column indices + row metadata, and 4 (j+1) + 9 passes over
+    // 3N-vectors (u gather, v_j, w, two dot passes over V_0..V_j and w, two
+    // axpy passes over V_0..V_j reading and writing w)
+    a.it_fixed = (double)msh.nnzb * ((h16 ? 22.0 : 9.0 * sizeof(T)) + 4.0) + 4.0 * (msh.N + 1);
+    a.it_unit = 3.0 * msh.N * sizeof(T);
+    HYEL_CK(cudaMemsetAsync(L.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(h16 ? L.pg_grid16 : L.pg_grid));
+    cfg.blockDim = dim3(kPgThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaEvent_t ev;
+    prof_begin(c, HYEL_K_GMRES_A, &ev);
+    bool launched = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (h16) {
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_a<float, true>, a));
+            launched = true;
         }
-        spmv_A_ind<T>(c, Sys<T>::A(c), L.z, L.V, L.n, &st->k);
-    });
+    }
+    if (!launched) HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_a<T, false>, a));
+    count_launch();
+    prof_end(c, HYEL_K_GMRES_A, ev, 0.0);  // bytes are added from the level states after the solve
 }
 
 // Algorithm 2: y = D x - C A^-1 (B x), y indexed by the S-level state
@@ -968,6 +1560,8 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
         for (int64_t q = 0; q < k; q++) count_launch();
     }
     const LevelState *hs = w.h_states;
+    if (c.prof.on && !p.graph)
+        c.prof.bytes[HYEL_K_GMRES_A] += hs[ST_A1].alg_bytes + hs[ST_A2].alg_bytes + hs[ST_INNER].alg_bytes;
     const double bn = hs[ST_OUTER].bnorm;
     const double rel = bn > 0 ? std::sqrt(c.h_red[8]) / bn : std::sqrt(c.h_red[8]);
     int st = HYEL_OK;
@@ -978,6 +1572,8 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
         if (hs[q].status_any & 1) st = HYEL_ENAN;
     }
     if (!std::isfinite(rel)) st = HYEL_ENAN;
+    const bool barrier_timeout = ((hs[ST_A1].status_any | hs[ST_A2].status_any | hs[ST_INNER].status_any) & 8) != 0;
+    if (barrier_timeout) st = HYEL_ECUDA;
     if (out) {
         out->status = st;
         out->outer_its = (int32_t)hs[ST_OUTER].its;
@@ -992,7 +1588,8 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
         out->ms_solve = 1e3 * seconds_since(t1);
     }
     if (st != HYEL_OK) {
-        const char *what = st == HYEL_ENOCONV   ? "outer FGMRES reached its iteration cap"
+        const char *what = barrier_timeout      ? "a grid barrier of the persistent A-solve timed out"
+                           : st == HYEL_ENOCONV ? "outer FGMRES reached its iteration cap"
                            : st == HYEL_ENAN    ? "NaN or Inf in the solve"
                            : st == HYEL_EBREAKDOWN ? "GMRES breakdown without convergence"
                                                    : "solve failed";
@@ -1024,7 +1621,9 @@ void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y
     HYEL_CK(cudaStreamSynchronize(c.stream));
     if (out) {
         *out = hyel_solve_stats{};
-        out->status = (w.h_states[ST_INNER].status_any & 1) ? HYEL_ENAN : HYEL_OK;
+        out->status = (w.h_states[ST_INNER].status_any & 8)   ? HYEL_ECUDA
+                      : (w.h_states[ST_INNER].status_any & 1) ? HYEL_ENAN
+                                                               : HYEL_OK;
         out->inner_its = w.h_states[ST_INNER].its;
         out->inner_solves = w.h_states[ST_INNER].solves;
     }

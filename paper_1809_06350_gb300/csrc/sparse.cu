@@ -25,6 +25,11 @@ struct ScaleArgs {
     uint4 *Ah8;
     uint16_t *Ah1;
     float *Ahs;
+    double *Ams;
+    float *Amf;
+    uint4 *Amh8;
+    uint16_t *Amh1;
+    float *Amhs;
     double *w;  // [4N]
     double *jac64;
     float *jac32;
@@ -47,6 +52,23 @@ __global__ void k_scale_diag(ScaleArgs a) {
     a.w[3 * a.N + i] = d >= 1e-15 ? 1.0 / sqrt(d) : 1.0;
 }
 
+// BF16 copy of one 3x3 block with one FP32 scale: s = float(max |v|),
+// e_k = bf16_rn(float(v_k) / s); all zero for a zero block
+__device__ __forceinline__ void quant_block(const double v[9], int64_t q, uint4 *h8, uint16_t *h1, float *hs) {
+    double amax = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; k++) amax = fmax(amax, fabs(v[k]));
+    const float sc = (float)amax;
+    unsigned short h[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++)
+        h[k] = sc > 0.0f ? __bfloat16_as_ushort(__float2bfloat16_rn(__fdiv_rn((float)v[k], sc))) : (unsigned short)0;
+    h8[q] = make_uint4(h[0] | ((unsigned)h[1] << 16), h[2] | ((unsigned)h[3] << 16), h[4] | ((unsigned)h[5] << 16),
+                       h[6] | ((unsigned)h[7] << 16));
+    h1[q] = h[8];
+    hs[q] = sc;
+}
+
 __global__ void k_scale_values(ScaleArgs a) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a.nslots) return;
@@ -65,7 +87,7 @@ __global__ void k_scale_values(ScaleArgs a) {
         wpr = a.w[3 * a.N + r];
         wpc = a.w[3 * a.N + c];
     }
-    double v[9], amax = 0.0;
+    double v[9];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -74,18 +96,8 @@ __global__ void k_scale_values(ScaleArgs a) {
             v[3 * i + j] = a.A[o] * wr[i] * wc[j];
             a.As[o] = v[3 * i + j];
             a.Af[o] = (float)v[3 * i + j];
-            amax = fmax(amax, fabs(v[3 * i + j]));
         }
-    // BF16 copy with one FP32 scale per block: e_k = bf16_rn(float(v_k) / s)
-    const float sc = (float)amax;
-    unsigned short h[9];
-#pragma unroll
-    for (int k = 0; k < 9; k++)
-        h[k] = sc > 0.0f ? __bfloat16_as_ushort(__float2bfloat16_rn(__fdiv_rn((float)v[k], sc))) : (unsigned short)0;
-    a.Ah8[q] = make_uint4(h[0] | ((unsigned)h[1] << 16), h[2] | ((unsigned)h[3] << 16), h[4] | ((unsigned)h[5] << 16),
-                          h[6] | ((unsigned)h[7] << 16));
-    a.Ah1[q] = h[8];
-    a.Ahs[q] = sc;
+    quant_block(v, q, a.Ah8, a.Ah1, a.Ahs);
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         const int64_t o = (b * 3 + i) * 32 + t;
@@ -141,6 +153,43 @@ __global__ void k_jacobi(ScaleArgs a) {
             a.jac64[(3 * r + s) * a.N + i] = v;
             a.jac32[(3 * r + s) * a.N + i] = (float)v;
         }
+}
+
+// A~ = A M^-1 block by block: A~_(r,c) = A_(r,c) M_c^-1, M_c^-1 the inverse of
+// the scaled diagonal block of node c (right block-Jacobi preconditioning
+// folded into the operator of the A-solves)
+__global__ void k_fold_jacobi(ScaleArgs a) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.nslots) return;
+    const int64_t b = q >> 5;
+    const int t = (int)(q & 31);
+    const int s = a.col_slice[b];
+    const int64_t r = (int64_t)s * 32 + t;
+    double v[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) v[k] = 0.0;
+    if (r < a.N && b - a.slice_ptr[s] < a.row_len[r]) {
+        const int64_t c = a.col[q];
+        double m[3][3], ji[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                m[i][j] = a.As[(b * 9 + 3 * i + j) * 32 + t];
+                ji[i][j] = a.jac64[(3 * i + j) * a.N + c];
+            }
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) v[3 * i + j] = m[i][0] * ji[0][j] + m[i][1] * ji[1][j] + m[i][2] * ji[2][j];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const int64_t o = (b * 9 + k) * 32 + t;
+        a.Ams[o] = v[k];
+        a.Amf[o] = (float)v[k];
+    }
+    quant_block(v, q, a.Amh8, a.Amh1, a.Amhs);
 }
 
 // diag(S^)_i = D_ii - sum_c sum_s C_(i,c)[s] B_(c,i)[s] / A_(c,c)[s][s]  (scaled system)
@@ -442,6 +491,11 @@ ScaleArgs scale_args(Ctx &c) {
     a.Ah8 = M.Ah8;
     a.Ah1 = M.Ah1;
     a.Ahs = M.Ahs;
+    a.Ams = M.Ams;
+    a.Amf = M.Amf;
+    a.Amh8 = M.Amh8;
+    a.Amh1 = M.Amh1;
+    a.Amhs = M.Amhs;
     a.w = M.w;
     a.jac64 = M.jac64;
     a.jac32 = M.jac32;
@@ -464,6 +518,7 @@ void solve_setup(Ctx &c) {
     (k_scale_diag<<<blocks_for(N, 256), 256, 0, c.stream>>>(a), ::hyel::count_launch());
     (k_scale_values<<<blocks_for(c.mesh.nslots, 256), 256, 0, c.stream>>>(a), ::hyel::count_launch());
     (k_jacobi<<<blocks_for(N, 256), 256, 0, c.stream>>>(a), ::hyel::count_launch());
+    (k_fold_jacobi<<<blocks_for(c.mesh.nslots, 256), 256, 0, c.stream>>>(a), ::hyel::count_launch());
     (k_schur_hat<<<blocks_for(N, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
     HYEL_CK(cudaGetLastError());
     HYEL_CK(cudaMemcpyAsync(c.h_err, c.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
@@ -507,13 +562,13 @@ template void spmv_A<float>(Ctx &, const float *, const float *, float *);
 template void spmv_A_ind<double>(Ctx &, const double *, const double *, double *, int64_t, const int *);
 template void spmv_A_ind<float>(Ctx &, const float *, const float *, float *, int64_t, const int *);
 
-void spmv_A16_ind(Ctx &c, const float *x, float *y, int64_t ystride, const int *kd) {
+void spmv_A16_ind(Ctx &c, const uint4 *h8, const uint16_t *h1, const float *hs, const float *x, float *y,
+                  int64_t ystride, const int *kd) {
     const DeviceMesh &m = c.mesh;
-    const DeviceMatrix &M = c.mat;
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_SPMV_A16, &ev);
-    (k_spmv_A16<<<blocks_for(m.N, 32), 32, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, M.Ah8, M.Ah1, M.Ahs, x, y,
-                                                            m.N, kd, ystride), ::hyel::count_launch());
+    (k_spmv_A16<<<blocks_for(m.N, 32), 32, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, h8, h1, hs, x, y, m.N, kd,
+                                                            ystride), ::hyel::count_launch());
     // algorithmic bytes: 9 BF16 values + 1 FP32 scale + 1 column index per block, x and y once
     prof_end(c, HYEL_K_SPMV_A16, ev, (double)m.nnzb * (18.0 + 4.0 + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * 4);
 }

@@ -20,11 +20,12 @@ HYEL_EINVAL, HYEL_ECUDA, HYEL_ENOMEM, HYEL_ENOCONV = -1, -2, -3, -4
 HYEL_EBREAKDOWN, HYEL_ENAN, HYEL_EINVERTED, HYEL_ESINGULAR, HYEL_ESTATE = -5, -6, -7, -8, -9
 HYEL_VOL_GIBBS, HYEL_VOL_INCOMPRESSIBLE = 0, 1
 HYEL_PREC_FP64, HYEL_PREC_FP32, HYEL_PREC_BF16S = 0, 1, 2
-HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D = 0, 1, 2, 3, 4
+HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D, HYEL_OP_AM = 0, 1, 2, 3, 4, 5
 HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32, HYEL_MAT_TRANSPOSED, HYEL_MAT_SCALED_BF16S = 0, 1, 2, 3, 4
-HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER, HYEL_K_SPMV_A16 = range(6)
-HYEL_K_NCLASSES = 6
-K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather", "spmv_A16"]
+(HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER, HYEL_K_SPMV_A16,
+ HYEL_K_GMRES_A) = range(7)
+HYEL_K_NCLASSES = 7
+K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather", "spmv_A16", "gmres_A"]
 
 # every symbol include/hyel.h declares
 EXPORTS = [

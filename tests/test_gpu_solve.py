@@ -9,6 +9,9 @@
 * the nested FGMRES solve vs the oracle's direct solve: relative error <= 1e-9
   at outer tolerance 1e-13, in FP64, with FP32 preconditioner levels and with
   the BF16 A in the FP32 levels;
+* the same with GMRES restarts forced at every level;
+* A M^-1 (block-Jacobi folded into the operator of the A-solves) in FP64,
+  FP32 and BF16 with block scale;
 * tight intermediate/inner tolerances give convergence in <= 2 outer
   iterations (exact LDU preconditioner, §4.4);
 * status codes: iteration cap, NaN right-hand side.
@@ -126,6 +129,68 @@ def test_bf16s_spmv(cube):
     dev_exact = np.abs(yg - As @ x)
     assert np.all(dev_exact <= (2.0 ** -9 + 4e-6) * bound)
     assert np.max(dev_exact / bound) > 2.0 ** -14
+
+
+def _block_jacobi_fold(As, N):
+    """A M^-1 with M the 3x3 block diagonal of A (oracle's scaled A)."""
+    Ad = As.toarray() if hasattr(As, "toarray") else As
+    Minv = np.zeros_like(Ad)
+    for i in range(N):
+        sl = slice(3 * i, 3 * i + 3)
+        Minv[sl, sl] = np.linalg.inv(Ad[sl, sl])
+    return sp.csr_matrix(Ad @ Minv)
+
+
+def test_folded_block_jacobi_operator(cube):
+    """A M^-1 (the operator the A-solves iterate on) in FP64, FP32 and BF16
+    with block scale, against the oracle's scaled A times its block-diagonal
+    inverse."""
+    gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
+    H.hyel_solve_setup(gp.ctx)
+    wo = S.diag_scaling(Kd)
+    As = S.split_blocks(sp.diags(wo) @ Kd @ sp.diags(wo), N)[0]
+    AM = _block_jacobi_fold(As, N)
+    x = inputs.random_vector(3 * N, seed=23)
+    bound = abs(AM) @ np.abs(x)
+    y = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    H.hyel_spmv(gp.ctx, H.HYEL_OP_AM, H.HYEL_MAT_SCALED64, _dev(x).data_ptr(), y.data_ptr())
+    assert np.all(np.abs(y.cpu().numpy() - AM @ x) <= 1e-12 * bound)
+    x32 = x.astype(np.float32)
+    y32 = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
+    H.hyel_spmv(gp.ctx, H.HYEL_OP_AM, H.HYEL_MAT_SCALED32, _dev(x32, torch.float32).data_ptr(), y32.data_ptr())
+    assert np.all(np.abs(y32.cpu().numpy() - AM @ x32.astype(np.float64)) <= 2e-6 * bound)
+    y16 = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
+    H.hyel_spmv(gp.ctx, H.HYEL_OP_AM, H.HYEL_MAT_SCALED_BF16S, _dev(x32, torch.float32).data_ptr(),
+                y16.data_ptr())
+    d = np.abs(y16.cpu().numpy() - AM @ x32.astype(np.float64))
+    assert np.all(d <= (2.0 ** -9 + 4e-6) * bound)
+    assert np.max(d / bound) > 2.0 ** -14
+    # the diagonal blocks of A M^-1 are the identity
+    bsr = sp.bsr_matrix(AM, blocksize=(3, 3))
+    for i in range(0, N, 37):
+        for q in range(bsr.indptr[i], bsr.indptr[i + 1]):
+            if bsr.indices[q] == i:
+                assert np.max(np.abs(bsr.data[q] - np.eye(3))) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S])
+def test_nested_solve_with_restarts(cube, precision):
+    """GMRES(m) restarts at every level (outer FGMRES(2), A- and inner
+    GMRES(3), S GMRES(2), sub-tolerances 1e-6 so that every level runs past
+    its restart length): the restarted solve still reaches the direct
+    solution."""
+    gp, Kd, N = cube["gp"], cube["Kd"], cube["N"]
+    xo = S.direct_solve(Kd, cube["rhs_o"])
+    x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    sub = 1e-6 if precision == H.HYEL_PREC_FP64 else 1e-5
+    params = H.solver_params(outer_rtol=1e-13, sub_rtol=sub, precision=precision, outer=(2000, 2),
+                             a=(3000, 3), s=(2000, 2), inner=(3000, 3))
+    st, rc = H.hyel_solve_nested(gp.ctx, params, cube["rhs"].data_ptr(), x.data_ptr())
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-9, (err, st.as_dict())
+    # every level ran more iterations per solve than its restart length
+    assert st.outer_its > 2
+    assert st.a_its > 3 * st.a_solves and st.inner_its > 3 * st.inner_solves and st.s_its > 2 * st.s_solves
 
 
 @pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
