@@ -59,7 +59,9 @@ __device__ __forceinline__ double qpair(const double *X, double S, int A, int B)
 }
 __device__ __forceinline__ double qone(const double *X, double S, int A) { return QAB * X[A] + QB * S; }
 
-template <bool TAN>
+// TAN: also the tangent blocks; CORR: also the K_{.,udot} R_k right-hand-side
+// correction (record 17; zeros otherwise)
+template <bool TAN, bool CORR>
 __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= a.E) return;
@@ -259,18 +261,20 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
     }
     if (!TAN) return;
 
-    // ---- tangent: per-element coefficients (all scaled by c2 = (a_f g dt)^2/a_m)
+    // ---- tangent. The weights c2 = (a_f g dt)^2/a_m, c1 = a_f g dt and a_m are
+    // folded into per-element and per-node coefficients first, so that each
+    // of the 16 node pairs costs about 70 FP64 operations.
     const double c1 = a.c1, c2 = a.c2, am = a.am;
-    // A_u(A,B,i,j) = Q1_Ai n_Bj + Q2_Ai f_Bj + q3 n_Aj n_Bi + [i==j] q4 gg_AB + fibre terms
+    // A_u(A,B,i,j) = Q1_Ai n_Bj + Q2_Ai f_Bj + q3 n_Aj n_Bi + [i==j] q4 gg + fibre terms; here times c2
     double Q1[4][3], Q2[4][3];
     double q3 = V * mu * aJ * I1 / 3.0 + Pbar;
-    const double q4 = V * mu * aJ;
+    const double q4 = c2 * V * mu * aJ;
 #pragma unroll
     for (int A = 0; A < 4; A++)
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             Q1[A][i] = -V * (mu / 3.0) * E0[A][i] - Pbar * n[A][i] + W * qone(xrv[i], Srv[i], A);
-            Q2[A][i] = -V * (2.0 / 3.0) * mu * aJ * n[A][i];
+            Q2[A][i] = c2 * (-V * (2.0 / 3.0) * mu * aJ * n[A][i]);
         }
     if (a.nfib) {
 #pragma unroll
@@ -282,14 +286,54 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
                 for (int i = 0; i < 3; i++) Q1[A][i] -= V * (2.0 / 3.0) * fd1[tf] * fE[tf][A][i];
         }
     }
-    // C coefficients
-    double cA[4], cB[4], LvTn[4][3];
+#pragma unroll
+    for (int A = 0; A < 4; A++)
+#pragma unroll
+        for (int i = 0; i < 3; i++) Q1[A][i] *= c2;
+    q3 *= c2;
+    // mass (a_m int rho J N_A N_B), B-block and D-block quadrature values, pre-weighted
+    double xm[4], xpc[3][4], xdw[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        xm[q] = am * W * xr[q];
+        xdw[q] = W * xd[q];
+#pragma unroll
+        for (int i = 0; i < 3; i++) xpc[i][q] = c1 * W * xrp[i][q];
+    }
+    const double Sm = am * W * Sr, Sdw = W * Sd;
+    double Spc[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) Spc[i] = c1 * W * Srp[i];
+    const double jv4c1 = c1 * JV4;
+    // C^j_AB = cAs_A n_Bj + cBs_B n_Aj - LvTnc_Bj - gpc_j nn
+    //   cAs_A = c2 (W rb_A + JV/4 div v + tau n_A.sigma) + c1 JV/4,
+    //   cBs_B = -c2 tau n_B.sigma + a_m tau int(rho J N_B), LvTnc = c2 JV/4 (grad v^T n), gpc = c2 tau J V p_,j
+    // D_AB = int J (a_m beta + c1 beta_,p pdot) N_A N_B + c1 tau J V nn + n_A . qrc_B,
+    //   qrc_B,i = c1 tau int J rho_,p (vdot_i - b_i) N_B
+    double cA[4], cB[4], cAs[4], cBs[4], LvTn[4][3], qrc[4][3], gpc[3];
+    const double c1tJV = c1 * tau * JV;
 #pragma unroll
     for (int A = 0; A < 4; A++) {
-        cA[A] = W * qone(xb, Sb, A) + JV4 * divv + tau * ns[A];   // (times c2) + c1 JV/4
-        cB[A] = -tau * ns[A];                                     // (times c2); + am tau rB
+        cA[A] = W * qone(xb, Sb, A) + JV4 * divv + tau * ns[A];
+        cB[A] = -tau * ns[A];
+        cAs[A] = c2 * cA[A] + c1 * JV4;
+        cBs[A] = c2 * cB[A] + am * tau * W * qone(xr, Sr, A);
 #pragma unroll
-        for (int j = 0; j < 3; j++) LvTn[A][j] = Lv[0][j] * n[A][0] + Lv[1][j] * n[A][1] + Lv[2][j] * n[A][2];
+        for (int j = 0; j < 3; j++) {
+            LvTn[A][j] = Lv[0][j] * n[A][0] + Lv[1][j] * n[A][1] + Lv[2][j] * n[A][2];
+            qrc[A][j] = c1 * tau * W * qone(xrp[j], Srp[j], A);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) gpc[j] = c2 * tau * JV * gp[j];
+    double w2c[2] = {0.0, 0.0}, w1c[2] = {0.0, 0.0}, w0c[2] = {0.0, 0.0};
+    if (a.nfib) {
+#pragma unroll
+        for (int tf = 0; tf < 2; tf++) {
+            w2c[tf] = c2 * V * fd2[tf];
+            w1c[tf] = -c2 * V * (4.0 / 3.0) * fd1[tf] * aJ;
+            w0c[tf] = c2 * 2.0 * V * fd1[tf] * aJ;
+        }
     }
     double corr[4][4];
 #pragma unroll
@@ -304,71 +348,69 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
             double out[16];
             const double gg = g[A][0] * g[B][0] + g[A][1] * g[B][1] + g[A][2] * g[B][2];
             const double nn = n[A][0] * n[B][0] + n[A][1] * n[B][1] + n[A][2] * n[B][2];
-            const double mr = W * qpair(xr, Sr, A, B);
-            double Au[3][3];
+            // A block: c2 A_u + a_m (mass) on the diagonal
+            const double dg = q4 * gg + qpair(xm, Sm, A, B);
 #pragma unroll
             for (int i = 0; i < 3; i++)
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
                     double s = Q1[A][i] * n[B][j] + Q2[A][i] * f[B][j] + q3 * n[A][j] * n[B][i];
-                    if (i == j) s += q4 * gg;
-                    Au[i][j] = s;
+                    if (i == j) s += dg;
+                    out[3 * i + j] = s;
                 }
             if (a.nfib) {
 #pragma unroll
                 for (int tf = 0; tf < 2; tf++) {
                     const double gHg = kd * gg + kd3 * fga[tf][A] * fga[tf][B];
-                    const double w2 = V * fd2[tf], w1 = -V * (4.0 / 3.0) * fd1[tf] * aJ, w0 = 2.0 * V * fd1[tf] * aJ * gHg;
+                    const double d0 = w0c[tf] * gHg;
 #pragma unroll
-                    for (int i = 0; i < 3; i++)
+                    for (int i = 0; i < 3; i++) {
+                        const double e2 = w2c[tf] * fE[tf][A][i], e1 = w1c[tf] * n[A][i];
 #pragma unroll
                         for (int j = 0; j < 3; j++) {
                             const double FHgB = kd * f[B][j] + kd3 * fFa[tf][j] * fga[tf][B];
-                            double s = w2 * fE[tf][A][i] * fE[tf][B][j] + w1 * n[A][i] * FHgB;
-                            if (i == j) s += w0;
-                            Au[i][j] += s;
+                            out[3 * i + j] += e2 * fE[tf][B][j] + e1 * FHgB + (i == j ? d0 : 0.0);
                         }
+                    }
                 }
             }
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) out[3 * i + j] = c2 * Au[i][j] + (i == j ? am * mr : 0.0);
             // B^i_AB = c1 (int rho_,p J (vdot_i - b_i) N_A N_B - J N_A,i V/4)
 #pragma unroll
-            for (int i = 0; i < 3; i++) out[9 + i] = c1 * (W * qpair(xrp[i], Srp[i], A, B) - JV4 * n[A][i]);
-            // C^j_AB = am tau n_Aj int(rho J N_B) + c1 JV/4 n_Bj + c2 C_u
-            const double rB = W * qone(xr, Sr, B);
-            double Cu[3];
+            for (int i = 0; i < 3; i++) out[9 + i] = qpair(xpc[i], Spc[i], A, B) - jv4c1 * n[A][i];
 #pragma unroll
-            for (int j = 0; j < 3; j++) {
-                Cu[j] = cA[A] * n[B][j] + cB[B] * n[A][j] - JV4 * LvTn[B][j] - tau * JV * gp[j] * nn;
-                out[12 + j] = c2 * Cu[j] + am * tau * rB * n[A][j] + c1 * JV4 * n[B][j];
-            }
-            // D_AB = int J (am beta + c1 beta_,p pdot) N_A N_B + c1 tau (J V n_A.n_B + n_Ai int J rho_,p (vdot_i-b_i) N_B)
-            double tB = 0.0;
+            for (int j = 0; j < 3; j++) out[12 + j] = cAs[A] * n[B][j] + cBs[B] * n[A][j] - c2 * JV4 * LvTn[B][j] - gpc[j] * nn;
+            out[15] = qpair(xdw, Sdw, A, B) + c1tJV * nn + n[A][0] * qrc[B][0] + n[A][1] * qrc[B][1] + n[A][2] * qrc[B][2];
+            if (CORR) {
+                // c2 A_u R_k (the A block less its mass part) and C_u R_k
 #pragma unroll
-            for (int i = 0; i < 3; i++) tB += n[A][i] * W * qone(xrp[i], Srp[i], B);
-            out[15] = W * qpair(xd, Sd, A, B) + c1 * tau * (JV * nn + tB);
-            if (a.corr) {
+                for (int i = 0; i < 3; i++) {
+                    double s = 0.0;
 #pragma unroll
-                for (int i = 0; i < 3; i++)
-                    corr[A][i] += Au[i][0] * rk[B][0] + Au[i][1] * rk[B][1] + Au[i][2] * rk[B][2];
-                corr[A][3] += Cu[0] * rk[B][0] + Cu[1] * rk[B][1] + Cu[2] * rk[B][2];
+                    for (int j = 0; j < 3; j++) s += (out[3 * i + j] - (i == j ? qpair(xm, Sm, A, B) : 0.0)) * rk[B][j];
+                    corr[A][i] += s;
+                }
+                double sp = 0.0;
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const double Cu = cA[A] * n[B][j] + cB[B] * n[A][j] - JV4 * LvTn[B][j] - tau * JV * gp[j] * nn;
+                    sp += Cu * rk[B][j];
+                }
+                corr[A][3] += sp;
             }
             double2 *rec = reinterpret_cast<double2 *>(record(a.stage, e, 4 * A + B));
 #pragma unroll
             for (int k = 0; k < 8; k++) rec[k] = make_double2(out[2 * k], out[2 * k + 1]);
         }
     }
-    // A_u = dR_m/du and C_u = dR_p/du (the c2-free parts above); since
-    // K_{.,udot} = c1 d(.)/du, (1/a_m) K_{.,udot} R_k = (c1/a_m) [A_u ; C_u] R_k.
+    // A_u = dR_m/du and C_u = dR_p/du; since K_{.,udot} = c1 d(.)/du,
+    // (1/a_m) K_{.,udot} R_k = (c1/a_m) [A_u ; C_u] R_k. corr[.][0..2] holds
+    // c2 A_u R_k (c2 > 0 whenever the correction is formed: dt > 0).
     double2 *rc = reinterpret_cast<double2 *>(record(a.stage, e, 17));
-    const double sc = a.corr ? c1 / am : 0.0;
+    const double su = CORR ? c1 / (am * c2) : 0.0, sp = CORR ? c1 / am : 0.0;
 #pragma unroll
     for (int A = 0; A < 4; A++) {
-        rc[2 * A] = make_double2(sc * corr[A][0], sc * corr[A][1]);
-        rc[2 * A + 1] = make_double2(sc * corr[A][2], sc * corr[A][3]);
+        rc[2 * A] = make_double2(su * corr[A][0], su * corr[A][1]);
+        rc[2 * A + 1] = make_double2(su * corr[A][2], sp * corr[A][3]);
     }
 }
 
@@ -550,7 +592,7 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     a.E = m.E;
     a.vol = m.vol_model;
     a.nfib = m.n_fibres;
-    a.corr = tc.literal ? 0 : 1;
+    a.corr = (tc.literal || tc.skip_corr) ? 0 : 1;
     a.rho0 = m.rho0;
     a.kd = m.kd;
     a.b0 = m.body[0];
@@ -570,7 +612,10 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_ASSEMBLE, &ev);
-    (k_element<true><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
+    if (a.corr)
+        (k_element<true, true><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
+    else
+        (k_element<true, false><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
     HYEL_CK(cudaGetLastError());
     // algorithmic bytes: element geometry+material (18 doubles), 4 nodes x 17 state doubles, staging writes
     prof_end(c, HYEL_K_ASSEMBLE, ev, (double)m.E * (8.0 * 18 + 16 + 4 * 8.0 * 17 + 8.0 * kRecords * kRecordDoubles));

@@ -179,6 +179,7 @@ struct TimeConsts {
     double am, af, gam, dt, c1, c2;  // c1 = af*gam*dt, c2 = c1^2/am
     double t_alpha, load;            // load factor s(t_alpha)
     int literal;
+    int skip_corr = 0;  // R_k is zero up to rounding (after a corrector update): no K_{.,udot} R_k term
 };
 TimeConsts time_consts(const DeviceMesh &m, const hyel_time_params &tp);
 // Assembles residual, rhs, tangent; returns squared norms (host) when norms != nullptr.

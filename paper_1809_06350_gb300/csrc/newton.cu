@@ -158,7 +158,12 @@ void newton_step(Ctx &c, const hyel_time_params &tp, const hyel_solver_params &s
         (k_stage<<<blocks_for(n7, 256), 256, 0, c.stream>>>(a), ::hyel::count_launch());
         auto ta = std::chrono::steady_clock::now();
         double norms[4];
-        assemble(c, tc, stage, nullptr, rhs, norms);
+        // after a corrector update the kinematic residual R_k vanishes up to
+        // rounding (the Delta udot of eq. NR_smaller_eqn_2 cancels it), so the
+        // K_{.,udot} R_k correction of the right-hand side is formed at l = 1 only
+        TimeConsts tcl = tc;
+        tcl.skip_corr = l > 1 ? 1 : 0;
+        assemble(c, tcl, stage, nullptr, rhs, norms);
         ms_asm += 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - ta).count();
         if (l == 1) norm0 = norms[0];
         ns.res_norm = norms[0];

@@ -1,7 +1,9 @@
 """GPU parity of element assembly (Appendix A) against the FP64 oracle.
 
 Residual, right-hand side of eq. NR_smaller_eqn_1 (with the K_{.,udot} R_k
-terms) and the tangent blocks A, B, C, D with Dirichlet elimination, on random
+terms, and the literal -[R_m; R_p] of the multi-corrector stage, which runs
+the kernel form without the correction) and the tangent blocks A, B, C, D
+with Dirichlet elimination, on random
 stage states that exercise every term, for the compressible Gibbs, the
 incompressible and the HGO materials, global and per-element parameters, a
 body force and a traction. Tangent bar: |a_gpu - a_orc| <= 1e-12 max|block row|
@@ -45,8 +47,9 @@ def _state(prob, seed, scale=1.0):
     return st
 
 
+@pytest.mark.parametrize("literal", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_assembly_matches_oracle(name):
+def test_assembly_matches_oracle(name, literal):
     m, mat, fields = _case(name)
     load = {"p_max": 2e4, "t_ramp": 5e-3}
     gp = GpuProblem(m, mat, fields, load)
@@ -54,7 +57,7 @@ def test_assembly_matches_oracle(name):
     st = _state(prob, 13)
     dt = 1e-3
     am, af, gam = S.gen_alpha(0.5)
-    tp = H.time_params(dt=dt, t_n=1e-3)
+    tp = H.time_params(dt=dt, t_n=1e-3, rhs_literal=literal)
     t_alpha = 1e-3 + af * dt
     dev, sst = gp.stage(st)
     N = gp.N
@@ -64,7 +67,7 @@ def test_assembly_matches_oracle(name):
     rp, col, A, B, Cb, D = gp.download()
 
     ga = (am, af, gam, dt)
-    rhs_o, Rm, Rp, Rk = S.newton_rhs(prob, st, t_alpha, ga, exact=True)
+    rhs_o, Rm, Rp, Rk = S.newton_rhs(prob, st, t_alpha, ga, exact=(literal == 0))
     K = S.assemble_matrix(prob, st, ga)
     Kd, rhs_o = S.apply_dirichlet(K, rhs_o, S.dirichlet_dofs(prob))
     Ao, Bo, Co, Do = oracle_blocks(Kd, N, rp, col)
