@@ -471,19 +471,34 @@ __global__ void __launch_bounds__(kThreads) k_sumsq(const double *__restrict__ r
 // gid, gid + G*B, ... for the whole solve and the phases of an iteration are
 // separated by grid barriers instead of kernel boundaries. Per iteration j:
 //   P1  v_j = s u (s = 1/||u||, applied lazily), w = s A~ u (SELL-32 SpMV,
-//       gathering u), partial dots V_l . w            -> barrier, h1 = sum
-//   P2  w -= V h1, partial dots V_l . w                -> barrier, h2 = sum
-//   P3  w -= V h2, partial ||w||^2                     -> barrier: Givens,
-//       stopping test and, at the end of a cycle, y = R^-1 g and the
-//       restart combination (all by the last block to arrive)
-// The last block to reach a barrier sums the per-block partials in block
-// order before releasing the others, so every result is reproducible bit for
-// bit. Row-local vectors (V, w, x) are only touched by the thread that owns
-// the node; values written by other blocks are read after a barrier.
+//       gathering u), partial dots V_l . w and w . w  -> barrier, h1, ||w||
+//   test in the manner of Daniel, Gragg, Kaufman and Stewart: when
+//   ||w - V h1||, from Pythagoras, is at least eta ||w|| (kPgEta2), one
+//   classical Gram-Schmidt pass is kept:
+//   P2  w -= V h1; Givens and stopping test        -> barrier (w complete)
+//   otherwise the second pass follows (CGS2):
+//   P2  w -= V h1, partial dots V_l . w            -> barrier, h2
+//   P3  w -= V h2, partial ||w||^2                 -> barrier; Givens, test
+//   At the end of a cycle: y = R^-1 g, x += M^-1 V y and the restart
+//   combination.
+// After each barrier every block sums the per-block partials itself, in
+// block order, and keeps its own copy of the Givens rotations, g and the
+// current Hessenberg column: all blocks compute bitwise-identical values and
+// take the same decisions, and no block waits on another's reduction. Block 0
+// alone writes the Hessenberg columns (read back at the end of a cycle) and
+// the level state. Partials are double-buffered by barrier parity, so a block
+// never overwrites sums another block is still reading. Row-local vectors (V,
+// w, x) are only touched by the thread that owns the node; values written by
+// other blocks are read after a barrier.
 // Every barrier wait is bounded (1 s): a block that runs out of time sets the
 // abort word, every block then leaves, and the level state reports flag 8.
 
 constexpr int kPgThreads = 512;
+// eta^2 of the single-pass test: 1e-6 in FP64 (norm to ~4e-10, orthogonality
+// to ~2e-13), 1e-2 in FP32 (norm to ~1e-5, orthogonality to ~1e-6); the
+// A-solves stop at a relative residual of about 1e-2
+template <typename T>
+constexpr double kPgEta2 = sizeof(T) == 8 ? 1e-6 : 1e-2;
 constexpr unsigned long long kBarrierNs = 1000000000ull;
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -503,8 +518,8 @@ struct PgArgs {
     int64_t N;                                // nodes (vectors have 3N entries)
     const T *b;
     T *x, *V, *U0, *U1;
-    double *H, *cs, *sn, *g, *y, *cr, *tot;   // tot: [m + 3] sums and scalars
-    double *partial;                          // [m + 1][grid]
+    double *H;                                // rotated Hessenberg columns (written by block 0)
+    double *partial;                          // 2 x [m + 1][grid], by barrier parity
     unsigned *bar;                            // barrier words (arrivals, generation, abort)
     LevelState *st;
     int m, maxit;
@@ -512,50 +527,44 @@ struct PgArgs {
     double it_fixed, it_unit;  // algorithmic bytes per iteration: fixed + (4 (j+1) + 9) unit
 };
 
-// Barrier words, each on its own 128-byte line: arrivals, generation, abort.
-constexpr int kBarArrive = 0, kBarGen = 32, kBarAbort = 64, kBarWords = 96;
+// Barrier words, each on its own 128-byte line: arrivals (they only grow
+// within a launch), release (the number of completed barriers), abort.
+constexpr int kBarArrive = 0, kBarRelease = 32, kBarAbort = 64, kBarWords = 96;
 
-// Grid barrier; red() runs in the last block to arrive, before the release.
-// false: a wait ran out of time or another block gave up. The fence after
-// the wait makes the other blocks' writes visible to ordinary loads of every
-// thread of the block once it passes the closing __syncthreads.
-template <typename F>
-__device__ bool grid_step(unsigned *bw, unsigned &gen, F &&red) {
-    __shared__ int s_last, s_ok;
+// Grid barrier number `phase` (then phase + 1). The last block to arrive
+// releases the others; a wait is bounded by kBarrierNs. false: the wait ran
+// out of time or a block gave up (every block then leaves). The fences around
+// the wait make writes issued before the barrier by any block visible to
+// ordinary loads of every thread of the block after it.
+__device__ bool pg_barrier(unsigned *bw, unsigned &phase) {
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(&bw[kBarArrive], 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last) {
-        if (threadIdx.x == 0) __threadfence();
-        __syncthreads();
-        red();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            s_ok = ((volatile unsigned *)bw)[kBarAbort] == 0u;
-            atomicExch(&bw[kBarArrive], 0u);
-            __threadfence();
-            atomicAdd(&bw[kBarGen], 1u);
-        }
-    } else if (threadIdx.x == 0) {
-        volatile unsigned *vb = bw;
-        const unsigned long long t0 = global_ns();
+        const unsigned target = (phase + 1u) * gridDim.x;
+        const unsigned prev = atomicAdd(&bw[kBarArrive], 1u);
         int ok = 1;
-        while (vb[kBarGen] == gen) {
-            __nanosleep(64);
-            if (vb[kBarAbort] != 0u || global_ns() - t0 > kBarrierNs) {
-                atomicExch(&bw[kBarAbort], 1u);
-                ok = 0;
-                break;
+        volatile unsigned *vb = bw;
+        if (prev + 1u == target) {
+            __threadfence();
+            atomicExch(&bw[kBarRelease], phase + 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (vb[kBarRelease] < phase + 1u) {
+                __nanosleep(32);
+                if (vb[kBarAbort] != 0u || global_ns() - t0 > kBarrierNs) {
+                    atomicExch(&bw[kBarAbort], 1u);
+                    ok = 0;
+                    break;
+                }
             }
         }
+        if (vb[kBarAbort] != 0u) ok = 0;
         s_ok = ok;
         __threadfence();
     }
     __syncthreads();
-    gen += 1;
+    phase += 1u;
     return s_ok != 0;
 }
 
@@ -621,13 +630,15 @@ __device__ __forceinline__ double pg_block_sum(T v, double *red) {
     return t;
 }
 
-// Partial dots V_l . w (l < nk) of this block's nodes into partial[l][block];
-// sums within a warp in T, across the block's warps in double.
+// Partial dots V_l . w (l < nv), and w . w as column nv when self, of this
+// block's nodes into partial[l][block]; sums within a warp in T, across the
+// block's warps in double.
 template <typename T>
-__device__ void pg_dots(const T *V, const T *w, int64_t N, int nk, double *partial) {
+__device__ void pg_dots(const T *V, const T *w, int64_t N, int nv, bool self, double *partial) {
     __shared__ double red[kPgThreads / 32][KC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = 3 * N;
+    const int nk = nv + (self ? 1 : 0);
     for (int k0 = 0; k0 < nk; k0 += KC) {
         const int kc = min(KC, nk - k0);
         T acc[KC];
@@ -638,7 +649,7 @@ __device__ void pg_dots(const T *V, const T *w, int64_t N, int nk, double *parti
 #pragma unroll
             for (int c = 0; c < KC; c++)
                 if (c < kc) {
-                    const T *v = V + (int64_t)(k0 + c) * n + 3 * i;
+                    const T *v = k0 + c < nv ? V + (int64_t)(k0 + c) * n + 3 * i : w + 3 * i;
                     acc[c] = fma(v[0], w0, fma(v[1], w1, fma(v[2], w2, acc[c])));
                 }
         }
@@ -729,14 +740,19 @@ __device__ __forceinline__ void pg_row(const PgArgs<T> &a, int64_t i, const T *u
 }
 
 template <typename T, bool H16>
-__global__ void __launch_bounds__(kPgThreads) k_gmres_a(PgArgs<T> a) {
-    __shared__ T hs[kMaxK + 1];
-    __shared__ double s_sc[2];
+__global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
+    // per-block copies of the small GMRES state (identical in every block)
+    __shared__ double s_cs[kMaxK], s_sn[kMaxK], s_g[kMaxK + 1], s_col[kMaxK + 2], s_tmp[kMaxK + 2];
+    __shared__ T hs[kMaxK + 2];
+    __shared__ double s_sc[4];  // 0: squared norm, 1: next scale, 2: 1 / h_{j+1,j}, 3: tol
+    __shared__ int s_fl[5];     // 0: done, 1: stop, 2: y usable, 3: total iterations, 4: second pass
     const int64_t N = a.N, n = 3 * N;
     const int m = a.m;
+    const int G = gridDim.x;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;  // writes the level state and H
     LevelState *st = a.st;
-    volatile LevelState *vst = st;
-    unsigned gen = 0u;  // the barrier words are cleared before every launch
+    unsigned phase = 0u;  // barriers passed; the barrier words are cleared before every launch
+    auto pbuf = [&](unsigned ph) { return a.partial + (size_t)(ph & 1u) * G * (m + 1); };
 
     auto abort_out = [&]() {
         if (threadIdx.x == 0) {
@@ -747,25 +763,34 @@ __global__ void __launch_bounds__(kPgThreads) k_gmres_a(PgArgs<T> a) {
     };
 
     // ---- start: x = 0, beta = ||b||
-    T ss = 0;
-    PG_FOR_OWN_NODES(N, i)
-#pragma unroll
-        for (int r = 0; r < 3; r++) {
-            const T v = a.b[3 * i + r];
-            a.x[3 * i + r] = 0;
-            ss = fma(v, v, ss);
-        }
     {
+        T ss = 0;
+        PG_FOR_OWN_NODES(N, i)
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                const T v = a.b[3 * i + r];
+                a.x[3 * i + r] = 0;
+                ss = fma(v, v, ss);
+            }
         __shared__ double red1[kPgThreads / 32];
         const double tb = pg_block_sum<T>(ss, red1);
-        if (threadIdx.x == 0) a.partial[blockIdx.x] = tb;
+        if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
     }
-    bool ok = grid_step(a.bar, gen, [&]() {
-        __shared__ double tot0;
-        pg_sum(a.partial, 1, &tot0);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double beta = sqrt(tot0);
+    if (!pg_barrier(a.bar, phase)) return abort_out();
+    pg_sum(pbuf(phase - 1), 1, s_sc);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double beta = sqrt(s_sc[0]);
+        const double tol = fmax(a.rtol * beta, a.atol);
+        const int nan = isfinite(beta) ? 0 : 1;
+        const int conv = (!nan && beta <= tol) ? 1 : 0;
+        s_sc[1] = beta > 0.0 ? 1.0 / beta : 0.0;
+        s_sc[3] = tol;
+        s_fl[1] = (conv || nan) ? 1 : 0;
+        s_fl[3] = 0;
+        s_g[0] = beta;
+        for (int l = 1; l <= m; l++) s_g[l] = 0.0;
+        if (lead) {
             st->k = 0;
             st->total = 0;
             st->cycles = 0;
@@ -773,31 +798,27 @@ __global__ void __launch_bounds__(kPgThreads) k_gmres_a(PgArgs<T> a) {
             st->m = m;
             st->beta = beta;
             st->bnorm = beta;
-            st->tol = fmax(a.rtol * beta, a.atol);
+            st->tol = tol;
             st->res = beta;
-            st->inv_scale = beta > 0.0 ? 1.0 / beta : 0.0;
-            const int nan = isfinite(beta) ? 0 : 1;
+            st->inv_scale = s_sc[1];
             st->flags = nan;
-            st->converged = (!nan && beta <= st->tol) ? 1 : 0;
-            st->stop = (st->converged || nan) ? 1 : 0;
-            st->done = st->stop;
+            st->converged = conv;
+            st->stop = s_fl[1];
+            st->done = s_fl[1];
             st->yok = 0;
-            if (st->stop) {
+            if (s_fl[1]) {
                 st->solves += 1;
                 st->status_any |= nan;
                 st->stop = 2;
             }
-            a.g[0] = beta;
-            for (int l = 1; l <= m; l++) a.g[l] = 0.0;
-            a.tot[m + 1] = st->inv_scale;
         }
-    });
-    if (!ok) return abort_out();
-    if (vst->stop) return;
+    }
+    __syncthreads();
+    if (s_fl[1]) return;
 
     const T *uin = a.b;
     T *uout = a.U0;
-    T s = (T)a.tot[m + 1];
+    T s = (T)s_sc[1];
     int j = 0;
     for (;;) {
         // ---- P1: v_j = s u; w = s A~ u; dots with V_0..V_j
@@ -812,159 +833,147 @@ __global__ void __launch_bounds__(kPgThreads) k_gmres_a(PgArgs<T> a) {
             uout[3 * i + 1] = y1 * s;
             uout[3 * i + 2] = y2 * s;
         }
-        pg_dots<T>(a.V, uout, N, j + 1, a.partial);
-        ok = grid_step(a.bar, gen, [&]() {
-            pg_sum(a.partial, j + 1, a.tot);
-            __syncthreads();
-            for (int l = threadIdx.x; l <= j; l += blockDim.x) a.H[(int64_t)j * (m + 1) + l] = a.tot[l];
-        });
-        if (!ok) return abort_out();
-        // ---- P2: w -= V h1; dots again (second Gram-Schmidt pass)
-        for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = (T)a.tot[l];
+        pg_dots<T>(a.V, uout, N, j + 1, true, pbuf(phase));
+        if (!pg_barrier(a.bar, phase)) return abort_out();
+        pg_sum(pbuf(phase - 1), j + 2, s_col);  // h1, and ||w||^2 in s_col[j + 1]
         __syncthreads();
-        pg_axpy<T>(a.V, uout, N, j + 1, hs);
-        pg_dots<T>(a.V, uout, N, j + 1, a.partial);
-        ok = grid_step(a.bar, gen, [&]() {
-            pg_sum(a.partial, j + 1, a.tot);
+        // DGKS-type test: one Gram-Schmidt pass suffices when it keeps at
+        // least eta of ||w|| (the norm after the pass by Pythagoras, accurate
+        // to about eps / eta^2; orthogonality to about eps / eta)
+        if (threadIdx.x == 0) {
+            const double ww = s_col[j + 1];
+            double hh = 0.0;
+            for (int l = 0; l <= j; l++) hh += s_col[l] * s_col[l];
+            const double w2 = ww - hh;
+            s_fl[4] = (w2 >= kPgEta2<T> * ww) ? 0 : 1;
+            s_sc[0] = w2;
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = (T)s_col[l];
+        __syncthreads();
+        const bool reorth = s_fl[4] != 0;
+        if (!reorth) {
+            // ---- P2: w -= V h1, the new direction (norm from the test above)
+            pg_axpy<T>(a.V, uout, N, j + 1, hs);
+        } else {
+            // ---- P2: w -= V h1; dots again (second Gram-Schmidt pass)
+            pg_axpy<T>(a.V, uout, N, j + 1, hs);
+            pg_dots<T>(a.V, uout, N, j + 1, false, pbuf(phase));
+            if (!pg_barrier(a.bar, phase)) return abort_out();
+            pg_sum(pbuf(phase - 1), j + 1, s_tmp);  // h2
             __syncthreads();
             for (int l = threadIdx.x; l <= j; l += blockDim.x) {
-                volatile double *Hc = a.H + (int64_t)j * (m + 1);
-                Hc[l] = Hc[l] + a.tot[l];
+                hs[l] = (T)s_tmp[l];
+                s_col[l] += s_tmp[l];
             }
-        });
-        if (!ok) return abort_out();
-        // ---- P3: w -= V h2; ||w||
-        for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = (T)a.tot[l];
-        __syncthreads();
-        {
-            __shared__ double red1[kPgThreads / 32];
-            const double tb = pg_block_sum<T>(pg_axpy<T>(a.V, uout, N, j + 1, hs), red1);
-            if (threadIdx.x == 0) a.partial[blockIdx.x] = tb;
-        }
-        ok = grid_step(a.bar, gen, [&]() {
-            __shared__ double tot0;
-            __shared__ int s_yok;
-            pg_sum(a.partial, 1, &tot0);
             __syncthreads();
-            if (threadIdx.x == 0) {
-                volatile double *Hc = a.H + (int64_t)j * (m + 1);
-                volatile double *cs = a.cs, *sn = a.sn, *g = a.g;
-                const double hn = sqrt(tot0);
-                for (int l = 0; l < j; l++) {
-                    const double a0 = Hc[l], a1 = Hc[l + 1];
-                    Hc[l] = cs[l] * a0 + sn[l] * a1;
-                    Hc[l + 1] = -sn[l] * a0 + cs[l] * a1;
-                }
-                const double al = Hc[j];
-                double c, s2, r;
-                if (hn == 0.0) {
-                    c = 1.0;
-                    s2 = 0.0;
-                    r = al;
-                } else {
-                    r = sqrt(al * al + hn * hn);
-                    c = al / r;
-                    s2 = hn / r;
-                }
-                cs[j] = c;
-                sn[j] = s2;
-                Hc[j] = r;
-                Hc[j + 1] = 0.0;
-                const double gj = g[j];
-                g[j] = c * gj;
-                g[j + 1] = -s2 * gj;
-                const double res = fabs(g[j + 1]);
+            // ---- P3: w -= V h2; ||w||
+            {
+                __shared__ double red1[kPgThreads / 32];
+                const double tb = pg_block_sum<T>(pg_axpy<T>(a.V, uout, N, j + 1, hs), red1);
+                if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
+            }
+            if (!pg_barrier(a.bar, phase)) return abort_out();
+            pg_sum(pbuf(phase - 1), 1, s_sc);
+            __syncthreads();
+        }
+        // ---- Givens step and stopping test, redundantly in every block
+        if (threadIdx.x == 0) {
+            const double hn = sqrt(fmax(s_sc[0], 0.0));
+            for (int l = 0; l < j; l++) {
+                const double a0 = s_col[l], a1 = s_col[l + 1];
+                s_col[l] = s_cs[l] * a0 + s_sn[l] * a1;
+                s_col[l + 1] = -s_sn[l] * a0 + s_cs[l] * a1;
+            }
+            const double al = s_col[j];
+            double c, s2, r;
+            if (hn == 0.0) {
+                c = 1.0;
+                s2 = 0.0;
+                r = al;
+            } else {
+                r = sqrt(al * al + hn * hn);
+                c = al / r;
+                s2 = hn / r;
+            }
+            s_cs[j] = c;
+            s_sn[j] = s2;
+            s_col[j] = r;
+            s_col[j + 1] = 0.0;
+            const double gj = s_g[j];
+            s_g[j] = c * gj;
+            s_g[j + 1] = -s2 * gj;
+            const double res = fabs(s_g[j + 1]);
+            const int total = s_fl[3] + 1;
+            s_fl[3] = total;
+            int done = 0, stop = 0, flags = 0, conv = 0;
+            if (!isfinite(res) || !isfinite(hn)) {
+                flags = 1;
+                done = stop = 1;
+            } else if (r == 0.0) {
+                flags = 2;
+                done = stop = 1;
+            } else if (res <= s_sc[3]) {
+                conv = 1;
+                done = stop = 1;
+            } else if (hn == 0.0) {
+                flags = 2;
+                done = stop = 1;
+            } else if (total >= a.maxit) {
+                done = stop = 1;
+            } else if (j + 1 == m) {
+                done = 1;
+            }
+            s_fl[0] = done;
+            s_fl[1] = stop;
+            s_fl[2] = done && isfinite(res) && isfinite(hn) && r != 0.0;
+            s_sc[1] = hn > 0.0 ? 1.0 / hn : 0.0;
+            s_sc[2] = s_sc[1];
+            if (lead) {
+                for (int l = 0; l <= j + 1; l++) a.H[(int64_t)j * (m + 1) + l] = s_col[l];
                 st->k = j + 1;
-                st->total += 1;
+                st->total = total;
                 st->res = res;
-                st->inv_scale = hn > 0.0 ? 1.0 / hn : 0.0;
-                st->alg_bytes += a.it_fixed + (4.0 * (j + 1) + 9.0) * a.it_unit;
-                int done = 0, stop = 0;
-                if (!isfinite(res) || !isfinite(hn)) {
-                    st->flags |= 1;
-                    done = stop = 1;
-                } else if (r == 0.0) {
-                    st->flags |= 2;
-                    done = stop = 1;
-                } else if (res <= st->tol) {
-                    st->converged = 1;
-                    done = stop = 1;
-                } else if (hn == 0.0) {
-                    st->flags |= 2;
-                    done = stop = 1;
-                } else if (st->total >= st->maxit) {
-                    done = stop = 1;
-                } else if (j + 1 == m) {
-                    done = 1;
-                }
+                st->inv_scale = s_sc[1];
+                // one Gram-Schmidt pass: 2 (j+1) + 6 vector passes; two: 4 (j+1) + 10
+                st->alg_bytes += a.it_fixed + (reorth ? 4.0 * (j + 1) + 10.0 : 2.0 * (j + 1) + 6.0) * a.it_unit;
+                st->flags |= flags;
+                if (conv) st->converged = 1;
                 st->done = done;
                 st->stop = stop;
-                s_yok = done && isfinite(res) && isfinite(hn) && r != 0.0;
-                st->yok = s_yok;
-                a.tot[m + 1] = st->inv_scale;  // scale of the next basis vector
-                a.tot[m + 2] = st->inv_scale;  // 1 / h_{j+1,j}
+                st->yok = s_fl[2];
             }
-            __syncthreads();
-            if (s_yok && threadIdx.x < 32) {  // y = R^-1 g over the k = j+1 columns (warp 0)
-                const int k = j + 1, lane = threadIdx.x;
-                volatile double *H = a.H, *yv = a.y, *g = a.g;
-                for (int i = k - 1; i >= 0; i--) {
-                    double sacc = 0.0;
-                    for (int l = i + 1 + lane; l < k; l += 32) sacc += H[(int64_t)l * (m + 1) + i] * yv[l];
-                    sacc = warp_sum_d(sacc);
-                    if (lane == 0) yv[i] = (g[i] - sacc) / H[(int64_t)i * (m + 1) + i];
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0 && st->done) {
-                if (st->stop) {
-                    st->its += st->total;
-                    st->solves += 1;
-                    st->status_any |= st->flags | ((!st->converged && !st->flags) ? 4 : 0);
-                    st->stop = 2;
-                } else {
-                    // restart: c = G_0^T ... G_{k-1}^T (g_k e_k); new residual norm |g_k|
-                    const int k = j + 1;
-                    volatile double *cs = a.cs, *sn = a.sn, *g = a.g, *cr = a.cr;
-                    double carry = g[k];
-                    for (int i = k - 1; i >= 0; i--) {
-                        cr[i + 1] = cs[i] * carry;
-                        carry = -sn[i] * carry;
-                    }
-                    cr[0] = carry;
-                    const double beta = fabs(g[k]);
-                    st->k = 0;
-                    st->done = 0;
-                    st->cycles += 1;
-                    st->beta = beta;
-                    st->res = beta;
-                    st->inv_scale = beta > 0.0 ? 1.0 / beta : 0.0;
-                    a.tot[m + 1] = st->inv_scale;
-                    g[0] = beta;
-                    for (int l = 1; l <= m; l++) g[l] = 0.0;
-                }
-            }
-        });
-        if (!ok) return abort_out();
-        if (threadIdx.x == 0) {
-            s_sc[0] = a.tot[m + 1];
-            s_sc[1] = a.tot[m + 2];
         }
         __syncthreads();
-        const int done = vst->done, stop = vst->stop, yok = vst->yok;
-        if (!done) {
-            // next iteration: u = w, scaled lazily by 1 / h_{j+1,j}
-            s = (T)s_sc[0];
+        if (!s_fl[0]) {
+            // next iteration: u = w, scaled lazily by 1 / h_{j+1,j}; after a
+            // single pass w was finished after the last barrier
+            if (!reorth && !pg_barrier(a.bar, phase)) return abort_out();
+            s = (T)s_sc[1];
             uin = uout;
             uout = (uout == a.U0) ? a.U1 : a.U0;
             j += 1;
             continue;
         }
+        // ---- end of a cycle: y = R^-1 g over the k = j+1 columns (columns
+        // < j from H, written by block 0 before earlier barriers; column j here)
         const int k = j + 1;
-        if (yok) {  // x += M^-1 V y
-            for (int l = threadIdx.x; l < k; l += blockDim.x) hs[l] = (T)a.y[l];
+        if (s_fl[2]) {
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                for (int i = k - 1; i >= 0; i--) {
+                    double sacc = 0.0;
+                    for (int l = i + 1 + lane; l < k; l += 32)
+                        sacc += (l == j ? s_col[i] : a.H[(int64_t)l * (m + 1) + i]) * s_tmp[l];
+                    sacc = warp_sum_d(sacc);
+                    if (lane == 0) s_tmp[i] = (s_g[i] - sacc) / (i == j ? s_col[i] : a.H[(int64_t)i * (m + 1) + i]);
+                    __syncwarp();
+                }
+            }
             __syncthreads();
+            for (int l = threadIdx.x; l < k; l += blockDim.x) hs[l] = (T)s_tmp[l];
+            __syncthreads();
+            // x += M^-1 V y
             PG_FOR_OWN_NODES(N, i) {
                 T u0 = 0, u1 = 0, u2 = 0;
                 for (int l = 0; l < k; l++) {
@@ -980,11 +989,41 @@ __global__ void __launch_bounds__(kPgThreads) k_gmres_a(PgArgs<T> a) {
             }
             __syncthreads();
         }
-        if (stop) return;
-        // restart vector r = sum_{l<k} c_l V_l + c_k (w / h_{k,k-1}), unnormalised
-        for (int l = threadIdx.x; l <= k; l += blockDim.x) hs[l] = (T)a.cr[l];
+        if (s_fl[1]) {
+            if (lead) {
+                st->its += s_fl[3];
+                st->solves += 1;
+                st->status_any |= st->flags | ((!st->converged && !st->flags) ? 4 : 0);
+                st->stop = 2;
+            }
+            return;
+        }
+        // ---- restart: c = G_0^T ... G_{k-1}^T (g_k e_k), residual norm |g_k|;
+        // r = sum_{l<k} c_l V_l + c_k (w / h_{k,k-1}), unnormalised
+        if (threadIdx.x == 0) {
+            double carry = s_g[k];
+            for (int i = k - 1; i >= 0; i--) {
+                s_tmp[i + 1] = s_cs[i] * carry;
+                carry = -s_sn[i] * carry;
+            }
+            s_tmp[0] = carry;
+            const double beta = fabs(s_g[k]);
+            s_sc[1] = beta > 0.0 ? 1.0 / beta : 0.0;
+            s_g[0] = beta;
+            for (int l = 1; l <= m; l++) s_g[l] = 0.0;
+            if (lead) {
+                st->k = 0;
+                st->done = 0;
+                st->cycles += 1;
+                st->beta = beta;
+                st->res = beta;
+                st->inv_scale = s_sc[1];
+            }
+        }
         __syncthreads();
-        const T hinv = (T)s_sc[1];
+        for (int l = threadIdx.x; l <= k; l += blockDim.x) hs[l] = (T)s_tmp[l];
+        __syncthreads();
+        const T hinv = (T)s_sc[2];
         T *unew = (uout == a.U0) ? a.U1 : a.U0;
         PG_FOR_OWN_NODES(N, i) {
             T r0 = uout[3 * i] * hinv * hs[k], r1 = uout[3 * i + 1] * hinv * hs[k], r2 = uout[3 * i + 2] * hinv * hs[k];
@@ -998,9 +1037,8 @@ __global__ void __launch_bounds__(kPgThreads) k_gmres_a(PgArgs<T> a) {
             unew[3 * i + 1] = r1;
             unew[3 * i + 2] = r2;
         }
-        ok = grid_step(a.bar, gen, [&]() {});
-        if (!ok) return abort_out();
-        s = (T)a.tot[m + 1];
+        if (!pg_barrier(a.bar, phase)) return abort_out();
+        s = (T)s_sc[1];
         uin = unew;
         uout = (unew == a.U0) ? a.U1 : a.U0;
         j = 0;
@@ -1101,10 +1139,10 @@ struct Level {
     double *partial = nullptr;
     unsigned *counter = nullptr;
     int grid = 0;
-    // persistent A-solve (kind 0): second work vector, reduced sums, restart
-    // coefficients, per-block partials, barrier words, cooperative grid sizes
+    // persistent A-solve (kind 0): second work vector, per-block partials,
+    // barrier words, cooperative grid sizes
     T *z2 = nullptr;
-    double *tot = nullptr, *cr = nullptr, *pg_partial = nullptr;
+    double *pg_partial = nullptr;
     unsigned *bar = nullptr;
     int pg_grid = 0, pg_grid16 = 0;
 };
@@ -1187,8 +1225,6 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
         // the persistent A-solve: a cooperative grid of all co-resident blocks
         // (at most one thread per node)
         L.z2 = (T *)walloc(c, w, sizeof(T) * (size_t)n);
-        L.tot = (double *)walloc(c, w, sizeof(double) * (m + 3));
-        L.cr = (double *)walloc(c, w, sizeof(double) * (m + 1));
         L.bar = (unsigned *)walloc(c, w, sizeof(unsigned) * kBarWords);
         const int64_t need = std::max<int64_t>(1, (n / 3 + 31) / 32);  // no block without a slice
         int occ = 0, occ16 = 0;
@@ -1200,7 +1236,7 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
         L.pg_grid = (int)std::min<int64_t>((int64_t)occ * c.num_sms, need);
         L.pg_grid16 = (int)std::min<int64_t>((int64_t)occ16 * c.num_sms, need);
         L.pg_partial =
-            (double *)walloc(c, w, sizeof(double) * (size_t)std::max(L.pg_grid, L.pg_grid16) * (m + 1));
+            (double *)walloc(c, w, sizeof(double) * 2 * (size_t)std::max(L.pg_grid, L.pg_grid16) * (m + 1));
     }
 }
 
@@ -1339,12 +1375,6 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
     a.U0 = L.z;
     a.U1 = L.z2;
     a.H = L.H;
-    a.cs = L.cs;
-    a.sn = L.sn;
-    a.g = L.g;
-    a.y = L.y;
-    a.cr = L.cr;
-    a.tot = L.tot;
     a.partial = L.pg_partial;
     a.bar = L.bar;
     a.st = st;
