@@ -476,6 +476,7 @@ struct ResArgs {
     double load;
     int64_t N;
     int literal;
+    int use_g;           // add the K_{.,udot} R_k records (record 17) to the rhs
     double *res_out, *rhs_out;
     double *partial;     // [gridDim.x][3]
     unsigned *counter;
@@ -502,10 +503,10 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
             const double *r16 = a.stage + ((((e >> 5) * kRecords + 16) * 32 + (e & 31)) * kRecordDoubles) + 4 * A;
             const double *r17 = a.stage + ((((e >> 5) * kRecords + 17) * 32 + (e & 31)) * kRecordDoubles) + 4 * A;
 #pragma unroll
-            for (int m = 0; m < 4; m++) {
-                R[m] += r16[m];
-                G[m] += r17[m];
-            }
+            for (int m = 0; m < 4; m++) R[m] += r16[m];
+            if (a.use_g)
+#pragma unroll
+                for (int m = 0; m < 4; m++) G[m] += r17[m];
         }
         const unsigned d = a.dir[i];
 #pragma unroll
@@ -580,9 +581,11 @@ TimeConsts time_consts(const DeviceMesh &m, const hyel_time_params &tp) {
     return tc;
 }
 
-void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_out, double *rhs_out, double *norms4) {
+void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_out, double *rhs_out, double *norms4,
+              bool tangent) {
     DeviceMesh &m = c.mesh;
     if (m.N == 0) fail(HYEL_ESTATE, "assemble: no mesh uploaded");
+    if (!tangent && rhs_out) fail(HYEL_EINVAL, "assemble: a right-hand side needs the tangent pass");
     ElemArgs a;
     a.tets = m.tets;
     a.geo = m.geo;
@@ -592,7 +595,7 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     a.E = m.E;
     a.vol = m.vol_model;
     a.nfib = m.n_fibres;
-    a.corr = (tc.literal || tc.skip_corr) ? 0 : 1;
+    a.corr = (tc.literal || tc.skip_corr || !tangent) ? 0 : 1;
     a.rho0 = m.rho0;
     a.kd = m.kd;
     a.b0 = m.body[0];
@@ -612,7 +615,9 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_ASSEMBLE, &ev);
-    if (a.corr)
+    if (!tangent)
+        (k_element<false, false><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
+    else if (a.corr)
         (k_element<true, true><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
     else
         (k_element<true, false><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
@@ -620,25 +625,27 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     // algorithmic bytes: element geometry+material (18 doubles), 4 nodes x 17 state doubles, staging writes
     prof_end(c, HYEL_K_ASSEMBLE, ev, (double)m.E * (8.0 * 18 + 16 + 4 * 8.0 * 17 + 8.0 * kRecords * kRecordDoubles));
 
-    GatherArgs g;
-    g.col_slice = m.col_slice;
-    g.slice_ptr = m.slice_ptr;
-    g.row_len = m.row_len;
-    g.col = m.col;
-    g.slot_ptr = m.slot_ptr;
-    g.slot_list = m.slot_list;
-    g.dir = m.dir;
-    g.stage = c.stage;
-    g.A = c.mat.A;
-    g.B = c.mat.B;
-    g.C = c.mat.C;
-    g.D = c.mat.D;
-    g.N = m.N;
-    g.nslots = m.nslots;
-    prof_begin(c, HYEL_K_GATHER, &ev);
-    (k_gather<<<blocks_for(m.nslots, 256), 256, 0, c.stream>>>(g), ::hyel::count_launch());
-    HYEL_CK(cudaGetLastError());
-    prof_end(c, HYEL_K_GATHER, ev, (double)m.E * 16 * (128.0 + 4.0) + (double)m.nnzb * 128.0);
+    if (tangent) {
+        GatherArgs g;
+        g.col_slice = m.col_slice;
+        g.slice_ptr = m.slice_ptr;
+        g.row_len = m.row_len;
+        g.col = m.col;
+        g.slot_ptr = m.slot_ptr;
+        g.slot_list = m.slot_list;
+        g.dir = m.dir;
+        g.stage = c.stage;
+        g.A = c.mat.A;
+        g.B = c.mat.B;
+        g.C = c.mat.C;
+        g.D = c.mat.D;
+        g.N = m.N;
+        g.nslots = m.nslots;
+        prof_begin(c, HYEL_K_GATHER, &ev);
+        (k_gather<<<blocks_for(m.nslots, 256), 256, 0, c.stream>>>(g), ::hyel::count_launch());
+        HYEL_CK(cudaGetLastError());
+        prof_end(c, HYEL_K_GATHER, ev, (double)m.E * 16 * (128.0 + 4.0) + (double)m.nnzb * 128.0);
+    }
 
     ResArgs r;
     r.node_ptr = m.node_ptr;
@@ -657,11 +664,14 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     r.partial = c.red + 64;
     r.counter = c.counter;
     r.norms = c.red;
+    r.use_g = (rhs_out && !tc.literal) ? 1 : 0;
     (k_residual<<<nb, 256, 0, c.stream>>>(r), ::hyel::count_launch());
     HYEL_CK(cudaGetLastError());
-    c.mat.assembled = true;
-    c.mat.scaled = false;
-    c.mat.transposed = false;
+    if (tangent) {
+        c.mat.assembled = true;
+        c.mat.scaled = false;
+        c.mat.transposed = false;
+    }
     HYEL_CK(cudaMemcpyAsync(c.h_red, c.red, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     HYEL_CK(cudaMemcpyAsync(c.h_err, c.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
     HYEL_CK(cudaStreamSynchronize(c.stream));

@@ -182,9 +182,10 @@ struct TimeConsts {
     int skip_corr = 0;  // R_k is zero up to rounding (after a corrector update): no K_{.,udot} R_k term
 };
 TimeConsts time_consts(const DeviceMesh &m, const hyel_time_params &tp);
-// Assembles residual, rhs, tangent; returns squared norms (host) when norms != nullptr.
+// Assembles residual, rhs, tangent; returns the norms (host) when norms != nullptr.
+// tangent = false: residual and norms only (no rhs, the matrix is left as it was).
 void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_out, double *rhs_out,
-              double *norms4);
+              double *norms4, bool tangent = true);
 void matrix_download(Ctx &c, int32_t *row_ptr, int32_t *col, double *A, double *B, double *C, double *D);
 
 // sparse.cu

@@ -473,8 +473,8 @@ __global__ void __launch_bounds__(kThreads) k_sumsq(const double *__restrict__ r
 //   P1  v_j = s u (s = 1/||u||, applied lazily), w = s A~ u (SELL-32 SpMV,
 //       gathering u), partial dots V_l . w and w . w  -> barrier, h1, ||w||
 //   test in the manner of Daniel, Gragg, Kaufman and Stewart: when
-//   ||w - V h1||, from Pythagoras, is at least eta ||w|| (kPgEta2), one
-//   classical Gram-Schmidt pass is kept:
+//   ||w - V h1||, from Pythagoras, is at least eta ||w|| (eta^2 = kPgEta2
+//   for loose solves, 1/2 otherwise), one classical Gram-Schmidt pass is kept:
 //   P2  w -= V h1; Givens and stopping test        -> barrier (w complete)
 //   otherwise the second pass follows (CGS2):
 //   P2  w -= V h1, partial dots V_l . w            -> barrier, h2
@@ -494,11 +494,15 @@ __global__ void __launch_bounds__(kThreads) k_sumsq(const double *__restrict__ r
 // abort word, every block then leaves, and the level state reports flag 8.
 
 constexpr int kPgThreads = 512;
-// eta^2 of the single-pass test: 1e-6 in FP64 (norm to ~4e-10, orthogonality
-// to ~2e-13), 1e-2 in FP32 (norm to ~1e-5, orthogonality to ~1e-6); the
-// A-solves stop at a relative residual of about 1e-2
+// eta^2 of the single-pass test for loose solves: 1e-6 in FP64 (norm to
+// ~4e-10, orthogonality to ~2e-13), 1e-2 in FP32 (norm to ~1e-5,
+// orthogonality to ~1e-6). Solves asked for rtol below kPgLoose<T> use the
+// classical 1/2 (eta = 1/sqrt(2)), where the basis stays orthogonal to
+// working precision.
 template <typename T>
 constexpr double kPgEta2 = sizeof(T) == 8 ? 1e-6 : 1e-2;
+template <typename T>
+constexpr double kPgLoose = sizeof(T) == 8 ? 1e-6 : 1e-3;
 constexpr unsigned long long kBarrierNs = 1000000000ull;
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -524,7 +528,8 @@ struct PgArgs {
     LevelState *st;
     int m, maxit;
     double rtol, atol;
-    double it_fixed, it_unit;  // algorithmic bytes per iteration: fixed + (4 (j+1) + 9) unit
+    double it_fixed, it_unit;  // algorithmic bytes per iteration: fixed + passes x unit
+    double eta2;               // single Gram-Schmidt pass when ||w - V h||^2 >= eta2 ||w||^2
 };
 
 // Barrier words, each on its own 128-byte line: arrivals (they only grow
@@ -845,7 +850,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
             double hh = 0.0;
             for (int l = 0; l <= j; l++) hh += s_col[l] * s_col[l];
             const double w2 = ww - hh;
-            s_fl[4] = (w2 >= kPgEta2<T> * ww) ? 0 : 1;
+            s_fl[4] = (w2 >= a.eta2 * ww) ? 0 : 1;
             s_sc[0] = w2;
         }
         __syncthreads();
@@ -1382,6 +1387,7 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
     a.maxit = P.maxit;
     a.rtol = P.rtol;
     a.atol = P.atol;
+    a.eta2 = P.rtol >= kPgLoose<T> ? kPgEta2<T> : 0.5;
     bool h16 = false;
     if constexpr (std::is_same<T, float>::value) {
         h16 = w.prec == HYEL_PREC_BF16S;
