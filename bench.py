@@ -216,10 +216,10 @@ def run_reference(args, rank, world):
 def run_hyel(args, rank, world, local_rank):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     from paper_1809_06350_gb300 import build as bld
     from paper_1809_06350_gb300 import hyel as H
+    from paper_1809_06350_gb300 import replicas
 
     bld.build()
     torch.cuda.set_device(local_rank)
@@ -260,8 +260,7 @@ def run_hyel(args, rank, world, local_rank):
         return its
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
 
     def timed(K, sp, host=None, profile=False):
         reset()
@@ -285,15 +284,7 @@ def run_hyel(args, rank, world, local_rank):
         prof = H.hyel_profile_read(ctx) if profile else None
         if profile:
             H.hyel_profile(ctx, 0)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-            it = torch.tensor([its], device="cuda", dtype=torch.float64)
-            dist.all_reduce(it, op=dist.ReduceOp.SUM)
-            its_total = int(it.item())
-        else:
-            its_total = its
+        ms, its_total = replicas.reduce_timing(ms, its, device="cuda")
         return ms, its, its_total, launches, prof
 
     graph = 0 if args.host_loops else 1
