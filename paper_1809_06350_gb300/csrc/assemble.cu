@@ -437,15 +437,38 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
 #pragma unroll
     for (int k = 0; k < 16; k++) acc[k] = 0.0;
     const int k0 = g.slot_ptr[q], k1 = g.slot_ptr[q + 1];
-    for (int k = k0; k < k1; k++) {
-        const int rec = g.slot_list[k];
+    auto rec_ptr = [&](int k) {
+        const int rec = __ldg(g.slot_list + k);
         const int64_t e = rec / kRecords;
         const int kk = rec - (int)e * kRecords;
-        const double2 *src =
-            reinterpret_cast<const double2 *>(g.stage + ((((e >> 5) * kRecords + kk) * 32 + (e & 31)) * kRecordDoubles));
+        return reinterpret_cast<const double2 *>(g.stage +
+                                                 ((((e >> 5) * kRecords + kk) * 32 + (e & 31)) * kRecordDoubles));
+    };
+    // two records in flight at a time, summed in ascending element order
+    int k = k0;
+    for (; k + 2 <= k1; k += 2) {
+        const double2 *s0 = rec_ptr(k), *s1 = rec_ptr(k + 1);
+        double2 v0[8], v1[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) v0[m] = __ldg(s0 + m);
+#pragma unroll
+        for (int m = 0; m < 8; m++) v1[m] = __ldg(s1 + m);
 #pragma unroll
         for (int m = 0; m < 8; m++) {
-            const double2 v = __ldg(src + m);
+            acc[2 * m] += v0[m].x;
+            acc[2 * m + 1] += v0[m].y;
+        }
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            acc[2 * m] += v1[m].x;
+            acc[2 * m + 1] += v1[m].y;
+        }
+    }
+    if (k < k1) {
+        const double2 *s0 = rec_ptr(k);
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            const double2 v = __ldg(s0 + m);
             acc[2 * m] += v.x;
             acc[2 * m + 1] += v.y;
         }

@@ -236,11 +236,13 @@ __global__ void __launch_bounds__(kThreads) k_multiaxpy(T *__restrict__ V, int64
 
 // Second CGS pass, norm of the new basis vector, Givens step on column j, the
 // stopping decision, and (when the cycle ends) y = R^-1 g.
+// single != 0: one classical pass (h2 holds the only coefficients, which
+// become the Hessenberg column); otherwise the second CGS2 pass (added to it).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_axpy_norm_givens(T *__restrict__ V, int64_t n,
                                                                const double *__restrict__ h2, double *partial,
                                                                unsigned *counter, double *H, double *cs, double *sn,
-                                                               double *g, double *y, LevelState *st) {
+                                                               double *g, double *y, LevelState *st, int single) {
     if (st->done) return;
     const int j = st->k, nk = j + 1, m = st->m;
     T *w = V + (int64_t)(j + 1) * n;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm_givens(T *__restrict__ V
     if (threadIdx.x == 0) partial[blockIdx.x] = tb;
     if (!last_block(counter)) return;
     double *Hc = H + (int64_t)j * (m + 1);
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) Hc[k] += h2[k];
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) Hc[k] = single ? h2[k] : Hc[k] + h2[k];
     __shared__ int s_done;
     __shared__ double tot;
     sum_partials(partial, 1, 1, &tot);
@@ -1329,6 +1331,10 @@ void gm_solve(Rec &R, Level<T> &L, LevelState *st, const hyel_krylov_level &P, c
               const std::function<void()> &prec_flex, const std::function<void()> &op) {
     Ctx &c = *R.c;
     const int m = std::min(P.restart, L.m);
+    // S-level solves as loose as the paper's (rtol >= kPgLoose) keep one
+    // classical Gram-Schmidt pass, as PETSc's default GMRES does; the outer
+    // FGMRES and tighter S-solves run CGS2
+    const int single = (KIND == 1 && P.rtol >= kPgLoose<T>) ? 1 : 0;
     // the operator of both looped levels is itself a solve: the host-driven
     // mode checks them every iteration
     R.loop(
@@ -1346,11 +1352,18 @@ void gm_solve(Rec &R, Level<T> &L, LevelState *st, const hyel_krylov_level &P, c
                 prec_flex();
             }
             op();
-            LAUNCH(k_multidot<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.partial, L.counter, L.H, L.h2, st, 1));
-            LAUNCH(k_multiaxpy<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.H, st));
-            LAUNCH(k_multidot<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.partial, L.counter, L.H, L.h2, st, 2));
+            if (single) {
+                LAUNCH(k_multidot<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.partial, L.counter, L.H, L.h2, st,
+                                                                         2));
+            } else {
+                LAUNCH(k_multidot<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.partial, L.counter, L.H, L.h2, st,
+                                                                         1));
+                LAUNCH(k_multiaxpy<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.H, st));
+                LAUNCH(k_multidot<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.partial, L.counter, L.H, L.h2, st,
+                                                                         2));
+            }
             LAUNCH(k_axpy_norm_givens<T><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.n, L.h2, L.partial, L.counter, L.H,
-                                                                            L.cs, L.sn, L.g, L.y, st));
+                                                                            L.cs, L.sn, L.g, L.y, st, single));
             LAUNCH(k_cycle_end<T, KIND><<<L.grid, kThreads, 0, c.stream>>>(L.V, L.Z, x, prec, L.n, L.y, L.cs, L.sn, L.g,
                                                                           L.counter, st, h));
         });
