@@ -424,8 +424,13 @@ struct GatherArgs {
     int64_t N, nslots;
 };
 
+// Eight lanes per slot: lane l sums components 2l and 2l+1 of the slot's
+// records (one 16-byte load per record), so one warp-wide load reads four
+// whole 128-byte records; every lane adds in ascending element order.
 __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t q = gt >> 3;
+    const int l = (int)(gt & 7);
     if (q >= g.nslots) return;
     const int64_t b = q >> 5;
     const int t = (int)(q & 31);
@@ -433,62 +438,39 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
     const int64_t r = (int64_t)s * 32 + t;
     if (r >= g.N) return;
     if (b - g.slice_ptr[s] >= g.row_len[r]) return;  // padding stays zero
-    double acc[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) acc[k] = 0.0;
+    double a0 = 0.0, a1 = 0.0;
     const int k0 = g.slot_ptr[q], k1 = g.slot_ptr[q + 1];
-    auto rec_ptr = [&](int k) {
+    for (int k = k0; k < k1; k++) {
         const int rec = __ldg(g.slot_list + k);
         const int64_t e = rec / kRecords;
         const int kk = rec - (int)e * kRecords;
-        return reinterpret_cast<const double2 *>(g.stage +
-                                                 ((((e >> 5) * kRecords + kk) * 32 + (e & 31)) * kRecordDoubles));
-    };
-    // two records in flight at a time, summed in ascending element order
-    int k = k0;
-    for (; k + 2 <= k1; k += 2) {
-        const double2 *s0 = rec_ptr(k), *s1 = rec_ptr(k + 1);
-        double2 v0[8], v1[8];
-#pragma unroll
-        for (int m = 0; m < 8; m++) v0[m] = __ldg(s0 + m);
-#pragma unroll
-        for (int m = 0; m < 8; m++) v1[m] = __ldg(s1 + m);
-#pragma unroll
-        for (int m = 0; m < 8; m++) {
-            acc[2 * m] += v0[m].x;
-            acc[2 * m + 1] += v0[m].y;
-        }
-#pragma unroll
-        for (int m = 0; m < 8; m++) {
-            acc[2 * m] += v1[m].x;
-            acc[2 * m + 1] += v1[m].y;
-        }
-    }
-    if (k < k1) {
-        const double2 *s0 = rec_ptr(k);
-#pragma unroll
-        for (int m = 0; m < 8; m++) {
-            const double2 v = __ldg(s0 + m);
-            acc[2 * m] += v.x;
-            acc[2 * m + 1] += v.y;
-        }
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(
+                                    g.stage + ((((e >> 5) * kRecords + kk) * 32 + (e & 31)) * kRecordDoubles)) +
+                                l);
+        a0 += v.x;
+        a1 += v.y;
     }
     const int c = g.col[q];
     const unsigned dr = g.dir[r], dc = g.dir[c];
+    const double val[2] = {a0, a1};
 #pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            double val = acc[3 * i + j];
-            if (((dr >> i) & 1u) || ((dc >> j) & 1u)) val = (r == c && i == j) ? 1.0 : 0.0;
-            g.A[(b * 9 + 3 * i + j) * 32 + t] = val;
+    for (int h = 0; h < 2; h++) {
+        const int comp = 2 * l + h;  // 0..8 A (row-major), 9..11 B, 12..14 C, 15 D
+        if (comp < 9) {
+            const int i = comp / 3, j = comp % 3;
+            double v = val[h];
+            if (((dr >> i) & 1u) || ((dc >> j) & 1u)) v = (r == c && i == j) ? 1.0 : 0.0;
+            g.A[(b * 9 + comp) * 32 + t] = v;
+        } else if (comp < 12) {
+            const int i = comp - 9;
+            g.B[(b * 3 + i) * 32 + t] = ((dr >> i) & 1u) ? 0.0 : val[h];
+        } else if (comp < 15) {
+            const int i = comp - 12;
+            g.C[(b * 3 + i) * 32 + t] = ((dc >> i) & 1u) ? 0.0 : val[h];
+        } else {
+            g.D[b * 32 + t] = val[h];
         }
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        g.B[(b * 3 + i) * 32 + t] = ((dr >> i) & 1u) ? 0.0 : acc[9 + i];
-        g.C[(b * 3 + i) * 32 + t] = ((dc >> i) & 1u) ? 0.0 : acc[12 + i];
     }
-    g.D[b * 32 + t] = acc[15];
 }
 
 // ---- nodal residual gather, traction, Dirichlet, rhs and squared norms
@@ -665,7 +647,7 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
         g.N = m.N;
         g.nslots = m.nslots;
         prof_begin(c, HYEL_K_GATHER, &ev);
-        (k_gather<<<blocks_for(m.nslots, 256), 256, 0, c.stream>>>(g), ::hyel::count_launch());
+        (k_gather<<<blocks_for(8 * m.nslots, 256), 256, 0, c.stream>>>(g), ::hyel::count_launch());
         HYEL_CK(cudaGetLastError());
         prof_end(c, HYEL_K_GATHER, ev, (double)m.E * 16 * (128.0 + 4.0) + (double)m.nnzb * 128.0);
     }
