@@ -152,11 +152,22 @@ typedef struct {
  * iterates. Every A-solve (intermediate and inner) is one cooperative launch
  * of a persistent GMRES kernel on A M^-1 (M the 3x3 block diagonal of A) in
  * both modes. check_every (>= 1) is validated and otherwise unused. */
+/* Preconditioner of the A-solves (intermediate and inner):
+ * HYEL_APREC_BJACOBI: 3x3 block-Jacobi, folded into the operator (A M^-1) of a
+ *   persistent GMRES kernel (the default);
+ * HYEL_APREC_AMG: one V-cycle of aggregation multigrid (the stand-in for the
+ *   paper's algebraic multigrid, §4.4): unsmoothed-aggregation Galerkin levels
+ *   with 3x3 blocks, damped block-Jacobi smoothing, as the right preconditioner
+ *   of an FGMRES A-level. The hierarchy's pattern is built once per mesh, its
+ *   operators once per assembly (after the scaling). */
+enum { HYEL_APREC_BJACOBI = 0, HYEL_APREC_AMG = 1 };
+
 typedef struct {
     hyel_krylov_level outer, a, s, inner;
     int32_t precision;      /* HYEL_PREC_* */
     int32_t check_every;
     int32_t graph;
+    int32_t a_precond;      /* HYEL_APREC_* */
 } hyel_solver_params;
 
 typedef struct {

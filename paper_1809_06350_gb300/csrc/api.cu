@@ -157,6 +157,7 @@ int hyel_destroy(hyel_ctx *ctx) {
     cudaSetDevice(ctx->c.device);
     cudaStreamSynchronize(ctx->c.stream);
     hyel::free_workspace(ctx->c);
+    hyel::amg_free(ctx->c);
     hyel::dfree_all(ctx->c);
     for (auto &r : ctx->c.prof.pending) {
         cudaEventDestroy(r.a);

@@ -108,6 +108,7 @@ struct DeviceMatrix {
     double *At = nullptr, *Bt = nullptr, *Ct = nullptr, *Dt = nullptr;
     bool assembled = false;
     bool scaled = false;
+    bool amg_ready = false;   // multigrid operators built from the current scaled A
     bool transposed = false;  // At..Dt hold the transpose of the current assembly
 };
 
@@ -134,6 +135,7 @@ struct Profile {
 };
 
 struct Workspace;  // Krylov workspaces (solver.cu)
+struct Amg;        // multigrid hierarchy of the A-solves (amg.cu)
 
 struct Ctx {
     int device = 0;
@@ -149,6 +151,7 @@ struct Ctx {
     unsigned *h_err = nullptr;   // pinned mirror
     double *h_red = nullptr;     // pinned scalars
     Workspace *ws = nullptr;
+    Amg *amg = nullptr;
     Profile prof;
     size_t bytes_held = 0;
     int num_sms = 152;
@@ -187,6 +190,13 @@ TimeConsts time_consts(const DeviceMesh &m, const hyel_time_params &tp);
 void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_out, double *rhs_out,
               double *norms4, bool tangent = true);
 void matrix_download(Ctx &c, int32_t *row_ptr, int32_t *col, double *A, double *B, double *C, double *D);
+
+// amg.cu
+void amg_free(Ctx &c);
+void amg_numeric(Ctx &c);  // builds the hierarchy on first use, then the level operators
+int amg_levels(const Ctx &c, int64_t *sizes, int max);
+template <typename T>
+void amg_apply(Ctx &c, const T *v, T *z);  // z = V-cycle(v), [3N]
 
 // sparse.cu
 void solve_setup(Ctx &c);

@@ -46,6 +46,7 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
 
     // release the previous mesh and everything sized by it
     free_workspace(c);
+    amg_free(c);
     dfree_all(c);
     c.mesh = DeviceMesh();
     c.mat = DeviceMatrix();
@@ -387,6 +388,7 @@ void mesh_upload(Ctx &c, int64_t N, const double *X, int64_t E, const int32_t *t
     } catch (...) {
         // leave the context empty (no mesh) rather than half-built
         free_workspace(c);
+        amg_free(c);
         dfree_all(c);
         c.mesh = DeviceMesh();
         c.mat = DeviceMatrix();

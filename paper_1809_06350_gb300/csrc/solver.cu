@@ -1157,10 +1157,12 @@ struct Level {
 }  // namespace
 
 struct Workspace {
-    int m_outer = 0, m_a = 0, m_s = 0, prec = -1;
+    int m_outer = 0, m_a = 0, m_s = 0, prec = -1, a_amg = 0;
     Level<double> outer;
     Level<double> a64, s64;
     Level<float> a32, s32;
+    Level<double> am64;  // FGMRES A-level with the multigrid preconditioner
+    Level<float> am32;
     LevelState *states = nullptr;  // [5]: outer, a1, a2, s, inner
     LevelState *h_states = nullptr;
     double *d = nullptr;  // 12 x 4N doubles
@@ -1250,7 +1252,9 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
 Workspace &workspace(Ctx &c, const hyel_solver_params &p) {
     const int mo = p.outer.restart, ma = std::max(p.a.restart, p.inner.restart), ms = p.s.restart;
     Workspace *w = c.ws;
-    if (w && w->m_outer >= mo && w->m_a >= ma && w->m_s >= ms && w->prec == p.precision) return *w;
+    if (w && w->m_outer >= mo && w->m_a >= ma && w->m_s >= ms && w->prec == p.precision &&
+        w->a_amg == (p.a_precond == HYEL_APREC_AMG))
+        return *w;
     free_workspace(c);
     w = new Workspace();
     c.ws = w;
@@ -1259,12 +1263,19 @@ Workspace &workspace(Ctx &c, const hyel_solver_params &p) {
     w->m_a = ma;
     w->m_s = ms;
     w->prec = p.precision;
+    w->a_amg = p.a_precond == HYEL_APREC_AMG;
     level_init(c, *w, w->outer, 4 * N, mo, 2);
     if (p.precision == HYEL_PREC_FP64) {
-        level_init(c, *w, w->a64, 3 * N, ma, 0);
+        if (w->a_amg)
+            level_init(c, *w, w->am64, 3 * N, ma, 2);
+        else
+            level_init(c, *w, w->a64, 3 * N, ma, 0);
         level_init(c, *w, w->s64, N, ms, 1);
     } else {
-        level_init(c, *w, w->a32, 3 * N, ma, 0);
+        if (w->a_amg)
+            level_init(c, *w, w->am32, 3 * N, ma, 2);
+        else
+            level_init(c, *w, w->a32, 3 * N, ma, 0);
         level_init(c, *w, w->s32, N, ms, 1);
     }
     w->states = (LevelState *)walloc(c, *w, sizeof(LevelState) * 5);
@@ -1285,6 +1296,8 @@ void check_params(const hyel_solver_params &p) {
     if (p.precision != HYEL_PREC_FP64 && p.precision != HYEL_PREC_FP32 && p.precision != HYEL_PREC_BF16S)
         fail(HYEL_EINVAL, "solver params: bad precision");
     if (p.check_every < 1) fail(HYEL_EINVAL, "solver params: check_every must be >= 1");
+    if (p.a_precond != HYEL_APREC_BJACOBI && p.a_precond != HYEL_APREC_AMG)
+        fail(HYEL_EINVAL, "solver params: bad a_precond");
 }
 
 bool same_params(const hyel_solver_params &a, const hyel_solver_params &b) {
@@ -1303,6 +1316,7 @@ struct Sys<double> {
     static const double *jac(Ctx &c) { return c.mat.jac64; }
     static const double *shat(Ctx &c) { return c.mat.shat64; }
     static Level<double> &la(Workspace &w) { return w.a64; }
+    static Level<double> &lam(Workspace &w) { return w.am64; }
     static Level<double> &ls(Workspace &w) { return w.s64; }
     static double *vec(Workspace &w, int k, int64_t N) { return w.d + (size_t)k * 4 * N; }
 };
@@ -1315,6 +1329,7 @@ struct Sys<float> {
     static const float *jac(Ctx &c) { return c.mat.jac32; }
     static const float *shat(Ctx &c) { return c.mat.shat32; }
     static Level<float> &la(Workspace &w) { return w.a32; }
+    static Level<float> &lam(Workspace &w) { return w.am32; }
     static Level<float> &ls(Workspace &w) { return w.s32; }
     static float *vec(Workspace &w, int k, int64_t N) { return w.f + (size_t)k * 4 * N; }
 };
@@ -1328,13 +1343,13 @@ enum { ST_OUTER = 0, ST_A1 = 1, ST_A2 = 2, ST_S = 3, ST_INNER = 4 };
 // (z, or Z_k for KIND 2) to V_{k+1}.
 template <typename T, int KIND>
 void gm_solve(Rec &R, Level<T> &L, LevelState *st, const hyel_krylov_level &P, const T *b, T *x, const T *prec,
-              const std::function<void()> &prec_flex, const std::function<void()> &op) {
+              const std::function<void()> &prec_flex, const std::function<void()> &op, bool loose_single) {
     Ctx &c = *R.c;
     const int m = std::min(P.restart, L.m);
-    // S-level solves as loose as the paper's (rtol >= kPgLoose) keep one
-    // classical Gram-Schmidt pass, as PETSc's default GMRES does; the outer
-    // FGMRES and tighter S-solves run CGS2
-    const int single = (KIND == 1 && P.rtol >= kPgLoose<T>) ? 1 : 0;
+    // S-level and multigrid A-level solves as loose as the paper's (rtol >=
+    // kPgLoose) keep one classical Gram-Schmidt pass, as PETSc's default GMRES
+    // does; the outer FGMRES and tighter solves run CGS2
+    const int single = (loose_single && P.rtol >= kPgLoose<T>) ? 1 : 0;
     // the operator of both looped levels is itself a solve: the host-driven
     // mode checks them every iteration
     R.loop(
@@ -1374,6 +1389,22 @@ void gm_solve(Rec &R, Level<T> &L, LevelState *st, const hyel_krylov_level &P, c
 template <typename T>
 void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, const T *b, T *x) {
     Ctx &c = *R.c;
+    if (w.a_amg) {
+        // FGMRES on A with one multigrid V-cycle as the right preconditioner:
+        // V_k -> (V-cycle) -> Z_k, A Z_k -> V_{k+1}, x = Z y
+        Level<T> &L = Sys<T>::lam(w);
+        const int64_t N = c.mesh.N, n = 3 * N;
+        T *vin = Sys<T>::vec(w, 3, N), *zout = Sys<T>::vec(w, 11, N);
+        gm_solve<T, 2>(
+            R, L, st, P, b, x, nullptr,
+            [&]() {
+                LAUNCH(k_copy_ind<T, T><<<blocks_for(n, 256), 256, 0, c.stream>>>(L.V, vin, n, st, n, 0));
+                amg_apply<T>(c, vin, zout);
+                LAUNCH(k_copy_ind<T, T><<<blocks_for(n, 256), 256, 0, c.stream>>>(zout, L.Z, n, st, 0, n));
+            },
+            [&]() { spmv_A_ind<T>(c, Sys<T>::A(c), zout, L.V, L.n, &st->k); }, true);
+        return;
+    }
     Level<T> &L = Sys<T>::la(w);
     const DeviceMesh &msh = c.mesh;
     const DeviceMatrix &M = c.mat;
@@ -1467,7 +1498,7 @@ void pscr(Rec &R, Workspace &w, const hyel_solver_params &p, const T *rv, const 
     Level<T> &Ls = Sys<T>::ls(w);
     LevelState *sst = w.states + ST_S;
     gm_solve<T, 1>(R, Ls, sst, p.s, rp2, xp, Sys<T>::shat(c), nullptr,
-                   [&]() { schur_op<T>(R, w, p, Ls.z, Ls.V, &sst->k, Ls.n); });
+                   [&]() { schur_op<T>(R, w, p, Ls.z, Ls.V, &sst->k, Ls.n); }, true);
     // 4: r_v <- r_v - B x_p
     spmv_B<T>(c, Sys<T>::B(c), xp, rv2, rv);
     // 5: A x_v = r_v
@@ -1494,7 +1525,7 @@ void outer_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const double
         }
     };
     auto op = [&]() { spmv_full64_ind(c, c.mat.As, c.mat.Bs, c.mat.Cs, c.mat.Ds, L.Z, L.V, n, &st->k); };
-    gm_solve<double, 2>(R, L, st, p.outer, b, xs, nullptr, prec, op);
+    gm_solve<double, 2>(R, L, st, p.outer, b, xs, nullptr, prec, op, false);
 }
 
 double seconds_since(std::chrono::steady_clock::time_point t0) {
@@ -1574,6 +1605,10 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
     if (!c.mat.assembled) fail(HYEL_ESTATE, "solve: nothing assembled");
     auto t0 = std::chrono::steady_clock::now();
     solve_setup(c);
+    if (p.a_precond == HYEL_APREC_AMG && !c.mat.amg_ready) {
+        amg_numeric(c);
+        c.mat.amg_ready = true;
+    }
     Workspace &w = workspace(c, p);
     if (p.graph) ensure_graph(c, w, p);
     HYEL_CK(cudaStreamSynchronize(c.stream));
@@ -1650,6 +1685,10 @@ void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y
     check_params(p);
     if (!c.mat.assembled) fail(HYEL_ESTATE, "schur_apply: nothing assembled");
     solve_setup(c);
+    if (p.a_precond == HYEL_APREC_AMG && !c.mat.amg_ready) {
+        amg_numeric(c);
+        c.mat.amg_ready = true;
+    }
     Workspace &w = workspace(c, p);
     const int64_t N = c.mesh.N;
     HYEL_CK(cudaMemsetAsync(w.states, 0, sizeof(LevelState) * 5, c.stream));

@@ -525,6 +525,7 @@ void solve_setup(Ctx &c) {
     HYEL_CK(cudaStreamSynchronize(c.stream));
     if (*c.h_err & ERR_SINGULAR) fail(HYEL_ESINGULAR, "solve_setup: a 3x3 diagonal block of A is singular");
     c.mat.scaled = true;
+    c.mat.amg_ready = false;
 }
 
 void transpose_assembled(Ctx &c) {

@@ -20,6 +20,7 @@ HYEL_EINVAL, HYEL_ECUDA, HYEL_ENOMEM, HYEL_ENOCONV = -1, -2, -3, -4
 HYEL_EBREAKDOWN, HYEL_ENAN, HYEL_EINVERTED, HYEL_ESINGULAR, HYEL_ESTATE = -5, -6, -7, -8, -9
 HYEL_VOL_GIBBS, HYEL_VOL_INCOMPRESSIBLE = 0, 1
 HYEL_PREC_FP64, HYEL_PREC_FP32, HYEL_PREC_BF16S = 0, 1, 2
+HYEL_APREC_BJACOBI, HYEL_APREC_AMG = 0, 1
 HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D, HYEL_OP_AM = 0, 1, 2, 3, 4, 5
 HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32, HYEL_MAT_TRANSPOSED, HYEL_MAT_SCALED_BF16S = 0, 1, 2, 3, 4
 (HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER, HYEL_K_SPMV_A16,
@@ -69,7 +70,7 @@ class HyelKrylovLevel(C.Structure):
 class HyelSolverParams(C.Structure):
     _fields_ = [("outer", HyelKrylovLevel), ("a", HyelKrylovLevel), ("s", HyelKrylovLevel),
                 ("inner", HyelKrylovLevel), ("precision", C.c_int32), ("check_every", C.c_int32),
-                ("graph", C.c_int32)]
+                ("graph", C.c_int32), ("a_precond", C.c_int32)]
 
 
 class HyelSolveStats(C.Structure):
@@ -305,12 +306,14 @@ def level(rtol, maxit, restart, atol=1e-50):
 
 
 def solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=HYEL_PREC_FP64, outer=(200, 200),
-                  a=(500, 500), s=(200, 200), inner=(500, 500), check_every=4, inner_rtol=None, graph=1):
+                  a=(500, 500), s=(200, 200), inner=(500, 500), check_every=4, inner_rtol=None, graph=1,
+                  a_precond=0):
     """Solver controls with the paper's defaults (§5: FGMRES(200), A: GMRES(500),
-    S: GMRES(200), inner GMRES(500), absolute tolerances 1e-50)."""
+    S: GMRES(200), inner GMRES(500), absolute tolerances 1e-50). a_precond:
+    HYEL_APREC_BJACOBI (default) or HYEL_APREC_AMG."""
     ir = sub_rtol if inner_rtol is None else inner_rtol
     return HyelSolverParams(level(outer_rtol, *outer), level(sub_rtol, *a), level(sub_rtol, *s),
-                            level(ir, *inner), precision, check_every, graph)
+                            level(ir, *inner), precision, check_every, graph, a_precond)
 
 
 def time_params(dt=1e-3, t_n=0.0, rho_inf=0.5, tol_r=1e-6, tol_a=1e-6, l_max=20, rhs_literal=0):
