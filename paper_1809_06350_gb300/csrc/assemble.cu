@@ -52,11 +52,6 @@ __device__ __forceinline__ double *record(double *stage, int64_t e, int k) {
     return stage + ((((e >> 5) * kRecords + k) * 32 + (e & 31)) * kRecordDoubles);
 }
 
-// sum_q X_q N_qA N_qB for the 4-point rule, given X at the point nearest each
-// node (X[A]) and the total S = sum_q X_q.
-__device__ __forceinline__ double qpair(const double *X, double S, int A, int B) {
-    return A == B ? QAA_BB * X[A] + QBB * S : QAB_BB * (X[A] + X[B]) + QBB * S;
-}
 __device__ __forceinline__ double qone(const double *X, double S, int A) { return QAB * X[A] + QB * S; }
 
 // TAN: also the tangent blocks; CORR: also the K_{.,udot} R_k right-hand-side
@@ -304,6 +299,21 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
     double Spc[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) Spc[i] = c1 * W * Srp[i];
+    // pair integrals split per node: sum_q X_q N_qA N_qB = d[A] (A = B) or
+    // o[A] + o[B] (A != B), with d = QAA_BB X + QBB S, o = QAB_BB X + QBB S / 2
+    double dm[4], om[4], ddw[4], odw[4], dpc[3][4], opc[3][4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        dm[q] = QAA_BB * xm[q] + QBB * Sm;
+        om[q] = QAB_BB * xm[q] + 0.5 * QBB * Sm;
+        ddw[q] = QAA_BB * xdw[q] + QBB * Sdw;
+        odw[q] = QAB_BB * xdw[q] + 0.5 * QBB * Sdw;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            dpc[i][q] = QAA_BB * xpc[i][q] + QBB * Spc[i];
+            opc[i][q] = QAB_BB * xpc[i][q] + 0.5 * QBB * Spc[i];
+        }
+    }
     const double jv4c1 = c1 * JV4;
     // C^j_AB = cAs_A n_Bj + cBs_B n_Aj - LvTnc_Bj - gpc_j nn
     //   cAs_A = c2 (W rb_A + JV/4 div v + tau n_A.sigma) + c1 JV/4,
@@ -335,6 +345,12 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
             w0c[tf] = c2 * 2.0 * V * fd1[tf] * aJ;
         }
     }
+    double q3n[4][3];  // q3 n_A (times c2)
+#pragma unroll
+    for (int A = 0; A < 4; A++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) q3n[A][j] = q3 * n[A][j];
+    const double c2jv4 = c2 * JV4;
     double corr[4][4];
 #pragma unroll
     for (int A = 0; A < 4; A++)
@@ -349,12 +365,14 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
             const double gg = g[A][0] * g[B][0] + g[A][1] * g[B][1] + g[A][2] * g[B][2];
             const double nn = n[A][0] * n[B][0] + n[A][1] * n[B][1] + n[A][2] * n[B][2];
             // A block: c2 A_u + a_m (mass) on the diagonal
-            const double dg = q4 * gg + qpair(xm, Sm, A, B);
+            const bool same = A == B;
+            const double mass = same ? dm[A] : om[A] + om[B];
+            const double dg = fma(q4, gg, mass);
 #pragma unroll
             for (int i = 0; i < 3; i++)
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    double s = Q1[A][i] * n[B][j] + Q2[A][i] * f[B][j] + q3 * n[A][j] * n[B][i];
+                    double s = fma(Q1[A][i], n[B][j], fma(Q2[A][i], f[B][j], q3n[A][j] * n[B][i]));
                     if (i == j) s += dg;
                     out[3 * i + j] = s;
                 }
@@ -376,17 +394,19 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
             }
             // B^i_AB = c1 (int rho_,p J (vdot_i - b_i) N_A N_B - J N_A,i V/4)
 #pragma unroll
-            for (int i = 0; i < 3; i++) out[9 + i] = qpair(xpc[i], Spc[i], A, B) - jv4c1 * n[A][i];
+            for (int i = 0; i < 3; i++) out[9 + i] = fma(-jv4c1, n[A][i], same ? dpc[i][A] : opc[i][A] + opc[i][B]);
 #pragma unroll
-            for (int j = 0; j < 3; j++) out[12 + j] = cAs[A] * n[B][j] + cBs[B] * n[A][j] - c2 * JV4 * LvTn[B][j] - gpc[j] * nn;
-            out[15] = qpair(xdw, Sdw, A, B) + c1tJV * nn + n[A][0] * qrc[B][0] + n[A][1] * qrc[B][1] + n[A][2] * qrc[B][2];
+            for (int j = 0; j < 3; j++)
+                out[12 + j] = fma(cAs[A], n[B][j], fma(cBs[B], n[A][j], fma(-c2jv4, LvTn[B][j], -gpc[j] * nn)));
+            out[15] = fma(c1tJV, nn, same ? ddw[A] : odw[A] + odw[B]) +
+                      fma(n[A][0], qrc[B][0], fma(n[A][1], qrc[B][1], n[A][2] * qrc[B][2]));
             if (CORR) {
                 // c2 A_u R_k (the A block less its mass part) and C_u R_k
 #pragma unroll
                 for (int i = 0; i < 3; i++) {
                     double s = 0.0;
 #pragma unroll
-                    for (int j = 0; j < 3; j++) s += (out[3 * i + j] - (i == j ? qpair(xm, Sm, A, B) : 0.0)) * rk[B][j];
+                    for (int j = 0; j < 3; j++) s += (out[3 * i + j] - (i == j ? mass : 0.0)) * rk[B][j];
                     corr[A][i] += s;
                 }
                 double sp = 0.0;
