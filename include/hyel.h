@@ -328,13 +328,14 @@ int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solv
 
 /* Kernel classes timed with CUDA events on the context's stream when enabled
  * (launches made while a solve runs as a CUDA graph are not timed).
- * HYEL_K_GMRES_A is the persistent A-solve kernel (one launch per A-solve);
- * its algorithmic bytes are counted per iteration j as the A M^-1 values and
- * indices plus 4 (j+1) + 9 passes over 3N-vectors, and are added when the
- * solve that launched it returns. */
+ * HYEL_K_GMRES_A is the persistent A-solve kernel (one launch per
+ * intermediate A-solve), HYEL_K_GMRES_S the persistent S-solve kernel (one
+ * launch per S-solve, its inner A-solves included); their algorithmic bytes
+ * are counted on the device per iteration (the operator's values and indices
+ * plus the passes over the Krylov vectors) and added when the solve returns. */
 enum { HYEL_K_SPMV_A64 = 0, HYEL_K_SPMV_A32 = 1, HYEL_K_SPMV_FULL64 = 2,
        HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_SPMV_A16 = 5, HYEL_K_GMRES_A = 6,
-       HYEL_K_NCLASSES = 7 };
+       HYEL_K_GMRES_S = 7, HYEL_K_NCLASSES = 8 };
 
 /* enable != 0 starts event timing of the kernel classes (and clears the
  * totals); 0 stops it. */

@@ -513,6 +513,23 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// One persistent GMRES level: vectors of NC values per node
+template <typename T>
+struct GmArgs {
+    int64_t N;                 // nodes
+    const T *b;
+    T *x, *V, *U0, *U1;
+    double *H;                 // rotated Hessenberg columns (written by block 0)
+    double *partial;           // 2 x [m + 1][grid], by barrier parity
+    unsigned *bar;             // barrier words (arrivals, release, abort), shared by nested levels
+    LevelState *st;
+    int m, maxit;
+    double rtol, atol;
+    double it_fixed, it_unit;  // algorithmic bytes per iteration: fixed + passes x unit
+    double eta2;               // single Gram-Schmidt pass when ||w - V h||^2 >= eta2 ||w||^2
+};
+
+// The A-solve: GMRES on A M^-1 (3 values per node)
 template <typename T>
 struct PgArgs {
     const int32_t *slice_ptr, *row_len, *col;
@@ -521,17 +538,16 @@ struct PgArgs {
     const uint16_t *Am1;
     const float *Ams;
     const T *jac;                             // [9][N] M^-1
-    int64_t N;                                // nodes (vectors have 3N entries)
-    const T *b;
-    T *x, *V, *U0, *U1;
-    double *H;                                // rotated Hessenberg columns (written by block 0)
-    double *partial;                          // 2 x [m + 1][grid], by barrier parity
-    unsigned *bar;                            // barrier words (arrivals, generation, abort)
-    LevelState *st;
-    int m, maxit;
-    double rtol, atol;
-    double it_fixed, it_unit;  // algorithmic bytes per iteration: fixed + passes x unit
-    double eta2;               // single Gram-Schmidt pass when ||w - V h||^2 >= eta2 ||w||^2
+    GmArgs<T> g;
+};
+
+// The S-solve: GMRES on S diag(S^)^-1 (1 value per node), S z = D z - C A^-1 B z
+template <typename T>
+struct SgArgs {
+    const int32_t *slice_ptr, *row_len, *col;
+    const T *B, *C, *D, *shat;
+    T *xbar, *xtil;  // [3N] right-hand side and solution of the inner A-solve
+    GmArgs<T> g;
 };
 
 // Barrier words, each on its own 128-byte line: arrivals (they only grow
@@ -640,11 +656,11 @@ __device__ __forceinline__ double pg_block_sum(T v, double *red) {
 // Partial dots V_l . w (l < nv), and w . w as column nv when self, of this
 // block's nodes into partial[l][block]; sums within a warp in T, across the
 // block's warps in double.
-template <typename T>
+template <typename T, int NC>
 __device__ void pg_dots(const T *V, const T *w, int64_t N, int nv, bool self, double *partial) {
     __shared__ double red[kPgThreads / 32][KC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t n = 3 * N;
+    const int64_t n = NC * N;
     const int nk = nv + (self ? 1 : 0);
     for (int k0 = 0; k0 < nk; k0 += KC) {
         const int kc = min(KC, nk - k0);
@@ -652,12 +668,15 @@ __device__ void pg_dots(const T *V, const T *w, int64_t N, int nv, bool self, do
 #pragma unroll
         for (int c = 0; c < KC; c++) acc[c] = 0;
         PG_FOR_OWN_NODES(N, i) {
-            const T w0 = w[3 * i], w1 = w[3 * i + 1], w2 = w[3 * i + 2];
+            T wi[NC];
+#pragma unroll
+            for (int r = 0; r < NC; r++) wi[r] = w[NC * i + r];
 #pragma unroll
             for (int c = 0; c < KC; c++)
                 if (c < kc) {
-                    const T *v = k0 + c < nv ? V + (int64_t)(k0 + c) * n + 3 * i : w + 3 * i;
-                    acc[c] = fma(v[0], w0, fma(v[1], w1, fma(v[2], w2, acc[c])));
+                    const T *v = k0 + c < nv ? V + (int64_t)(k0 + c) * n + NC * i : w + NC * i;
+#pragma unroll
+                    for (int r = NC - 1; r >= 0; r--) acc[c] = fma(v[r], wi[r], acc[c]);
                 }
         }
         if (kc == 1) {
@@ -680,23 +699,25 @@ __device__ void pg_dots(const T *V, const T *w, int64_t N, int nv, bool self, do
 
 // w -= V h (h in shared memory, l < nk) on this block's nodes; returns sum w^2
 // (accumulated in T per thread)
-template <typename T>
+template <typename T, int NC>
 __device__ T pg_axpy(const T *V, T *w, int64_t N, int nk, const T *h) {
-    const int64_t n = 3 * N;
+    const int64_t n = NC * N;
     T ss = 0;
     PG_FOR_OWN_NODES(N, i) {
-        T w0 = w[3 * i], w1 = w[3 * i + 1], w2 = w[3 * i + 2];
+        T wi[NC];
+#pragma unroll
+        for (int r = 0; r < NC; r++) wi[r] = w[NC * i + r];
         for (int l = 0; l < nk; l++) {
-            const T *v = V + (int64_t)l * n + 3 * i;
+            const T *v = V + (int64_t)l * n + NC * i;
             const T hl = h[l];
-            w0 = fma(-v[0], hl, w0);
-            w1 = fma(-v[1], hl, w1);
-            w2 = fma(-v[2], hl, w2);
+#pragma unroll
+            for (int r = 0; r < NC; r++) wi[r] = fma(-v[r], hl, wi[r]);
         }
-        w[3 * i] = w0;
-        w[3 * i + 1] = w1;
-        w[3 * i + 2] = w2;
-        ss = fma(w0, w0, fma(w1, w1, fma(w2, w2, ss)));
+#pragma unroll
+        for (int r = NC - 1; r >= 0; r--) {
+            w[NC * i + r] = wi[r];
+            ss = fma(wi[r], wi[r], ss);
+        }
     }
     return ss;
 }
@@ -746,19 +767,23 @@ __device__ __forceinline__ void pg_row(const PgArgs<T> &a, int64_t i, const T *u
     y2 = a2;
 }
 
-template <typename T, bool H16>
-__global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
+// One GMRES solve on the calling grid (all blocks of a cooperative launch),
+// NC values per node. op(u, s, w, phase) sets w = Op(s u) on the block's
+// nodes (it may run grid barriers of its own, in every block alike);
+// xupd(i, u) adds the preconditioned u = (V y)_i to x_i. phase counts the grid
+// barriers passed so far. false: a barrier gave up.
+template <typename T, int NC, typename Op, typename XUpd>
+__device__ bool pg_gmres(const GmArgs<T> &a, unsigned &phase, Op &&op, XUpd &&xupd) {
     // per-block copies of the small GMRES state (identical in every block)
     __shared__ double s_cs[kMaxK], s_sn[kMaxK], s_g[kMaxK + 1], s_col[kMaxK + 2], s_tmp[kMaxK + 2];
     __shared__ T hs[kMaxK + 2];
     __shared__ double s_sc[4];  // 0: squared norm, 1: next scale, 2: 1 / h_{j+1,j}, 3: tol
     __shared__ int s_fl[5];     // 0: done, 1: stop, 2: y usable, 3: total iterations, 4: second pass
-    const int64_t N = a.N, n = 3 * N;
+    const int64_t N = a.N, n = NC * N;
     const int m = a.m;
     const int G = gridDim.x;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;  // writes the level state and H
     LevelState *st = a.st;
-    unsigned phase = 0u;  // barriers passed; the barrier words are cleared before every launch
     auto pbuf = [&](unsigned ph) { return a.partial + (size_t)(ph & 1u) * G * (m + 1); };
 
     auto abort_out = [&]() {
@@ -767,6 +792,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
             atomicOr(&st->status_any, 8);
             st->stop = 1;
         }
+        return false;
     };
 
     // ---- start: x = 0, beta = ||b||
@@ -774,9 +800,9 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
         T ss = 0;
         PG_FOR_OWN_NODES(N, i)
 #pragma unroll
-            for (int r = 0; r < 3; r++) {
-                const T v = a.b[3 * i + r];
-                a.x[3 * i + r] = 0;
+            for (int r = 0; r < NC; r++) {
+                const T v = a.b[NC * i + r];
+                a.x[NC * i + r] = 0;
                 ss = fma(v, v, ss);
             }
         __shared__ double red1[kPgThreads / 32];
@@ -821,7 +847,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
         }
     }
     __syncthreads();
-    if (s_fl[1]) return;
+    if (s_fl[1]) return true;
 
     const T *uin = a.b;
     T *uout = a.U0;
@@ -830,17 +856,11 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
     for (;;) {
         // ---- P1: v_j = s u; w = s A~ u; dots with V_0..V_j
         T *Vj = a.V + (int64_t)j * n;
-        PG_FOR_OWN_NODES(N, i) {
-            Vj[3 * i] = uin[3 * i] * s;
-            Vj[3 * i + 1] = uin[3 * i + 1] * s;
-            Vj[3 * i + 2] = uin[3 * i + 2] * s;
-            T y0, y1, y2;
-            pg_row<T, H16>(a, i, uin, y0, y1, y2);
-            uout[3 * i] = y0 * s;
-            uout[3 * i + 1] = y1 * s;
-            uout[3 * i + 2] = y2 * s;
-        }
-        pg_dots<T>(a.V, uout, N, j + 1, true, pbuf(phase));
+        PG_FOR_OWN_NODES(N, i)
+#pragma unroll
+            for (int r = 0; r < NC; r++) Vj[NC * i + r] = uin[NC * i + r] * s;
+        if (!op(uin, s, uout, phase)) return abort_out();
+        pg_dots<T, NC>(a.V, uout, N, j + 1, true, pbuf(phase));
         if (!pg_barrier(a.bar, phase)) return abort_out();
         pg_sum(pbuf(phase - 1), j + 2, s_col);  // h1, and ||w||^2 in s_col[j + 1]
         __syncthreads();
@@ -861,11 +881,11 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
         const bool reorth = s_fl[4] != 0;
         if (!reorth) {
             // ---- P2: w -= V h1, the new direction (norm from the test above)
-            pg_axpy<T>(a.V, uout, N, j + 1, hs);
+            pg_axpy<T, NC>(a.V, uout, N, j + 1, hs);
         } else {
             // ---- P2: w -= V h1; dots again (second Gram-Schmidt pass)
-            pg_axpy<T>(a.V, uout, N, j + 1, hs);
-            pg_dots<T>(a.V, uout, N, j + 1, false, pbuf(phase));
+            pg_axpy<T, NC>(a.V, uout, N, j + 1, hs);
+            pg_dots<T, NC>(a.V, uout, N, j + 1, false, pbuf(phase));
             if (!pg_barrier(a.bar, phase)) return abort_out();
             pg_sum(pbuf(phase - 1), j + 1, s_tmp);  // h2
             __syncthreads();
@@ -877,7 +897,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
             // ---- P3: w -= V h2; ||w||
             {
                 __shared__ double red1[kPgThreads / 32];
-                const double tb = pg_block_sum<T>(pg_axpy<T>(a.V, uout, N, j + 1, hs), red1);
+                const double tb = pg_block_sum<T>(pg_axpy<T, NC>(a.V, uout, N, j + 1, hs), red1);
                 if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
             }
             if (!pg_barrier(a.bar, phase)) return abort_out();
@@ -982,17 +1002,15 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
             __syncthreads();
             // x += M^-1 V y
             PG_FOR_OWN_NODES(N, i) {
-                T u0 = 0, u1 = 0, u2 = 0;
-                for (int l = 0; l < k; l++) {
-                    const T *v = a.V + (int64_t)l * n + 3 * i;
-                    u0 = fma(v[0], hs[l], u0);
-                    u1 = fma(v[1], hs[l], u1);
-                    u2 = fma(v[2], hs[l], u2);
-                }
+                T u[NC];
 #pragma unroll
-                for (int r = 0; r < 3; r++)
-                    a.x[3 * i + r] += __ldg(a.jac + (3 * r) * N + i) * u0 + __ldg(a.jac + (3 * r + 1) * N + i) * u1 +
-                                      __ldg(a.jac + (3 * r + 2) * N + i) * u2;
+                for (int r = 0; r < NC; r++) u[r] = 0;
+                for (int l = 0; l < k; l++) {
+                    const T *v = a.V + (int64_t)l * n + NC * i;
+#pragma unroll
+                    for (int r = 0; r < NC; r++) u[r] = fma(v[r], hs[l], u[r]);
+                }
+                xupd(i, u);
             }
             __syncthreads();
         }
@@ -1003,7 +1021,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
                 st->status_any |= st->flags | ((!st->converged && !st->flags) ? 4 : 0);
                 st->stop = 2;
             }
-            return;
+            return true;
         }
         // ---- restart: c = G_0^T ... G_{k-1}^T (g_k e_k), residual norm |g_k|;
         // r = sum_{l<k} c_l V_l + c_k (w / h_{k,k-1}), unnormalised
@@ -1033,16 +1051,16 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
         const T hinv = (T)s_sc[2];
         T *unew = (uout == a.U0) ? a.U1 : a.U0;
         PG_FOR_OWN_NODES(N, i) {
-            T r0 = uout[3 * i] * hinv * hs[k], r1 = uout[3 * i + 1] * hinv * hs[k], r2 = uout[3 * i + 2] * hinv * hs[k];
+            T rr[NC];
+#pragma unroll
+            for (int r = 0; r < NC; r++) rr[r] = uout[NC * i + r] * hinv * hs[k];
             for (int l = 0; l < k; l++) {
-                const T *v = a.V + (int64_t)l * n + 3 * i;
-                r0 = fma(v[0], hs[l], r0);
-                r1 = fma(v[1], hs[l], r1);
-                r2 = fma(v[2], hs[l], r2);
+                const T *v = a.V + (int64_t)l * n + NC * i;
+#pragma unroll
+                for (int r = 0; r < NC; r++) rr[r] = fma(v[r], hs[l], rr[r]);
             }
-            unew[3 * i] = r0;
-            unew[3 * i + 1] = r1;
-            unew[3 * i + 2] = r2;
+#pragma unroll
+            for (int r = 0; r < NC; r++) unew[NC * i + r] = rr[r];
         }
         if (!pg_barrier(a.bar, phase)) return abort_out();
         s = (T)s_sc[1];
@@ -1050,6 +1068,87 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
         uout = (unew == a.U0) ? a.U1 : a.U0;
         j = 0;
     }
+}
+
+// The A-solve on the calling grid: operator A M^-1 (phase 1 of an iteration is
+// the SELL-32 SpMV, gathering u), x += M^-1 V y.
+template <typename T, bool H16>
+__device__ bool pg_gmres_a(const PgArgs<T> &a, unsigned &phase) {
+    const int64_t N = a.g.N;
+    auto op = [&](const T *u, T sc, T *w, unsigned &) {
+        PG_FOR_OWN_NODES(N, i) {
+            T y0, y1, y2;
+            pg_row<T, H16>(a, i, u, y0, y1, y2);
+            w[3 * i] = y0 * sc;
+            w[3 * i + 1] = y1 * sc;
+            w[3 * i + 2] = y2 * sc;
+        }
+        return true;
+    };
+    auto xupd = [&](int64_t i, const T (&u)[3]) {
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+            a.g.x[3 * i + r] += __ldg(a.jac + (3 * r) * N + i) * u[0] + __ldg(a.jac + (3 * r + 1) * N + i) * u[1] +
+                                __ldg(a.jac + (3 * r + 2) * N + i) * u[2];
+    };
+    return pg_gmres<T, 3>(a.g, phase, op, xupd);
+}
+
+template <typename T, bool H16>
+__global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
+    unsigned phase = 0u;  // the barrier words are cleared before every launch
+    pg_gmres_a<T, H16>(a, phase);
+}
+
+// The S-solve of Algorithm 1 (step 3) as one cooperative kernel: GMRES on
+// S diag(S^)^-1 with the matrix-free product of Algorithm 2 inside,
+//   z = diag(S^)^-1 v (applied while gathering), xbar = B z,
+//   xtil = A^-1 xbar (the A-solve above, on the same grid), barrier,
+//   w = D z - C xtil;
+// x = diag(S^)^-1 V y.
+template <typename T, bool H16>
+__global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T> a) {
+    unsigned phase = 0u;  // the barrier words are cleared before every launch
+    const int64_t N = s.g.N;
+    auto op = [&](const T *u, T sc, T *w, unsigned &ph) {
+        PG_FOR_OWN_NODES(N, i) {
+            const int t = (int)(i & 31);
+            const int64_t b0 = s.slice_ptr[i >> 5];
+            const int len = s.row_len[i];
+            T a0 = 0, a1 = 0, a2 = 0;
+            for (int jb = 0; jb < len; jb++) {
+                const int64_t q = (b0 + jb) * 32 + t;
+                const int64_t c = __ldg(s.col + q);
+                const T zc = __ldg(s.shat + c) * u[c];
+                const T *Bb = s.B + (q >> 5) * 96 + t;
+                a0 = fma(__ldg(Bb), zc, a0);
+                a1 = fma(__ldg(Bb + 32), zc, a1);
+                a2 = fma(__ldg(Bb + 64), zc, a2);
+            }
+            s.xbar[3 * i] = a0 * sc;
+            s.xbar[3 * i + 1] = a1 * sc;
+            s.xbar[3 * i + 2] = a2 * sc;
+        }
+        if (!pg_gmres_a<T, H16>(a, ph)) return false;
+        if (!pg_barrier(s.g.bar, ph)) return false;  // xtil complete before it is gathered
+        PG_FOR_OWN_NODES(N, i) {
+            const int t = (int)(i & 31);
+            const int64_t b0 = s.slice_ptr[i >> 5];
+            const int len = s.row_len[i];
+            T d = 0, m = 0;
+            for (int jb = 0; jb < len; jb++) {
+                const int64_t q = (b0 + jb) * 32 + t;
+                const int64_t c = __ldg(s.col + q);
+                d = fma(__ldg(s.D + (q >> 5) * 32 + t), __ldg(s.shat + c) * u[c], d);
+                const T *Cb = s.C + (q >> 5) * 96 + t;
+                m = fma(__ldg(Cb), s.xtil[3 * c], fma(__ldg(Cb + 32), s.xtil[3 * c + 1], fma(__ldg(Cb + 64), s.xtil[3 * c + 2], m)));
+            }
+            w[i] = d * sc - m;
+        }
+        return true;
+    };
+    auto xupd = [&](int64_t i, const T (&u)[1]) { s.g.x[i] += __ldg(s.shat + i) * u[0]; };
+    pg_gmres<T, 1>(s.g, phase, op, xupd);
 }
 
 // ------------------------------------------------------------ recording
@@ -1230,22 +1329,31 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
     L.partial = (double *)walloc(c, w, sizeof(double) * (size_t)L.grid * (m + 1));
     L.counter = (unsigned *)walloc(c, w, sizeof(unsigned) * 4);
     HYEL_CK(cudaMemsetAsync(L.counter, 0, sizeof(unsigned) * 4, c.stream));
-    if (kind == 0) {
-        // the persistent A-solve: a cooperative grid of all co-resident blocks
-        // (at most one thread per node)
+    if (kind == 0 || kind == 1) {
+        // the persistent A- and S-solves: cooperative grids of co-resident
+        // blocks (at most one thread per node); an A-level's partials serve
+        // every grid that can run it (its own and the S-solve's)
+        const int64_t nodes = kind == 0 ? n / 3 : n;
         L.z2 = (T *)walloc(c, w, sizeof(T) * (size_t)n);
         L.bar = (unsigned *)walloc(c, w, sizeof(unsigned) * kBarWords);
-        const int64_t need = std::max<int64_t>(1, (n / 3 + 31) / 32);  // no block without a slice
+        const int64_t need = std::max<int64_t>(1, (nodes + 31) / 32);  // no block without a slice
         int occ = 0, occ16 = 0;
-        HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_a<T, false>, kPgThreads, 0));
+        if (kind == 0)
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_a<T, false>, kPgThreads, 0));
+        else
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_s<T, false>, kPgThreads, 0));
         occ16 = occ;
-        if constexpr (std::is_same<T, float>::value)
-            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_a<float, true>, kPgThreads, 0));
-        if (occ < 1 || occ16 < 1) fail(HYEL_ECUDA, "persistent A-solve kernel does not fit on an SM");
+        if constexpr (std::is_same<T, float>::value) {
+            if (kind == 0)
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_a<float, true>, kPgThreads, 0));
+            else
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_s<float, true>, kPgThreads, 0));
+        }
+        if (occ < 1 || occ16 < 1) fail(HYEL_ECUDA, "persistent solve kernel does not fit on an SM");
         L.pg_grid = (int)std::min<int64_t>((int64_t)occ * c.num_sms, need);
         L.pg_grid16 = (int)std::min<int64_t>((int64_t)occ16 * c.num_sms, need);
-        L.pg_partial =
-            (double *)walloc(c, w, sizeof(double) * 2 * (size_t)std::max(L.pg_grid, L.pg_grid16) * (m + 1));
+        const int64_t gmax = (int64_t)(2048 / kPgThreads) * c.num_sms;  // any co-resident grid
+        L.pg_partial = (double *)walloc(c, w, sizeof(double) * 2 * (size_t)gmax * (m + 1));
     }
 }
 
@@ -1384,6 +1492,60 @@ void gm_solve(Rec &R, Level<T> &L, LevelState *st, const hyel_krylov_level &P, c
         });
 }
 
+// Arguments of the persistent A-solve for precision T (h16: the BF16 operator)
+template <typename T>
+PgArgs<T> pg_args(Ctx &c, Workspace &w, LevelState *st, const hyel_krylov_level &P, const T *b, T *x, bool &h16) {
+    Level<T> &L = Sys<T>::la(w);
+    const DeviceMesh &msh = c.mesh;
+    const DeviceMatrix &M = c.mat;
+    PgArgs<T> a;
+    a.slice_ptr = msh.slice_ptr;
+    a.row_len = msh.row_len;
+    a.col = msh.col;
+    a.Am = nullptr;
+    a.Am8 = M.Amh8;
+    a.Am1 = M.Amh1;
+    a.Ams = M.Amhs;
+    a.jac = Sys<T>::jac(c);
+    GmArgs<T> &g = a.g;
+    g.N = msh.N;
+    g.b = b;
+    g.x = x;
+    g.V = L.V;
+    g.U0 = L.z;
+    g.U1 = L.z2;
+    g.H = L.H;
+    g.partial = L.pg_partial;
+    g.bar = L.bar;
+    g.st = st;
+    g.m = std::min(P.restart, L.m);
+    g.maxit = P.maxit;
+    g.rtol = P.rtol;
+    g.atol = P.atol;
+    g.eta2 = P.rtol >= kPgLoose<T> ? kPgEta2<T> : 0.5;
+    h16 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        h16 = w.prec == HYEL_PREC_BF16S;
+        a.Am = h16 ? nullptr : M.Amf;
+    } else {
+        a.Am = M.Ams;
+    }
+    // algorithmic bytes of one iteration (matrix once, each vector pass once):
+    // A~ values + column indices + row metadata, and the passes over 3N-vectors
+    g.it_fixed = (double)msh.nnzb * ((h16 ? 22.0 : 9.0 * sizeof(T)) + 4.0) + 4.0 * (msh.N + 1);
+    g.it_unit = 3.0 * msh.N * sizeof(T);
+    return a;
+}
+
+cudaLaunchConfig_t coop_config(Ctx &c, int grid) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kPgThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c.stream;
+    return cfg;
+}
+
 // A-solve x = A^-1 b: one cooperative launch of the persistent GMRES kernel
 // (its barrier words cleared just before), in host-driven mode and in the graph
 template <typename T>
@@ -1405,52 +1567,11 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
             [&]() { spmv_A_ind<T>(c, Sys<T>::A(c), zout, L.V, L.n, &st->k); }, true);
         return;
     }
-    Level<T> &L = Sys<T>::la(w);
-    const DeviceMesh &msh = c.mesh;
-    const DeviceMatrix &M = c.mat;
-    PgArgs<T> a;
-    a.slice_ptr = msh.slice_ptr;
-    a.row_len = msh.row_len;
-    a.col = msh.col;
-    a.Am = nullptr;
-    a.Am8 = M.Amh8;
-    a.Am1 = M.Amh1;
-    a.Ams = M.Amhs;
-    a.jac = Sys<T>::jac(c);
-    a.N = msh.N;
-    a.b = b;
-    a.x = x;
-    a.V = L.V;
-    a.U0 = L.z;
-    a.U1 = L.z2;
-    a.H = L.H;
-    a.partial = L.pg_partial;
-    a.bar = L.bar;
-    a.st = st;
-    a.m = std::min(P.restart, L.m);
-    a.maxit = P.maxit;
-    a.rtol = P.rtol;
-    a.atol = P.atol;
-    a.eta2 = P.rtol >= kPgLoose<T> ? kPgEta2<T> : 0.5;
     bool h16 = false;
-    if constexpr (std::is_same<T, float>::value) {
-        h16 = w.prec == HYEL_PREC_BF16S;
-        a.Am = h16 ? nullptr : M.Amf;
-    } else {
-        a.Am = M.Ams;
-    }
-    // algorithmic bytes of one iteration (matrix once, each vector pass once):
-    // A~ values + column indices + row metadata, and 4 (j+1) + 9 passes over
-    // 3N-vectors (u gather, v_j, w, two dot passes over V_0..V_j and w, two
-    // axpy passes over V_0..V_j reading and writing w)
-    a.it_fixed = (double)msh.nnzb * ((h16 ? 22.0 : 9.0 * sizeof(T)) + 4.0) + 4.0 * (msh.N + 1);
-    a.it_unit = 3.0 * msh.N * sizeof(T);
+    Level<T> &L = Sys<T>::la(w);
+    PgArgs<T> a = pg_args<T>(c, w, st, P, b, x, h16);
     HYEL_CK(cudaMemsetAsync(L.bar, 0, kBarWords * sizeof(unsigned), c.stream));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(h16 ? L.pg_grid16 : L.pg_grid));
-    cfg.blockDim = dim3(kPgThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = c.stream;
+    cudaLaunchConfig_t cfg = coop_config(c, h16 ? L.pg_grid16 : L.pg_grid);
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
     at[0].val.cooperative = 1;
@@ -1468,6 +1589,70 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
     if (!launched) HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_a<T, false>, a));
     count_launch();
     prof_end(c, HYEL_K_GMRES_A, ev, 0.0);  // bytes are added from the level states after the solve
+}
+
+// The S-solve of Algorithm 1 step 3 as one cooperative launch of k_gmres_s
+// (the inner A-solves of Algorithm 2 run inside it on the A-level buffers)
+template <typename T>
+void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x) {
+    Ctx &c = *R.c;
+    const DeviceMesh &msh = c.mesh;
+    const DeviceMatrix &M = c.mat;
+    const int64_t N = msh.N;
+    Level<T> &La = Sys<T>::la(w);
+    Level<T> &Ls = Sys<T>::ls(w);
+    T *xbar = Sys<T>::vec(w, 4, N), *xtil = Sys<T>::vec(w, 5, N);
+    bool h16 = false;
+    PgArgs<T> a = pg_args<T>(c, w, w.states + ST_INNER, p.inner, xbar, xtil, h16);
+    SgArgs<T> sg;
+    sg.slice_ptr = msh.slice_ptr;
+    sg.row_len = msh.row_len;
+    sg.col = msh.col;
+    sg.B = Sys<T>::B(c);
+    sg.C = Sys<T>::C(c);
+    sg.D = Sys<T>::D(c);
+    sg.shat = Sys<T>::shat(c);
+    sg.xbar = xbar;
+    sg.xtil = xtil;
+    GmArgs<T> &g = sg.g;
+    g.N = N;
+    g.b = b;
+    g.x = x;
+    g.V = Ls.V;
+    g.U0 = Ls.z;
+    g.U1 = Ls.z2;
+    g.H = Ls.H;
+    g.partial = Ls.pg_partial;
+    g.bar = La.bar;
+    g.st = w.states + ST_S;
+    g.m = std::min(p.s.restart, Ls.m);
+    g.maxit = p.s.maxit;
+    g.rtol = p.s.rtol;
+    g.atol = p.s.atol;
+    g.eta2 = p.s.rtol >= kPgLoose<T> ? kPgEta2<T> : 0.5;
+    // one S-iteration outside its inner A-solve: B, C, D values and column
+    // indices (twice), and the vector passes over [N]-vectors
+    g.it_fixed = (double)msh.nnzb * (7.0 * sizeof(T) + 8.0) + 4.0 * (N + 1);
+    g.it_unit = (double)N * sizeof(T);
+    HYEL_CK(cudaMemsetAsync(La.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    cudaLaunchConfig_t cfg = coop_config(c, h16 ? Ls.pg_grid16 : Ls.pg_grid);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaEvent_t ev;
+    prof_begin(c, HYEL_K_GMRES_S, &ev);
+    bool launched = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (h16) {
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true>, sg, a));
+            launched = true;
+        }
+    }
+    if (!launched) HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false>, sg, a));
+    count_launch();
+    prof_end(c, HYEL_K_GMRES_S, ev, 0.0);
 }
 
 // Algorithm 2: y = D x - C A^-1 (B x), y indexed by the S-level state
@@ -1494,11 +1679,16 @@ void pscr(Rec &R, Workspace &w, const hyel_solver_params &p, const T *rv, const 
     a_solve<T>(R, w, w.states + ST_A1, p.a, rv, xhat);
     // 2: r_p <- r_p - C xhat
     spmv_C<T>(c, Sys<T>::C(c), xhat, rp2, rp);
-    // 3: S x_p = r_p, right-preconditioned by diag(S^)^-1
-    Level<T> &Ls = Sys<T>::ls(w);
-    LevelState *sst = w.states + ST_S;
-    gm_solve<T, 1>(R, Ls, sst, p.s, rp2, xp, Sys<T>::shat(c), nullptr,
-                   [&]() { schur_op<T>(R, w, p, Ls.z, Ls.V, &sst->k, Ls.n); }, true);
+    // 3: S x_p = r_p, right-preconditioned by diag(S^)^-1: one persistent
+    // kernel with block-Jacobi A-solves; kernel-per-step loop with multigrid ones
+    if (!w.a_amg) {
+        s_solve<T>(R, w, p, rp2, xp);
+    } else {
+        Level<T> &Ls = Sys<T>::ls(w);
+        LevelState *sst = w.states + ST_S;
+        gm_solve<T, 1>(R, Ls, sst, p.s, rp2, xp, Sys<T>::shat(c), nullptr,
+                       [&]() { schur_op<T>(R, w, p, Ls.z, Ls.V, &sst->k, Ls.n); }, true);
+    }
     // 4: r_v <- r_v - B x_p
     spmv_B<T>(c, Sys<T>::B(c), xp, rv2, rv);
     // 5: A x_v = r_v
@@ -1644,8 +1834,10 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
         for (int64_t q = 0; q < k; q++) count_launch();
     }
     const LevelState *hs = w.h_states;
-    if (c.prof.on && !p.graph)
-        c.prof.bytes[HYEL_K_GMRES_A] += hs[ST_A1].alg_bytes + hs[ST_A2].alg_bytes + hs[ST_INNER].alg_bytes;
+    if (c.prof.on && !p.graph) {
+        c.prof.bytes[HYEL_K_GMRES_A] += hs[ST_A1].alg_bytes + hs[ST_A2].alg_bytes;
+        c.prof.bytes[HYEL_K_GMRES_S] += hs[ST_S].alg_bytes + hs[ST_INNER].alg_bytes;
+    }
     const double bn = hs[ST_OUTER].bnorm;
     const double rel = bn > 0 ? std::sqrt(c.h_red[8]) / bn : std::sqrt(c.h_red[8]);
     int st = HYEL_OK;

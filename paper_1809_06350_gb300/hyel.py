@@ -24,9 +24,9 @@ HYEL_APREC_BJACOBI, HYEL_APREC_AMG = 0, 1
 HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D, HYEL_OP_AM = 0, 1, 2, 3, 4, 5
 HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32, HYEL_MAT_TRANSPOSED, HYEL_MAT_SCALED_BF16S = 0, 1, 2, 3, 4
 (HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER, HYEL_K_SPMV_A16,
- HYEL_K_GMRES_A) = range(7)
-HYEL_K_NCLASSES = 7
-K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather", "spmv_A16", "gmres_A"]
+ HYEL_K_GMRES_A, HYEL_K_GMRES_S) = range(8)
+HYEL_K_NCLASSES = 8
+K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather", "spmv_A16", "gmres_A", "gmres_S"]
 
 # every symbol include/hyel.h declares
 EXPORTS = [
