@@ -163,13 +163,18 @@ void newton_step(Ctx &c, const hyel_time_params &tp, const hyel_solver_params &s
         // K_{.,udot} R_k correction of the right-hand side is formed at l = 1 only
         TimeConsts tcl = tc;
         tcl.skip_corr = l > 1 ? 1 : 0;
-        // from the second corrector on, the stopping test runs on a
-        // residual-only pass; the tangent is assembled only if Newton goes on
-        assemble(c, tcl, stage, nullptr, l == 1 ? rhs : nullptr, norms, l == 1);
+        // the stopping test runs on a residual-only pass when the previous
+        // residual, squared as quadratic convergence would, already meets the
+        // tolerance (to within 10x); the tangent follows only if Newton goes
+        // on. Otherwise the tangent pass comes first and its norms decide.
+        const double prev = ns.res_norm;
+        const bool likely = l > 1 && norm0 > 0 &&
+                            ((prev / norm0) * (prev / norm0) <= 10.0 * tp.tol_r || prev * prev / norm0 <= 10.0 * tp.tol_a);
+        assemble(c, tcl, stage, nullptr, likely ? nullptr : rhs, norms, !likely);
         if (l == 1) norm0 = norms[0];
         ns.res_norm = norms[0];
         const bool conv = norms[0] <= tp.tol_a || (norm0 > 0 && norms[0] / norm0 <= tp.tol_r);
-        if (!conv && l > 1) assemble(c, tcl, stage, nullptr, rhs, nullptr, true);
+        if (!conv && likely) assemble(c, tcl, stage, nullptr, rhs, nullptr, true);
         ms_asm += 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - ta).count();
         if (conv) {
             ns.converged = 1;
