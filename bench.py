@@ -318,10 +318,26 @@ def run_hyel(args, rank, world, local_rank):
                 "newton_solves": itsm, "speedup_vs_fp64": ms / msm,
                 "state_rel_diff_vs_fp64": float(torch.linalg.norm(fin - final64) / torch.linalg.norm(final64))}
 
+    def per_step_states(spm):
+        # untimed: the state after every time step of the same run from rest
+        reset()
+        out = []
+        for k in range(args.steps):
+            tp = H.time_params(dt=dt, t_n=k * dt)
+            H.hyel_newton_step(ctx, tp, spm, state, raise_on_error=False)
+            out.append(torch.cat([dev[nm] for nm in names]).clone())
+        return out
+
     mixed = mixed16 = None
     if not args.no_mixed and args.precision == "fp64":
         mixed = mixed_run(sp32, "spmv_A32")
         mixed16 = mixed_run(sp16, "spmv_A16")
+        ref_states = per_step_states(sp64)
+        for md, spm in ((mixed, sp32), (mixed16, sp16)):
+            st_m = per_step_states(spm)
+            md["per_step_rel_diff_vs_fp64"] = [
+                float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(st_m, ref_states)]
+        del ref_states
     e2e = None
     if not args.no_e2e:
         host = {k: torch.zeros(sizes[k], dtype=torch.float64, pin_memory=True) for k in names}
