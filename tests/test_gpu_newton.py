@@ -52,6 +52,32 @@ def test_two_newton_steps_match_oracle(precision):
     gp.close()
 
 
+@pytest.mark.parametrize("nu", [0.45, 0.499, 0.5])
+def test_poisson_sweep_newton_step_matches_oracle(nu):
+    """The Poisson-ratio sweep of the cube workload (kappa from nu; nu = 0.5
+    is the incompressible model): one Newton step under the ramped dead load
+    matches the oracle's direct-solve Newton step, FP64 and FP32 levels."""
+    m = inputs.cube_mesh(6)
+    mat = inputs.material_nh(1e5, inputs.kappa_from_nu(1e5, nu), 1e3)
+    load = {"p_max": 2e4, "t_ramp": 10 * DT}
+    gp = GpuProblem(m, mat, load=load)
+    prob, N = gp.prob, gp.N
+    z = inputs.zero_state(N)
+    yz = {k: z[k] for k in ("u", "p", "v")}
+    ydz = {k: z[k] for k in ("udot", "pdot", "vdot")}
+    y1, yd1, info = Nw.newton_step(prob, yz, ydz, 0.0, DT, tol_r=1e-10, tol_a=1e-12)
+    assert info["converged"]
+    for precision in (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32):
+        dev = {k: gp.dev(z[k]) for k in z}
+        state = H.state_struct(dev["u"], dev["p"], dev["v"], dev["udot"], dev["pdot"], dev["vdot"])
+        sp_ = H.solver_params(outer_rtol=1e-13, sub_rtol=1e-2, precision=precision)
+        st, rc = H.hyel_newton_step(gp.ctx, H.time_params(dt=DT, tol_r=1e-10, tol_a=1e-12), sp_, state)
+        assert st.converged and st.iterations == info["iterations"], (nu, precision, st.as_dict(), info)
+        for k in ("u", "p", "v"):
+            assert _rel(dev[k].cpu().numpy().reshape(y1[k].shape), y1[k]) <= 1e-9, (nu, precision, k)
+    gp.close()
+
+
 def test_newton_iteration_cap_reports_noconv():
     m = inputs.cube_mesh(4)
     gp = GpuProblem(m, inputs.material_nh(), load={"p_max": 2e4, "t_ramp": DT}, with_oracle=False)
