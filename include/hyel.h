@@ -147,11 +147,13 @@ typedef struct {
  * graph = 1 (default): the whole nested solve is one CUDA graph whose Krylov
  * loops are device-driven `while` conditional nodes (no host round trip until
  * the solve ends); the graph is built once per context and parameter set.
- * graph = 0: the host drives the outer and S loops, reading the level state
- * after every iteration. Both run the same kernels and give the same
- * iterates. Every A-solve (intermediate and inner) is one cooperative launch
- * of a persistent GMRES kernel on A M^-1 (M the 3x3 block diagonal of A) in
- * both modes. check_every (>= 1) is validated and otherwise unused. */
+ * graph = 0: the host drives the kernel-per-step loops, reading the level
+ * state after every iteration. Both run the same kernels and give the same
+ * iterates. With block-Jacobi A-solves (the default), each intermediate
+ * A-solve is one cooperative launch of a persistent GMRES kernel on A M^-1 (M
+ * the 3x3 block diagonal of A), and each S-solve, its inner A-solves
+ * included, is one cooperative launch too, in both modes. check_every (>= 1)
+ * is validated and otherwise unused. */
 /* Preconditioner of the A-solves (intermediate and inner):
  * HYEL_APREC_BJACOBI: 3x3 block-Jacobi, folded into the operator (A M^-1) of a
  *   persistent GMRES kernel (the default);

@@ -1,10 +1,12 @@
 // Krylov solvers and the nested block preconditioner (§4).
 //
 // * Right-preconditioned GMRES(m) and FGMRES(m) (ref. Saad), zero initial
-//   guess, classical Gram-Schmidt with one full reorthogonalization (CGS2),
-//   Givens rotations and back-substitution on the device; stop when the
-//   rotated residual ||r|| <= max(rtol ||b||, atol) or after maxit iterations.
-//   A restart takes the new starting vector from the Arnoldi relation,
+//   guess, classical Gram-Schmidt with one full reorthogonalization (CGS2;
+//   loose A- and S-solves keep a single pass when a test in the manner of
+//   Daniel-Gragg-Kaufman-Stewart allows), Givens rotations and
+//   back-substitution on the device; stop when the rotated residual
+//   ||r|| <= max(rtol ||b||, atol) or after maxit iterations. A restart takes
+//   the new starting vector from the Arnoldi relation,
 //   r = V_{k+1} Q^T (g_k e_k), so no extra operator application is needed.
 // * Outer FGMRES on the symmetrically scaled system (§4.1) with the SCR
 //   preconditioner of Algorithm 1; the Schur product of Algorithm 2 is
@@ -20,16 +22,19 @@
 //   copy in the A-solves.
 //
 // Control flow: every Krylov level keeps its state (iteration index, norms,
-// flags) in device memory and every kernel reads it there. The whole nested
-// solve is recorded once into a CUDA graph in which each level's iteration
-// loop is a `while` conditional node; the last kernel of an iteration sets the
-// loop condition. One graph launch performs the entire solve; the host reads
-// the level states once at the end. The same kernels can instead be replayed
-// by a host loop (params.graph = 0).
+// flags) in device memory. The intermediate A-solves (k_gmres_a) and the
+// S-solve with its inner A-solves (k_gmres_s) are persistent cooperative
+// kernels: one launch runs a whole solve, its phases separated by grid
+// barriers. The outer FGMRES (and, with multigrid A-solves, the S-level) runs
+// as a sequence of kernels per iteration. The whole nested solve is recorded
+// once into a CUDA graph in which each kernel-per-step loop is a `while`
+// conditional node; the last kernel of an iteration sets the loop condition.
+// One graph launch performs the entire solve; the host reads the level states
+// once at the end. The same kernels can instead be replayed by a host loop
+// (params.graph = 0).
 //
 // Every reduction has a fixed grid and a fixed summation order (per-block
-// partials, then the last block to finish sums them in block order), so all
-// results are bitwise reproducible.
+// partials summed in block order), so all results are bitwise reproducible.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -1597,7 +1602,6 @@ template <typename T>
 void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x) {
     Ctx &c = *R.c;
     const DeviceMesh &msh = c.mesh;
-    const DeviceMatrix &M = c.mat;
     const int64_t N = msh.N;
     Level<T> &La = Sys<T>::la(w);
     Level<T> &Ls = Sys<T>::ls(w);
