@@ -23,6 +23,9 @@ as the direct-solve primitive):
   (§4.1); explicit Schur complement (§4.2); sparse direct solve.
 * ``newton``       -- generalized-alpha parameters (§3.2) and the predictor
   multi-corrector Newton step (§3.3), each linear system solved directly.
+* ``schur_hat``    -- the explicit sparse S^ = D - C diag(A)^-1 B (§4.2), a
+  power-method bound on diag(S^)^-1 S^ and the Chebyshev polynomial
+  preconditioner built on S^ (the stand-in for the paper's multigrid on S^).
 
 Parity pins (tests/test_oracle_*.py) tie every function to something other
 than itself: closed forms, finite differences, patch and rigid-motion tests,
