@@ -51,6 +51,11 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16s"],
                    help="preconditioner-level precision of the main timed run (fp64 is the headline; "
                         "the mixed forms are also timed beside it unless --no-mixed)")
+    p.add_argument("--s-precond", default="jacobi", choices=["jacobi", "cheb"],
+                   help="S-solve preconditioner: diag(S^)^-1, or the Chebyshev polynomial in the explicit S^")
+    p.add_argument("--cheb-degree", type=int, default=4)
+    p.add_argument("--cheb-ratio", type=float, default=0.0,
+                   help="0: interval from Ritz estimates; > 1: fixed lmax / lmin")
     return p.parse_args()
 
 
@@ -66,7 +71,11 @@ def workload(args):
 
 def config_dict(args, mesh):
     N = mesh["X"].shape[0]
+    sprec = "diag(S^)" if args.s_precond == "jacobi" else \
+        f"chebyshev(S^), degree {args.cheb_degree}, " + \
+        (f"lmax/lmin {args.cheb_ratio:g}" if args.cheb_ratio > 0 else "interval from Ritz values")
     return {"workload": f"cube{args.n}^3 compression, nu={args.nu}", "levels": args.precision,
+            "s_precond": sprec,
             "tets": int(mesh["tets"].shape[0]),
             "nodes": int(N), "unknowns": int(4 * N), "dt": 1e-3, "rho_inf": 0.5, "outer_rtol": 1e-10,
             "sub_rtol": 1e-2, "steps_per_run": "t = 0..K-1 from rest, load ramp over 10 steps",
@@ -288,10 +297,12 @@ def run_hyel(args, rank, world, local_rank):
         return ms, its, its_total, launches, prof
 
     graph = 0 if args.host_loops else 1
+    sprec_kw = {"s_precond": H.HYEL_SPREC_JACOBI if args.s_precond == "jacobi" else H.HYEL_SPREC_CHEB,
+                "s_cheb_degree": args.cheb_degree, "s_cheb_ratio": args.cheb_ratio}
     main_prec = {"fp64": H.HYEL_PREC_FP64, "fp32": H.HYEL_PREC_FP32, "bf16s": H.HYEL_PREC_BF16S}[args.precision]
-    sp64 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=graph)
-    sp32 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, graph=graph)
-    sp16 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_BF16S, graph=graph)
+    sp64 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=graph, **sprec_kw)
+    sp32 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, graph=graph, **sprec_kw)
+    sp16 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_BF16S, graph=graph, **sprec_kw)
     # warm-up (also builds the Krylov workspaces)
     reset()
     run_steps(args.warmup, sp64)
@@ -368,7 +379,7 @@ def run_hyel(args, rank, world, local_rank):
     # per-launch CUDA events need host-launched kernels: replay the same K
     # steps with host-driven Krylov loops (same kernels, same order, same
     # iterates) and time every launch of the profiled classes on the stream
-    sp_prof = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=0)
+    sp_prof = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=0, **sprec_kw)
     _, _, _, _, prof_host = timed(args.steps, sp_prof, profile=True)
     dom = max(("gmres_A", "gmres_S"), key=lambda k: prof_host[k]["ms"])  # the dominant persistent kernel
     pl = prof_host[dom]

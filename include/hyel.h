@@ -163,6 +163,20 @@ typedef struct {
  *   of an FGMRES A-level. The hierarchy's pattern is built once per mesh, its
  *   operators once per assembly (after the scaling). */
 enum { HYEL_APREC_BJACOBI = 0, HYEL_APREC_AMG = 1 };
+/* Preconditioner of the S-solve (§4.2):
+ * HYEL_SPREC_JACOBI: diag(S^)^-1, S^ = D - C diag(A)^-1 B (the default);
+ * HYEL_SPREC_CHEB: the polynomial p(diag(S^)^-1 S^) diag(S^)^-1 of degree
+ *   s_cheb_degree (1..16) given by that many steps of the Chebyshev iteration
+ *   for S^ z = v from z = 0 on an interval [lmin, lmax], with the explicit
+ *   sparse S^ (distance-2 node pattern, see hyel_schur_hat_setup). lmax and an
+ *   estimate of lmin come from Ritz values (hyel_schur_hat_setup);
+ *   s_cheb_ratio = 0 uses that lmin (clamped to [lmax / 1000, lmax / 1.5]),
+ *   s_cheb_ratio > 1 fixes lmin = lmax / s_cheb_ratio. Rebuilt after every
+ *   scaling of a new assembly. A fixed linear operator, applied inside the
+ *   persistent S-solve (one grid barrier per degree); the paper's own choice
+ *   is algebraic multigrid built from S^ (§5). Needs a_precond =
+ *   HYEL_APREC_BJACOBI. */
+enum { HYEL_SPREC_JACOBI = 0, HYEL_SPREC_CHEB = 1 };
 
 typedef struct {
     hyel_krylov_level outer, a, s, inner;
@@ -170,6 +184,9 @@ typedef struct {
     int32_t check_every;
     int32_t graph;
     int32_t a_precond;      /* HYEL_APREC_* */
+    int32_t s_precond;      /* HYEL_SPREC_* */
+    int32_t s_cheb_degree;  /* HYEL_SPREC_CHEB: polynomial degree, 1..16 */
+    double  s_cheb_ratio;   /* HYEL_SPREC_CHEB: 0 (estimated lmin) or lmax / lmin > 1 */
 } hyel_solver_params;
 
 typedef struct {
@@ -243,7 +260,8 @@ int hyel_matrix_download(hyel_ctx *ctx, int32_t *row_ptr, int32_t *col,
 
 /* ---------------------------------------------------------------- operators */
 
-enum { HYEL_OP_FULL = 0, HYEL_OP_A = 1, HYEL_OP_B = 2, HYEL_OP_C = 3, HYEL_OP_D = 4, HYEL_OP_AM = 5 };
+enum { HYEL_OP_FULL = 0, HYEL_OP_A = 1, HYEL_OP_B = 2, HYEL_OP_C = 3, HYEL_OP_D = 4, HYEL_OP_AM = 5,
+       HYEL_OP_SHAT = 6 };
 enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYEL_MAT_TRANSPOSED = 3,
        HYEL_MAT_SCALED_BF16S = 4 };
 
@@ -259,7 +277,9 @@ enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYE
  * scale copies described at HYEL_PREC_BF16S.
  * AM ([3N] -> [3N], scaled matrices only): y = A M^-1 x with M the 3x3 block
  * diagonal of the scaled A, i.e. A right-preconditioned by block-Jacobi; the
- * A-solves iterate on this operator (stored block by block as A_(r,c) M_c^-1). */
+ * A-solves iterate on this operator (stored block by block as A_(r,c) M_c^-1).
+ * SHAT ([N] -> [N], HYEL_MAT_SCALED64 or HYEL_MAT_SCALED32): y = S^ x with
+ * the explicit S^ of hyel_schur_hat_setup (HYEL_ESTATE before it). */
 int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y);
 
 /* Prepare the scaled system for the current assembly (§4.1): W_ii =
@@ -267,6 +287,36 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y);
  * BF16-with-block-scale copy of the scaled A, 3x3
  * block-Jacobi inverses of A and diag(S^). w_out: device [4N] or NULL. */
 int hyel_solve_setup(hyel_ctx *ctx, double *w_out);
+
+/* Explicit S^ = D - C diag(A)^-1 B of the scaled system (§4.2, the matrix
+ * the paper builds the S-solve's preconditioner from), diag(A) the scalar
+ * diagonal of the scaled A. Runs hyel_solve_setup if needed, then (unless
+ * current for this assembly) sums S^ on the GPU on the distance-2 node
+ * pattern (row i couples i with every node two block-graph steps away; the
+ * pattern and the per-contribution entry positions are built on the host on
+ * first use for the mesh) in FP64 and FP32, and estimates the spectrum of
+ * diag(S^)^-1 S^: 12 Arnoldi steps (two classical Gram-Schmidt passes each)
+ * on |M|^-1/2 S^ |M|^-1/2, M = diag(S^), from x0_i = 2 u_i - 1 (u_i the top 53
+ * bits of output i of SplitMix64 seeded with 0, over 2^53); the eigenvalues
+ * theta of the symmetric part of the 12 x 12 Hessenberg matrix give
+ * lmin = theta_min / 2 and lmax = 1.05 theta_max (FP64 vectors, the FP32
+ * values of S^). Synchronizes.
+ *   bounds_out host [2] or NULL: lmin, lmax.
+ *   info       host [n_info] or NULL: [0] nonzeros of S^, [1] padded slots,
+ *              [2] summed contributions, [3] longest row.
+ * HYEL_EINVAL if a row is longer than 800 entries; HYEL_ENAN if the Arnoldi
+ * run meets NaN/Inf or no positive Ritz value. */
+int hyel_schur_hat_setup(hyel_ctx *ctx, double *bounds_out, int64_t *info, int n_info);
+
+/* y = p(diag(S^)^-1 S^) diag(S^)^-1 x: `degree` steps of the Chebyshev
+ * iteration for S^ y = x from y = 0 on the interval HYEL_SPREC_CHEB uses
+ * (ratio = 0: the estimated one; ratio > 1: [lmax / ratio, lmax]), FP64
+ * vectors. matrix: HYEL_MAT_SCALED64 (FP64 values of S^) or HYEL_MAT_SCALED32
+ * (FP32 values, as inside the S-solve, where the polynomial reads S^ in FP32
+ * at every precision). x, y: device [N] double, distinct. HYEL_ESTATE before
+ * hyel_schur_hat_setup on the current assembly; HYEL_EINVAL for another
+ * matrix, degree outside 1..16 or another ratio. Synchronizes. */
+int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio, const double *x, double *y);
 
 /* y = S x for the scaled system (Algorithm 2: D x - C A^-1 (B x)), the inner
  * A-solve controlled by params->inner and params->precision. x, y: device
@@ -334,10 +384,11 @@ int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solv
  * intermediate A-solve), HYEL_K_GMRES_S the persistent S-solve kernel (one
  * launch per S-solve, its inner A-solves included); their algorithmic bytes
  * are counted on the device per iteration (the operator's values and indices
- * plus the passes over the Krylov vectors) and added when the solve returns. */
+ * plus the passes over the Krylov vectors) and added when the solve returns.
+ * HYEL_K_SCHUR_HAT times the numeric S^ and its power-method bound together. */
 enum { HYEL_K_SPMV_A64 = 0, HYEL_K_SPMV_A32 = 1, HYEL_K_SPMV_FULL64 = 2,
        HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_SPMV_A16 = 5, HYEL_K_GMRES_A = 6,
-       HYEL_K_GMRES_S = 7, HYEL_K_NCLASSES = 8 };
+       HYEL_K_GMRES_S = 7, HYEL_K_SCHUR_HAT = 8, HYEL_K_NCLASSES = 9 };
 
 /* enable != 0 starts event timing of the kernel classes (and clears the
  * totals); 0 stops it. */

@@ -8,18 +8,23 @@ Plain definitions, in float64:
   the distance-2 node graph of the mesh.
 * ``splitmix64`` / ``power_start`` -- the counter-based generator SplitMix64
   (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
-  OOPSLA 2014) and the start vector of the power method drawn from it; the
-  CUDA side implements the same published generator on its own.
-* ``lmax_estimate``  -- a fixed number of power-method steps on M^-1 S^,
-  M = diag(S^), times a safety factor: an estimate of the largest eigenvalue.
+  OOPSLA 2014) and the Krylov start vector drawn from it; the CUDA side
+  implements the same published generator on its own.
+* ``ritz_bounds``    -- k steps of Arnoldi (classical Gram-Schmidt, two
+  passes) on |M|^-1/2 S^ |M|^-1/2 (similar to M^-1 S^ when diag(S^) > 0) from
+  the normalised power_start vector; the extreme eigenvalues of the symmetric
+  part of the k x k Hessenberg matrix (Ritz values; for a symmetric operator
+  they interlace the spectrum, the Lanczos bounds) give the interval of the
+  Chebyshev preconditioner: [theta_min / RITZ_LOW, RITZ_SAFETY theta_max]
+  (``cheb_interval`` clamps it, or fixes lmin = lmax / ratio on request).
 * ``chebyshev_apply`` -- z = p(M^-1 S^) M^-1 v: a fixed number of steps of the
   Chebyshev iteration for S^ z = v, zero start, Jacobi-preconditioned, on the
-  interval [lmax / ratio, lmax] (the three-term recurrence of the classical
+  interval [lmin, lmax] (the three-term recurrence of the classical
   Chebyshev semi-iteration, e.g. Saad, Iterative Methods for Sparse Linear
   Systems, 2nd ed., §12.3). The paper applies algebraic multigrid built from
   S^ as the preconditioner of the Schur-complement solve (§5); this is the
-  polynomial stand-in, a fixed linear operator in S^ for given (lmax, ratio,
-  degree).
+  polynomial stand-in, a fixed linear operator in S^ for a given interval and
+  degree.
 """
 from __future__ import annotations
 
@@ -30,8 +35,11 @@ from .system import split_blocks
 
 MASK64 = (1 << 64) - 1
 GOLDEN64 = 0x9E3779B97F4A7C15
-POWER_STEPS = 10        # power-method steps for the bound
-POWER_SAFETY = 1.1      # the bound is POWER_SAFETY times the last estimate
+RITZ_STEPS = 12         # Arnoldi steps of ritz_bounds
+RITZ_SAFETY = 1.05      # lmax = RITZ_SAFETY x the largest Ritz value
+RITZ_LOW = 2.0          # lmin = the smallest Ritz value / RITZ_LOW
+CHEB_MAX_RATIO = 1000.0  # the interval's lmax / lmin is clamped to [CHEB_MIN_RATIO, CHEB_MAX_RATIO]
+CHEB_MIN_RATIO = 1.5
 DIAG_EPS = 1e-300       # |diag| at or below this is treated as 1
 
 
@@ -64,32 +72,73 @@ def jacobi_inverse(Sh):
     return out
 
 
-def lmax_estimate(Sh, steps=POWER_STEPS, safety=POWER_SAFETY):
-    """safety * ||y_k|| after k power steps y_j = M^-1 S^ x_{j-1} / ||x_{j-1}||,
-    x_j = y_j, from x_0 = power_start(N); M = diag(S^)."""
-    dinv = jacobi_inverse(Sh)
-    x = power_start(Sh.shape[0])
-    nx = np.linalg.norm(x)
-    lam = 0.0
-    for _ in range(steps):
-        y = dinv * (Sh @ x) / nx
-        lam = np.linalg.norm(y)
-        x, nx = y, lam
-    return safety * lam
+def float32_values(Sh):
+    """S^ with every entry rounded to FP32 (the copy the CUDA preconditioner
+    reads); M = diag(S^) stays FP64 wherever it appears."""
+    out = Sh.copy()
+    out.data = out.data.astype(np.float32).astype(np.float64)
+    return out
 
 
-def chebyshev_apply(Sh, lmax, ratio, degree, v):
+def arnoldi_hessenberg(Sh, k=RITZ_STEPS, Sv=None):
+    """H (k+1 x k) of k Arnoldi steps on |M|^-1/2 Sv |M|^-1/2 from power_start
+    (Sv = S^ unless given, M = diag(S^)), each new direction orthogonalised
+    twice against the basis (classical Gram-Schmidt); stops early (returning
+    the leading block) if a direction vanishes."""
+    Sv = Sh if Sv is None else Sv
+    s = np.sqrt(np.abs(jacobi_inverse(Sh)))
+    N = Sh.shape[0]
+    x = power_start(N)
+    V = np.zeros((k + 1, N))
+    H = np.zeros((k + 1, k))
+    V[0] = x / np.linalg.norm(x)
+    for j in range(k):
+        w = s * (Sv @ (s * V[j]))
+        for _ in range(2):
+            h = V[:j + 1] @ w
+            w = w - V[:j + 1].T @ h
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] == 0.0:
+            return H[:j + 2, :j + 1]
+        V[j + 1] = w / H[j + 1, j]
+    return H
+
+
+def ritz_bounds(Sh, k=RITZ_STEPS, Sv=None):
+    """(lmin, lmax) for the Chebyshev interval from the Ritz values of
+    arnoldi_hessenberg: the eigenvalues of (H_k + H_k^T) / 2, H_k the square
+    leading block."""
+    H = arnoldi_hessenberg(Sh, k, Sv)
+    kk = H.shape[1]
+    Hk = H[:kk, :kk]
+    theta = np.linalg.eigvalsh(0.5 * (Hk + Hk.T))
+    return theta[0] / RITZ_LOW, RITZ_SAFETY * theta[-1]
+
+
+def cheb_interval(bounds, ratio=0.0):
+    """The Chebyshev interval from (lmin, lmax) = ritz_bounds(...): ratio > 0
+    fixes lmin = lmax / ratio; ratio = 0 keeps the estimated lmin, clamped to
+    [lmax / CHEB_MAX_RATIO, lmax / CHEB_MIN_RATIO]."""
+    lmin, lmax = bounds
+    if ratio > 0:
+        return lmax / ratio, lmax
+    return min(max(lmin, lmax / CHEB_MAX_RATIO), lmax / CHEB_MIN_RATIO), lmax
+
+
+def chebyshev_apply(Sh, lmin, lmax, degree, v, Sv=None):
     """degree steps of the Chebyshev iteration for S^ z = v from z = 0 with the
-    Jacobi preconditioner M = diag(S^), on [lmax / ratio, lmax]:
+    Jacobi preconditioner M = diag(S^), on [lmin, lmax]:
         theta = (lmax + lmin) / 2, delta = (lmax - lmin) / 2, sigma = theta / delta,
         r_0 = v, rho_0 = 1 / sigma, d_0 = M^-1 r_0 / theta;
         z_{k+1} = z_k + d_k;  r_{k+1} = r_k - S^ d_k;
         rho_{k+1} = 1 / (2 sigma - rho_k);
         d_{k+1} = rho_{k+1} rho_k d_k + (2 rho_{k+1} / delta) M^-1 r_{k+1}.
     The residual after `degree` steps is T_degree((theta - M^-1 S^) / delta) /
-    T_degree(sigma) applied to v in the M^-1-preconditioned sense."""
+    T_degree(sigma) applied to v in the M^-1-preconditioned sense. Sv, if
+    given, replaces S^ in the products (M stays diag(S^))."""
+    Sv = Sh if Sv is None else Sv
     dinv = jacobi_inverse(Sh)
-    lmin = lmax / ratio
     theta = 0.5 * (lmax + lmin)
     delta = 0.5 * (lmax - lmin)
     sigma = theta / delta
@@ -101,7 +150,7 @@ def chebyshev_apply(Sh, lmax, ratio, degree, v):
         z = z + d
         if k == degree - 1:
             break
-        r = r - Sh @ d
+        r = r - Sv @ d
         rho_n = 1.0 / (2.0 * sigma - rho)
         d = rho_n * rho * d + (2.0 * rho_n / delta) * (dinv * r)
         rho = rho_n

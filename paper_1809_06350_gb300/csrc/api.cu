@@ -158,6 +158,7 @@ int hyel_destroy(hyel_ctx *ctx) {
     cudaStreamSynchronize(ctx->c.stream);
     hyel::free_workspace(ctx->c);
     hyel::amg_free(ctx->c);
+    hyel::shat_free(ctx->c);
     hyel::dfree_all(ctx->c);
     for (auto &r : ctx->c.prof.pending) {
         cudaEventDestroy(r.a);
@@ -210,7 +211,16 @@ int hyel_matrix_download(hyel_ctx *ctx, int32_t *row_ptr, int32_t *col, double *
 int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "spmv: null vector");
-        if (op < HYEL_OP_FULL || op > HYEL_OP_AM) hyel::fail(HYEL_EINVAL, "spmv: bad op");
+        if (op < HYEL_OP_FULL || op > HYEL_OP_SHAT) hyel::fail(HYEL_EINVAL, "spmv: bad op");
+        if (op == HYEL_OP_SHAT) {
+            if (matrix == HYEL_MAT_SCALED64)
+                hyel::shat_spmv<double>(c, (const double *)x, (double *)y);
+            else if (matrix == HYEL_MAT_SCALED32)
+                hyel::shat_spmv<float>(c, (const float *)x, (float *)y);
+            else
+                hyel::fail(HYEL_EINVAL, "spmv: S^ exists as HYEL_MAT_SCALED64 and HYEL_MAT_SCALED32 only");
+            return;
+        }
         if (op == HYEL_OP_AM && (matrix == HYEL_MAT_ASSEMBLED || matrix == HYEL_MAT_TRANSPOSED))
             hyel::fail(HYEL_EINVAL, "spmv: A M^-1 exists for the scaled matrices only");
         if (matrix < HYEL_MAT_ASSEMBLED || matrix > HYEL_MAT_SCALED_BF16S) hyel::fail(HYEL_EINVAL, "spmv: bad matrix");
@@ -267,6 +277,27 @@ int hyel_solve_setup(hyel_ctx *ctx, double *w_out) {
         if (w_out)
             HYEL_CK(cudaMemcpyAsync(w_out, c.mat.w, 4 * c.mesh.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         HYEL_CK(cudaStreamSynchronize(c.stream));
+    });
+}
+
+int hyel_schur_hat_setup(hyel_ctx *ctx, double *bounds_out, int64_t *info, int n_info) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (n_info < 0 || (n_info > 0 && !info)) hyel::fail(HYEL_EINVAL, "schur_hat_setup: bad info array");
+        hyel::shat_setup(c);
+        const hyel::SchurHat &h = *c.sh;
+        if (bounds_out) {
+            bounds_out[0] = h.h_bounds[0];
+            bounds_out[1] = h.h_bounds[1];
+        }
+        const int64_t v[4] = {h.nnz, h.nslots, h.ncontrib, h.max_row};
+        for (int k = 0; k < n_info && k < 4; k++) info[k] = v[k];
+    });
+}
+
+int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio, const double *x, double *y) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!x || !y) hyel::fail(HYEL_EINVAL, "schur_hat_cheb: null vector");
+        hyel::shat_cheb_apply(c, matrix, degree, ratio, x, y);
     });
 }
 

@@ -109,6 +109,7 @@ struct DeviceMatrix {
     bool assembled = false;
     bool scaled = false;
     bool amg_ready = false;   // multigrid operators built from the current scaled A
+    bool shat_ready = false;  // explicit S^ and its bound built from the current scaled blocks
     bool transposed = false;  // At..Dt hold the transpose of the current assembly
 };
 
@@ -137,6 +138,35 @@ struct Profile {
 struct Workspace;  // Krylov workspaces (solver.cu)
 struct Amg;        // multigrid hierarchy of the A-solves (amg.cu)
 
+// Explicit S^ = D - C diag(A)^-1 B of the scaled system (§4.2) on the
+// distance-2 node pattern, SELL-32 like the block pattern: entry p of row i at
+// slot (slice_ptr[i / 32] + p) * 32 + i % 32, columns ascending, padding with
+// column i and value 0 (schur_hat.cu).
+struct SchurHat {
+    int64_t nnz = 0, ncols = 0, nslots = 0, ncontrib = 0;
+    int32_t max_row = 0;
+    int32_t *slice_ptr = nullptr;  // [nslices + 1]
+    int32_t *row_len = nullptr;    // [N]
+    int32_t *col = nullptr;        // [nslots]
+    // contributions of row i, in the order the numeric kernel visits them
+    // (for each block slot (i, k): D_ik, then C_ik A_kk^-1 B_kj for each
+    // block slot (k, j)): cptr[i] .. cptr[i + 1] - 1, pos = entry index in row i
+    int64_t *cptr = nullptr;       // [N + 1]
+    uint16_t *pos = nullptr;       // [ncontrib]
+    double *v64 = nullptr;         // [nslots]
+    float *v32 = nullptr;
+    // Chebyshev interval from the Ritz values of diag(S^)^-1 S^: lmin, lmax
+    double *bounds = nullptr;      // device [2]
+    double h_bounds[2] = {0.0, 0.0};
+    // FP64 scratch of the Arnoldi run and the stand-alone Chebyshev apply
+    double *work = nullptr;        // [3N] (Arnoldi: two directions and |diag(S^)|^-1/2)
+    double *arn_V = nullptr;       // [(steps + 1) N]
+    double *arn_H = nullptr;       // [(steps + 1) steps]
+    double *partial = nullptr;     // [2][steps + 1][grid]
+    unsigned *bar = nullptr;       // barrier words
+    int grid = 0;                  // cooperative grid of the scratch kernels
+};
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -152,6 +182,7 @@ struct Ctx {
     double *h_red = nullptr;     // pinned scalars
     Workspace *ws = nullptr;
     Amg *amg = nullptr;
+    SchurHat *sh = nullptr;
     Profile prof;
     size_t bytes_held = 0;
     int num_sms = 152;
@@ -198,6 +229,12 @@ int amg_levels(const Ctx &c, int64_t *sizes, int max);
 template <typename T>
 void amg_apply(Ctx &c, const T *v, T *z);  // z = V-cycle(v), [3N]
 
+// schur_hat.cu
+void shat_free(Ctx &c);
+void shat_numeric(Ctx &c);  // builds the pattern on first use, then the values of the current scaled blocks
+template <typename T>
+void shat_spmv(Ctx &c, const T *x, T *y);  // y = S^ x, [N]
+
 // sparse.cu
 void solve_setup(Ctx &c);
 void transpose_assembled(Ctx &c);  // fills At..Dt from A..D (mirror slots)
@@ -229,6 +266,9 @@ void spmv_DC_ind(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp
 void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double *x, hyel_solve_stats *st);
 void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y, hyel_solve_stats *st);
 void free_workspace(Ctx &c);
+void shat_bounds(Ctx &c);  // Chebyshev interval of diag(S^)^-1 S^ from Arnoldi Ritz values (host-checked)
+void shat_setup(Ctx &c);  // solve_setup, then S^ and its bound unless current
+void shat_cheb_apply(Ctx &c, int matrix, int degree, double ratio, const double *x, double *y);
 
 // adjoint.cu
 void solve_nested_transpose(Ctx &c, const hyel_solver_params &p, const double *rhs, double *x,

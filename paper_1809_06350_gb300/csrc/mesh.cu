@@ -47,6 +47,7 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     // release the previous mesh and everything sized by it
     free_workspace(c);
     amg_free(c);
+    shat_free(c);
     dfree_all(c);
     c.mesh = DeviceMesh();
     c.mat = DeviceMatrix();
@@ -389,6 +390,7 @@ void mesh_upload(Ctx &c, int64_t N, const double *X, int64_t E, const int32_t *t
         // leave the context empty (no mesh) rather than half-built
         free_workspace(c);
         amg_free(c);
+        shat_free(c);
         dfree_all(c);
         c.mesh = DeviceMesh();
         c.mat = DeviceMatrix();

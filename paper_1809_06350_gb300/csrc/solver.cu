@@ -50,6 +50,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxK = 512;  // largest restart supported by the shared-memory coefficient buffers
+constexpr int kChebMaxDegree = 16;  // largest degree of the Chebyshev S-preconditioner
 constexpr int KC = 8;       // columns per multi-dot chunk
 
 struct LevelState {
@@ -546,12 +547,29 @@ struct PgArgs {
     GmArgs<T> g;
 };
 
-// The S-solve: GMRES on S diag(S^)^-1 (1 value per node), S z = D z - C A^-1 B z
+// Chebyshev polynomial preconditioner on the explicit S^: z = p(M^-1 S^) M^-1 v,
+// M = diag(S^), the interval [lmax / ratio, lmax]
+template <typename T, typename V = float>
+struct ChebArgs {
+    const int32_t *slice_ptr, *row_len, *col;  // S^ pattern (SELL-32)
+    const V *val;                              // S^ values (FP32 in the solver: a preconditioner)
+    const T *dinv;                             // [N] 1 / diag(S^)
+    const double *bounds;                      // device [2]: estimated lmin, lmax
+    double ratio;                              // > 0: lmin = lmax / ratio; 0: the estimate, clamped
+    int degree;
+    T *r;                                      // [N] residual, precision T
+    V *d0, *d1;                                // [N] directions, precision V (the S^ product runs in V)
+};
+
+// The S-solve: GMRES on S P^-1 (1 value per node), S z = D z - C A^-1 B z,
+// P^-1 = diag(S^)^-1 or the Chebyshev polynomial in S^
 template <typename T>
 struct SgArgs {
     const int32_t *slice_ptr, *row_len, *col;
     const T *B, *C, *D, *shat;
     T *xbar, *xtil;  // [3N] right-hand side and solution of the inner A-solve
+    T *zc;           // [N] P^-1 v (Chebyshev only)
+    ChebArgs<T> ch;
     GmArgs<T> g;
 };
 
@@ -777,8 +795,75 @@ __device__ __forceinline__ void pg_row(const PgArgs<T> &a, int64_t i, const T *u
 // nodes (it may run grid barriers of its own, in every block alike);
 // xupd(i, u) adds the preconditioned u = (V y)_i to x_i. phase counts the grid
 // barriers passed so far. false: a barrier gave up.
-template <typename T, int NC, typename Op, typename XUpd>
-__device__ bool pg_gmres(const GmArgs<T> &a, unsigned &phase, Op &&op, XUpd &&xupd) {
+constexpr double kChebMaxRatio = 1000.0, kChebMinRatio = 1.5;  // clamp of the estimated lmax / lmin
+
+// z = p(M^-1 S^) M^-1 (vs v) over the grid: `degree` steps of the Chebyshev
+// iteration for S^ z = vs v from z = 0, Jacobi-preconditioned, on
+// [lmin, lmax] (theta, delta the interval's centre and half-width,
+// sigma = theta / delta):
+//   r = vs v, d = M^-1 r / theta, rho = 1 / sigma; then degree - 1 times
+//   z += d; r -= S^ d; rho' = 1 / (2 sigma - rho);
+//   d = rho' rho d + (2 rho' / delta) M^-1 r; and a last z += d.
+// add: z += instead of z =. v may alias ch.r (each thread reads its own rows
+// before writing them). The directions d and the S^ d product are kept in the
+// value type V (FP32 in the solver: on this GPU an FP64 operation, a
+// conversion included, costs tens of FP32 ones), r and z in T; a fixed
+// operator up to V's rounding, which a preconditioner tolerates. Ends with a
+// grid barrier, so z and the scratch are complete for every block.
+template <typename T, typename V>
+__device__ bool pg_cheb(const ChebArgs<T, V> &ch, int64_t N, const T *v, T vs, T *z, bool add, unsigned *bar,
+                        unsigned &phase) {
+    const double lmax = ch.bounds[1];
+    const double lmin = ch.ratio > 0.0 ? lmax / ch.ratio
+                                       : fmin(fmax(ch.bounds[0], lmax / kChebMaxRatio), lmax / kChebMinRatio);
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    {
+        const T it = (T)(1.0 / theta);
+        PG_FOR_OWN_NODES(N, i) {
+            const T r = v[i] * vs;
+            ch.r[i] = r;
+            const V d = (V)(__ldg(ch.dinv + i) * r * it);
+            ch.d0[i] = d;
+            z[i] = add ? z[i] + (T)d : (T)d;
+        }
+    }
+    if (!pg_barrier(bar, phase)) return false;
+    V *dc = ch.d0, *dn = ch.d1;
+    for (int k = 1; k < ch.degree; k++) {
+        const double rho_n = 1.0 / (2.0 * sigma - rho);
+        const T a1 = (T)(rho_n * rho), a2 = (T)(2.0 * rho_n / delta);
+        PG_FOR_OWN_NODES(N, i) {
+            const int t = (int)(i & 31);
+            const int64_t b0 = __ldg(ch.slice_ptr + (i >> 5));
+            const int len = __ldg(ch.row_len + i);
+            V sd = 0;
+            for (int p = 0; p < len; p++) {
+                const int64_t q = (b0 + p) * 32 + t;
+                sd = fma(__ldg(ch.val + q), dc[__ldg(ch.col + q)], sd);
+            }
+            const T r = ch.r[i] - (T)sd;
+            ch.r[i] = r;
+            const V d = (V)(a1 * (T)dc[i] + a2 * (__ldg(ch.dinv + i) * r));
+            dn[i] = d;
+            z[i] += (T)d;
+        }
+        rho = rho_n;
+        if (!pg_barrier(bar, phase)) return false;
+        V *tmp = dc;
+        dc = dn;
+        dn = tmp;
+    }
+    return true;
+}
+
+// A no-op end-of-cycle step
+struct PgNoEnd {
+    __device__ bool operator()(unsigned &) const { return true; }
+};
+
+template <typename T, int NC, typename Op, typename XUpd, typename XEnd = PgNoEnd>
+__device__ bool pg_gmres(const GmArgs<T> &a, unsigned &phase, Op &&op, XUpd &&xupd, XEnd &&xend = XEnd()) {
     // per-block copies of the small GMRES state (identical in every block)
     __shared__ double s_cs[kMaxK], s_sn[kMaxK], s_g[kMaxK + 1], s_col[kMaxK + 2], s_tmp[kMaxK + 2];
     __shared__ T hs[kMaxK + 2];
@@ -1018,6 +1103,9 @@ __device__ bool pg_gmres(const GmArgs<T> &a, unsigned &phase, Op &&op, XUpd &&xu
                 xupd(i, u);
             }
             __syncthreads();
+            // a preconditioner that is not row-local finishes x here (every
+            // block takes this branch: s_fl is the same in all of them)
+            if (!xend(phase)) return abort_out();
         }
         if (s_fl[1]) {
             if (lead) {
@@ -1106,16 +1194,26 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
 }
 
 // The S-solve of Algorithm 1 (step 3) as one cooperative kernel: GMRES on
-// S diag(S^)^-1 with the matrix-free product of Algorithm 2 inside,
-//   z = diag(S^)^-1 v (applied while gathering), xbar = B z,
+// S P^-1 with the matrix-free product of Algorithm 2 inside,
+//   z = P^-1 v (diag(S^)^-1: applied while gathering; Chebyshev in S^: a few
+//   grid phases of its own), xbar = B z,
 //   xtil = A^-1 xbar (the A-solve above, on the same grid), barrier,
 //   w = D z - C xtil;
-// x = diag(S^)^-1 V y.
-template <typename T, bool H16>
+// x = P^-1 V y.
+template <typename T, bool H16, bool CHEB>
 __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T> a) {
     unsigned phase = 0u;  // the barrier words are cleared before every launch
     const int64_t N = s.g.N;
+    auto zval = [&](const T *u, int64_t c) -> T {
+        if constexpr (CHEB)
+            return s.zc[c];
+        else
+            return __ldg(s.shat + c) * u[c];
+    };
     auto op = [&](const T *u, T sc, T *w, unsigned &ph) {
+        if constexpr (CHEB) {
+            if (!pg_cheb(s.ch, N, u, (T)1, s.zc, false, s.g.bar, ph)) return false;
+        }
         PG_FOR_OWN_NODES(N, i) {
             const int t = (int)(i & 31);
             const int64_t b0 = s.slice_ptr[i >> 5];
@@ -1124,7 +1222,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
             for (int jb = 0; jb < len; jb++) {
                 const int64_t q = (b0 + jb) * 32 + t;
                 const int64_t c = __ldg(s.col + q);
-                const T zc = __ldg(s.shat + c) * u[c];
+                const T zc = zval(u, c);
                 const T *Bb = s.B + (q >> 5) * 96 + t;
                 a0 = fma(__ldg(Bb), zc, a0);
                 a1 = fma(__ldg(Bb + 32), zc, a1);
@@ -1144,7 +1242,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
             for (int jb = 0; jb < len; jb++) {
                 const int64_t q = (b0 + jb) * 32 + t;
                 const int64_t c = __ldg(s.col + q);
-                d = fma(__ldg(s.D + (q >> 5) * 32 + t), __ldg(s.shat + c) * u[c], d);
+                d = fma(__ldg(s.D + (q >> 5) * 32 + t), zval(u, c), d);
                 const T *Cb = s.C + (q >> 5) * 96 + t;
                 m = fma(__ldg(Cb), s.xtil[3 * c], fma(__ldg(Cb + 32), s.xtil[3 * c + 1], fma(__ldg(Cb + 64), s.xtil[3 * c + 2], m)));
             }
@@ -1152,8 +1250,128 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
         }
         return true;
     };
-    auto xupd = [&](int64_t i, const T (&u)[1]) { s.g.x[i] += __ldg(s.shat + i) * u[0]; };
-    pg_gmres<T, 1>(s.g, phase, op, xupd);
+    if constexpr (CHEB) {
+        // V y goes to the Chebyshev residual buffer, then x += P^-1 (V y)
+        auto xupd = [&](int64_t i, const T (&u)[1]) { s.ch.r[i] = u[0]; };
+        auto xend = [&](unsigned &ph) { return pg_cheb(s.ch, N, s.ch.r, (T)1, s.g.x, true, s.g.bar, ph); };
+        pg_gmres<T, 1>(s.g, phase, op, xupd, xend);
+    } else {
+        auto xupd = [&](int64_t i, const T (&u)[1]) { s.g.x[i] += __ldg(s.shat + i) * u[0]; };
+        pg_gmres<T, 1>(s.g, phase, op, xupd);
+    }
+}
+
+// Ritz values for the Chebyshev interval: kRitzSteps steps of Arnoldi on
+// T = |M|^-1/2 S^ |M|^-1/2 (M = diag(S^); T is similar to M^-1 S^ when
+// diag(S^) > 0), FP64 vectors with the FP32 copy of S^ (an estimate), one
+// cooperative launch. The start vector comes from
+// SplitMix64 (Steele, Lea and Flood 2014): output i of the generator seeded
+// with 0 gives x0[i] = 2 u - 1, u its top 53 bits over 2^53. Each new
+// direction is orthogonalised twice against the basis (classical
+// Gram-Schmidt); block 0 writes the Hessenberg columns H[j * (k + 1) + i].
+// The host takes the eigenvalues of the symmetric part of the leading k x k
+// block. V: [(k + 1) N]; U: [2N] (the unnormalised new direction, double-
+// buffered: a step gathers the previous one while writing the next); Sq: [N].
+constexpr int kRitzSteps = 12;
+constexpr double kRitzSafety = 1.05, kRitzLow = 2.0;  // lmax = 1.05 theta_max, lmin = theta_min / 2
+
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long k) {
+    unsigned long long z = (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct ArnArgs {
+    const int32_t *slice_ptr, *row_len, *col;
+    const float *val;
+    const double *dinv;
+    double *V, *U, *Sq, *H, *partial;  // U: [2N]; Sq: [N] |diag(S^)|^-1/2
+    unsigned *bar;
+    int64_t N;
+};
+
+__global__ void __launch_bounds__(kPgThreads) k_shat_arnoldi(ArnArgs a) {
+    __shared__ double red1[kPgThreads / 32];
+    __shared__ double s_sum[kRitzSteps + 2], s_h[kRitzSteps + 2];
+    __shared__ double hs[kRitzSteps + 2];
+    unsigned phase = 0u;
+    const int64_t N = a.N;
+    const int G = gridDim.x, K1 = kRitzSteps + 1;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    auto pbuf = [&](unsigned ph) { return a.partial + (size_t)(ph & 1u) * G * K1; };
+    auto fail_out = [&]() {
+        if (lead) a.H[0] = nan("");
+    };
+    double ss = 0.0;
+    PG_FOR_OWN_NODES(N, i) {
+        const double x = 2.0 * ((double)(splitmix64_at((unsigned long long)i) >> 11) * 0x1p-53) - 1.0;
+        a.U[i] = x;
+        a.Sq[i] = sqrt(fabs(__ldg(a.dinv + i)));
+        ss = fma(x, x, ss);
+    }
+    double tb = pg_block_sum<double>(ss, red1);
+    if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
+    if (!pg_barrier(a.bar, phase)) return fail_out();
+    pg_sum(pbuf(phase - 1), 1, s_sum);
+    __syncthreads();
+    double sc = 1.0 / sqrt(s_sum[0]);
+    for (int j = 0; j < kRitzSteps; j++) {
+        const double *u = a.U + (size_t)(j & 1) * N;
+        double *w = a.U + (size_t)((j + 1) & 1) * N;
+        double *Vj = a.V + (size_t)j * N;
+        // v_j = sc u; w = T v_j
+        PG_FOR_OWN_NODES(N, i) {
+            Vj[i] = u[i] * sc;
+            const int t = (int)(i & 31);
+            const int64_t b0 = __ldg(a.slice_ptr + (i >> 5));
+            const int len = __ldg(a.row_len + i);
+            double acc = 0.0;
+            for (int p = 0; p < len; p++) {
+                const int64_t q = (b0 + p) * 32 + t;
+                const int64_t c = __ldg(a.col + q);
+                acc = fma((double)__ldg(a.val + q), a.Sq[c] * u[c], acc);
+            }
+            w[i] = a.Sq[i] * acc * sc;
+        }
+        // two classical Gram-Schmidt passes, then ||w||
+        for (int l = threadIdx.x; l <= j; l += blockDim.x) s_h[l] = 0.0;
+        for (int pass = 0; pass < 2; pass++) {
+            pg_dots<double, 1>(a.V, w, N, j + 1, false, pbuf(phase));
+            if (!pg_barrier(a.bar, phase)) return fail_out();
+            pg_sum(pbuf(phase - 1), j + 1, s_sum);
+            __syncthreads();
+            for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+                hs[l] = s_sum[l];
+                s_h[l] += s_sum[l];
+            }
+            __syncthreads();
+            const double part = pg_axpy<double, 1>(a.V, w, N, j + 1, hs);
+            if (pass == 1) {
+                tb = pg_block_sum<double>(part, red1);
+                if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
+            }
+        }
+        if (!pg_barrier(a.bar, phase)) return fail_out();
+        pg_sum(pbuf(phase - 1), 1, s_sum);
+        __syncthreads();
+        const double hn = sqrt(s_sum[0]);
+        if (lead) {
+            for (int l = 0; l <= j; l++) a.H[(size_t)j * K1 + l] = s_h[l];
+            a.H[(size_t)j * K1 + j + 1] = hn;
+        }
+        if (!(hn > 0.0)) return;  // invariant subspace (or NaN): the host reads the leading block
+        sc = 1.0 / hn;
+    }
+}
+
+// y = p(M^-1 S^) M^-1 x (FP64, one cooperative launch); status 8 on a barrier timeout
+template <typename V>
+__global__ void __launch_bounds__(kPgThreads) k_cheb_apply(ChebArgs<double, V> ch, const double *x, double *y,
+                                                           int64_t N, unsigned *bar, unsigned *status) {
+    unsigned phase = 0u;
+    if (!pg_cheb(ch, N, x, 1.0, y, false, bar, phase) && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicOr(status, 8u);
 }
 
 // ------------------------------------------------------------ recording
@@ -1256,6 +1474,7 @@ struct Level {
     double *pg_partial = nullptr;
     unsigned *bar = nullptr;
     int pg_grid = 0, pg_grid16 = 0;
+    int pg_gridc = 0, pg_grid16c = 0;  // S-level with the Chebyshev preconditioner
 };
 
 }  // namespace
@@ -1346,17 +1565,26 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
         if (kind == 0)
             HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_a<T, false>, kPgThreads, 0));
         else
-            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_s<T, false>, kPgThreads, 0));
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_s<T, false, false>, kPgThreads, 0));
         occ16 = occ;
         if constexpr (std::is_same<T, float>::value) {
             if (kind == 0)
                 HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_a<float, true>, kPgThreads, 0));
             else
-                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_s<float, true>, kPgThreads, 0));
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_s<float, true, false>, kPgThreads, 0));
         }
-        if (occ < 1 || occ16 < 1) fail(HYEL_ECUDA, "persistent solve kernel does not fit on an SM");
+        int occc = occ, occ16c = occ16;
+        if (kind == 1) {
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occc, k_gmres_s<T, false, true>, kPgThreads, 0));
+            occ16c = occc;
+            if constexpr (std::is_same<T, float>::value)
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16c, k_gmres_s<float, true, true>, kPgThreads, 0));
+        }
+        if (occ < 1 || occ16 < 1 || occc < 1 || occ16c < 1) fail(HYEL_ECUDA, "persistent solve kernel does not fit on an SM");
         L.pg_grid = (int)std::min<int64_t>((int64_t)occ * c.num_sms, need);
         L.pg_grid16 = (int)std::min<int64_t>((int64_t)occ16 * c.num_sms, need);
+        L.pg_gridc = (int)std::min<int64_t>((int64_t)occc * c.num_sms, need);
+        L.pg_grid16c = (int)std::min<int64_t>((int64_t)occ16c * c.num_sms, need);
         const int64_t gmax = (int64_t)(2048 / kPgThreads) * c.num_sms;  // any co-resident grid
         L.pg_partial = (double *)walloc(c, w, sizeof(double) * 2 * (size_t)gmax * (m + 1));
     }
@@ -1399,6 +1627,12 @@ Workspace &workspace(Ctx &c, const hyel_solver_params &p) {
     return *w;
 }
 
+void check_cheb(int degree, double ratio) {
+    if (degree < 1 || degree > kChebMaxDegree) fail(HYEL_EINVAL, "solver params: s_cheb_degree must be in [1, 16]");
+    if (!(ratio == 0.0 || ratio > 1.0) || !std::isfinite(ratio))
+        fail(HYEL_EINVAL, "solver params: s_cheb_ratio must be 0 (estimated) or finite and > 1");
+}
+
 void check_params(const hyel_solver_params &p) {
     const hyel_krylov_level *lv[4] = {&p.outer, &p.a, &p.s, &p.inner};
     for (auto *l : lv) {
@@ -1411,6 +1645,13 @@ void check_params(const hyel_solver_params &p) {
     if (p.check_every < 1) fail(HYEL_EINVAL, "solver params: check_every must be >= 1");
     if (p.a_precond != HYEL_APREC_BJACOBI && p.a_precond != HYEL_APREC_AMG)
         fail(HYEL_EINVAL, "solver params: bad a_precond");
+    if (p.s_precond != HYEL_SPREC_JACOBI && p.s_precond != HYEL_SPREC_CHEB)
+        fail(HYEL_EINVAL, "solver params: bad s_precond");
+    if (p.s_precond == HYEL_SPREC_CHEB) {
+        if (p.a_precond != HYEL_APREC_BJACOBI)
+            fail(HYEL_EINVAL, "solver params: the Chebyshev S-preconditioner needs block-Jacobi A-solves");
+        check_cheb(p.s_cheb_degree, p.s_cheb_ratio);
+    }
 }
 
 bool same_params(const hyel_solver_params &a, const hyel_solver_params &b) {
@@ -1596,6 +1837,29 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
     prof_end(c, HYEL_K_GMRES_A, ev, 0.0);  // bytes are added from the level states after the solve
 }
 
+// Chebyshev arguments on the explicit S^ (built by shat_setup): vectors of
+// precision T, values V (FP32 in the solver, either in the stand-alone apply)
+template <typename T, typename V = float>
+ChebArgs<T, V> cheb_args(Ctx &c, int degree, double ratio, T *r, V *d0, V *d1) {
+    const SchurHat &h = *c.sh;
+    ChebArgs<T, V> ch;
+    ch.slice_ptr = h.slice_ptr;
+    ch.row_len = h.row_len;
+    ch.col = h.col;
+    if constexpr (std::is_same<V, double>::value)
+        ch.val = h.v64;
+    else
+        ch.val = h.v32;
+    ch.dinv = Sys<T>::shat(c);
+    ch.bounds = h.bounds;
+    ch.ratio = ratio;
+    ch.degree = degree;
+    ch.r = r;
+    ch.d0 = d0;
+    ch.d1 = d1;
+    return ch;
+}
+
 // The S-solve of Algorithm 1 step 3 as one cooperative launch of k_gmres_s
 // (the inner A-solves of Algorithm 2 run inside it on the A-level buffers)
 template <typename T>
@@ -1618,6 +1882,16 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
     sg.shat = Sys<T>::shat(c);
     sg.xbar = xbar;
     sg.xtil = xtil;
+    const bool cheb = p.s_precond == HYEL_SPREC_CHEB;
+    sg.zc = nullptr;
+    sg.ch = ChebArgs<T>{};
+    if (cheb) {
+        // [N] buffers from workspace vector 11 (used otherwise only by multigrid A-solves)
+        T *cb = Sys<T>::vec(w, 11, N);
+        float *db = reinterpret_cast<float *>(cb + 2 * N);  // 2N floats fit in 2N T
+        sg.zc = cb;
+        sg.ch = cheb_args<T>(c, p.s_cheb_degree, p.s_cheb_ratio, cb + N, db, db + N);
+    }
     GmArgs<T> &g = sg.g;
     g.N = N;
     g.b = b;
@@ -1638,8 +1912,16 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
     // indices (twice), and the vector passes over [N]-vectors
     g.it_fixed = (double)msh.nnzb * (7.0 * sizeof(T) + 8.0) + 4.0 * (N + 1);
     g.it_unit = (double)N * sizeof(T);
+    if (cheb) {
+        // per application: degree - 1 S^ products (FP32 values and columns, x
+        // gathered) and the row-local passes (3 + 6 (degree - 1) vectors of [N])
+        const SchurHat &h = *c.sh;
+        const int d = p.s_cheb_degree;
+        g.it_fixed += (d - 1) * ((double)h.nnz * 8.0 + (double)N * (sizeof(T) + 8.0)) +
+                      (3.0 + 6.0 * (d - 1)) * (double)N * sizeof(T);
+    }
     HYEL_CK(cudaMemsetAsync(La.bar, 0, kBarWords * sizeof(unsigned), c.stream));
-    cudaLaunchConfig_t cfg = coop_config(c, h16 ? Ls.pg_grid16 : Ls.pg_grid);
+    cudaLaunchConfig_t cfg = coop_config(c, cheb ? (h16 ? Ls.pg_grid16c : Ls.pg_gridc) : (h16 ? Ls.pg_grid16 : Ls.pg_grid));
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
     at[0].val.cooperative = 1;
@@ -1650,11 +1932,19 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
     bool launched = false;
     if constexpr (std::is_same<T, float>::value) {
         if (h16) {
-            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true>, sg, a));
+            if (cheb)
+                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, true>, sg, a));
+            else
+                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, false>, sg, a));
             launched = true;
         }
     }
-    if (!launched) HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false>, sg, a));
+    if (!launched) {
+        if (cheb)
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true>, sg, a));
+        else
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false>, sg, a));
+    }
     count_launch();
     prof_end(c, HYEL_K_GMRES_S, ev, 0.0);
 }
@@ -1803,6 +2093,7 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
         amg_numeric(c);
         c.mat.amg_ready = true;
     }
+    if (p.s_precond == HYEL_SPREC_CHEB) shat_setup(c);
     Workspace &w = workspace(c, p);
     if (p.graph) ensure_graph(c, w, p);
     HYEL_CK(cudaStreamSynchronize(c.stream));
@@ -1875,6 +2166,156 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
                                                    : "solve failed";
         fail(st, std::string("solve_nested: ") + what);
     }
+}
+
+namespace {
+
+int coop_grid(Ctx &c, const void *kernel) {
+    int occ = 0;
+    HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kPgThreads, 0));
+    if (occ < 1) fail(HYEL_ECUDA, "schur_hat: cooperative kernel does not fit on an SM");
+    const int64_t need = std::max<int64_t>(1, (c.mesh.N + 31) / 32);
+    return (int)std::min<int64_t>((int64_t)occ * c.num_sms, need);
+}
+
+void coop_launch(Ctx &c, int grid, const void *kernel, void **args) {
+    HYEL_CK(cudaLaunchCooperativeKernel(kernel, dim3((unsigned)grid), dim3(kPgThreads), args, 0, c.stream));
+    count_launch();
+}
+
+}  // namespace
+
+// Eigenvalues of a small symmetric matrix (n x n, row-major, overwritten) by
+// cyclic Jacobi rotations (Golub and Van Loan, Matrix Computations, §8.5):
+// each rotation zeroes one off-diagonal pair; sweeps until the off-diagonal
+// part is negligible against the whole.
+static void sym_eigenvalues(std::vector<double> &a, int n, std::vector<double> &ev) {
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0.0, all = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = 0; q < n; q++) {
+                all += a[p * n + q] * a[p * n + q];
+                if (p != q) off += a[p * n + q] * a[p * n + q];
+            }
+        if (off <= 1e-30 * all || off == 0.0) break;
+        for (int p = 0; p < n - 1; p++)
+            for (int q = p + 1; q < n; q++) {
+                const double apq = a[p * n + q];
+                if (apq == 0.0) continue;
+                const double th = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int r = 0; r < n; r++) {  // columns p, q
+                    const double x = a[r * n + p], y = a[r * n + q];
+                    a[r * n + p] = cs * x - sn * y;
+                    a[r * n + q] = sn * x + cs * y;
+                }
+                for (int r = 0; r < n; r++) {  // rows p, q
+                    const double x = a[p * n + r], y = a[q * n + r];
+                    a[p * n + r] = cs * x - sn * y;
+                    a[q * n + r] = sn * x + cs * y;
+                }
+            }
+    }
+    ev.resize(n);
+    for (int p = 0; p < n; p++) ev[p] = a[p * n + p];
+    std::sort(ev.begin(), ev.end());
+}
+
+void shat_bounds(Ctx &c) {
+    SchurHat &h = *c.sh;
+    const int64_t N = c.mesh.N;
+    const int K1 = kRitzSteps + 1;
+    const int grid = coop_grid(c, (const void *)k_shat_arnoldi);
+    const size_t gmax = (size_t)(2048 / kPgThreads) * c.num_sms;
+    if (!h.partial) h.partial = dalloc_n<double>(c, 2 * gmax * K1);
+    if (!h.arn_V) h.arn_V = dalloc_n<double>(c, (size_t)K1 * N);
+    if (!h.arn_H) h.arn_H = dalloc_n<double>(c, (size_t)K1 * kRitzSteps);
+    ArnArgs a;
+    a.slice_ptr = h.slice_ptr;
+    a.row_len = h.row_len;
+    a.col = h.col;
+    a.val = h.v32;
+    a.dinv = c.mat.shat64;
+    a.V = h.arn_V;
+    a.U = h.work;
+    a.Sq = h.work + 2 * N;
+    a.H = h.arn_H;
+    a.partial = h.partial;
+    a.bar = h.bar;
+    a.N = N;
+    HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    HYEL_CK(cudaMemsetAsync(h.arn_H, 0, sizeof(double) * K1 * kRitzSteps, c.stream));
+    void *args[] = {&a};
+    coop_launch(c, grid, (const void *)k_shat_arnoldi, args);
+    std::vector<double> H((size_t)K1 * kRitzSteps);
+    HYEL_CK(cudaMemcpyAsync(H.data(), h.arn_H, sizeof(double) * H.size(), cudaMemcpyDeviceToHost, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    if (!std::isfinite(H[0])) fail(HYEL_ENAN, "schur_hat: Arnoldi on S^ met NaN/Inf (or a grid barrier timed out)");
+    // leading block up to the first vanishing subdiagonal entry
+    int k = kRitzSteps;
+    for (int j = 0; j < kRitzSteps; j++) {
+        for (int l = 0; l <= j + 1; l++)
+            if (!std::isfinite(H[(size_t)j * K1 + l])) fail(HYEL_ENAN, "schur_hat: Arnoldi on S^ met NaN/Inf");
+        if (!(H[(size_t)j * K1 + j + 1] > 0.0)) {
+            k = j + 1;
+            break;
+        }
+    }
+    std::vector<double> S((size_t)k * k), ev;
+    for (int r = 0; r < k; r++)
+        for (int q = 0; q < k; q++) S[r * k + q] = 0.5 * (H[(size_t)q * K1 + r] + H[(size_t)r * K1 + q]);
+    sym_eigenvalues(S, k, ev);
+    if (!(ev.back() > 0.0)) fail(HYEL_ENAN, "schur_hat: diag(S^)^-1 S^ has no positive Ritz value");
+    double b[2] = {ev.front() / kRitzLow, kRitzSafety * ev.back()};
+    h.h_bounds[0] = b[0];
+    h.h_bounds[1] = b[1];
+    HYEL_CK(cudaMemcpy(h.bounds, b, sizeof b, cudaMemcpyHostToDevice));
+}
+
+void shat_setup(Ctx &c) {
+    solve_setup(c);
+    if (c.mat.shat_ready) return;
+    cudaEvent_t ev;
+    prof_begin(c, HYEL_K_SCHUR_HAT, &ev);
+    shat_numeric(c);
+    const SchurHat &h = *c.sh;
+    const DeviceMesh &m = c.mesh;
+    // numeric: D, C, column and diag(A) per block slot, B per neighbour slot,
+    // positions, rows written in FP64 and FP32; Arnoldi: S^ and the basis
+    // passes per step
+    const double bytes = (double)m.nnzb * (8.0 + 24.0 + 4.0 + 24.0) + (double)m.N * (24.0 + 8.0) +
+                         2.0 * (double)h.ncontrib + 12.0 * (double)h.nslots +
+                         kRitzSteps * ((double)h.nnz * 8.0 + (double)m.N * (16.0 + 8.0 * (2 * kRitzSteps + 4)));
+    shat_bounds(c);
+    prof_end(c, HYEL_K_SCHUR_HAT, ev, bytes);
+    c.mat.shat_ready = true;
+}
+
+void shat_cheb_apply(Ctx &c, int matrix, int degree, double ratio, const double *x, double *y) {
+    check_cheb(degree, ratio);
+    if (matrix != HYEL_MAT_SCALED64 && matrix != HYEL_MAT_SCALED32)
+        fail(HYEL_EINVAL, "schur_hat_cheb: matrix must be HYEL_MAT_SCALED64 or HYEL_MAT_SCALED32");
+    if (!c.sh || !c.mat.shat_ready) fail(HYEL_ESTATE, "schur_hat: S^ is not built for the current assembly");
+    SchurHat &h = *c.sh;
+    const int64_t N = c.mesh.N;
+    unsigned *bar = h.bar, *status = c.err;
+    int64_t n = N;
+    HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
+    if (matrix == HYEL_MAT_SCALED64) {
+        ChebArgs<double, double> ch = cheb_args<double, double>(c, degree, ratio, h.work, h.work + N, h.work + 2 * N);
+        void *args[] = {&ch, (void *)&x, (void *)&y, &n, &bar, &status};
+        coop_launch(c, coop_grid(c, (const void *)k_cheb_apply<double>), (const void *)k_cheb_apply<double>, args);
+    } else {
+        float *db = reinterpret_cast<float *>(h.work + N);
+        ChebArgs<double, float> ch = cheb_args<double, float>(c, degree, ratio, h.work, db, db + N);
+        void *args[] = {&ch, (void *)&x, (void *)&y, &n, &bar, &status};
+        coop_launch(c, coop_grid(c, (const void *)k_cheb_apply<float>), (const void *)k_cheb_apply<float>, args);
+    }
+    HYEL_CK(cudaMemcpyAsync(c.h_err, c.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    if (*c.h_err & 8u) fail(HYEL_ECUDA, "schur_hat: a grid barrier timed out");
 }
 
 void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y, hyel_solve_stats *out) {

@@ -526,6 +526,7 @@ void solve_setup(Ctx &c) {
     if (*c.h_err & ERR_SINGULAR) fail(HYEL_ESINGULAR, "solve_setup: a 3x3 diagonal block of A is singular");
     c.mat.scaled = true;
     c.mat.amg_ready = false;
+    c.mat.shat_ready = false;
 }
 
 void transpose_assembled(Ctx &c) {

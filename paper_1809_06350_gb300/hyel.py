@@ -21,12 +21,14 @@ HYEL_EBREAKDOWN, HYEL_ENAN, HYEL_EINVERTED, HYEL_ESINGULAR, HYEL_ESTATE = -5, -6
 HYEL_VOL_GIBBS, HYEL_VOL_INCOMPRESSIBLE = 0, 1
 HYEL_PREC_FP64, HYEL_PREC_FP32, HYEL_PREC_BF16S = 0, 1, 2
 HYEL_APREC_BJACOBI, HYEL_APREC_AMG = 0, 1
-HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D, HYEL_OP_AM = 0, 1, 2, 3, 4, 5
+HYEL_SPREC_JACOBI, HYEL_SPREC_CHEB = 0, 1
+HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D, HYEL_OP_AM, HYEL_OP_SHAT = 0, 1, 2, 3, 4, 5, 6
 HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32, HYEL_MAT_TRANSPOSED, HYEL_MAT_SCALED_BF16S = 0, 1, 2, 3, 4
 (HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER, HYEL_K_SPMV_A16,
- HYEL_K_GMRES_A, HYEL_K_GMRES_S) = range(8)
-HYEL_K_NCLASSES = 8
-K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather", "spmv_A16", "gmres_A", "gmres_S"]
+ HYEL_K_GMRES_A, HYEL_K_GMRES_S, HYEL_K_SCHUR_HAT) = range(9)
+HYEL_K_NCLASSES = 9
+K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather", "spmv_A16", "gmres_A", "gmres_S",
+           "schur_hat"]
 
 # every symbol include/hyel.h declares
 EXPORTS = [
@@ -35,6 +37,7 @@ EXPORTS = [
     "hyel_schur_apply", "hyel_solve_nested", "hyel_newton_step", "hyel_profile", "hyel_profile_read",
     "hyel_launch_count", "hyel_residual_norm_static", "hyel_update_material",
     "hyel_solve_nested_transpose", "hyel_param_sensitivity", "hyel_adjoint_step",
+    "hyel_schur_hat_setup", "hyel_schur_hat_cheb",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -70,7 +73,8 @@ class HyelKrylovLevel(C.Structure):
 class HyelSolverParams(C.Structure):
     _fields_ = [("outer", HyelKrylovLevel), ("a", HyelKrylovLevel), ("s", HyelKrylovLevel),
                 ("inner", HyelKrylovLevel), ("precision", C.c_int32), ("check_every", C.c_int32),
-                ("graph", C.c_int32), ("a_precond", C.c_int32)]
+                ("graph", C.c_int32), ("a_precond", C.c_int32), ("s_precond", C.c_int32),
+                ("s_cheb_degree", C.c_int32), ("s_cheb_ratio", C.c_double)]
 
 
 class HyelSolveStats(C.Structure):
@@ -138,6 +142,8 @@ def lib():
             "hyel_adjoint_step": (C.c_int, [vp, C.POINTER(HyelTimeParams), C.POINTER(HyelSolverParams),
                                             C.POINTER(HyelState), C.POINTER(HyelState), vp, vp, vp, vp,
                                             C.POINTER(HyelSolveStats)]),
+            "hyel_schur_hat_setup": (C.c_int, [vp, _dp, C.POINTER(C.c_int64), C.c_int]),
+            "hyel_schur_hat_cheb": (C.c_int, [vp, C.c_int, C.c_int32, C.c_double, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -225,6 +231,20 @@ def hyel_solve_setup(ctx, w_out=0):
     return _check(ctx, lib().hyel_solve_setup(ctx, C.c_void_p(w_out or 0)))
 
 
+def hyel_schur_hat_setup(ctx):
+    """Builds the explicit S^ of the current scaled system; returns
+    ((lmin, lmax) estimated for the Chebyshev interval, info dict)."""
+    b = (C.c_double * 2)()
+    info = (C.c_int64 * 4)()
+    _check(ctx, lib().hyel_schur_hat_setup(ctx, b, info, 4))
+    return (b[0], b[1]), {"nnz": info[0], "slots": info[1], "contributions": info[2], "max_row": info[3]}
+
+
+def hyel_schur_hat_cheb(ctx, degree, ratio, x_ptr, y_ptr, matrix=HYEL_MAT_SCALED64):
+    _check(ctx, lib().hyel_schur_hat_cheb(ctx, int(matrix), int(degree), float(ratio), C.c_void_p(x_ptr),
+                                          C.c_void_p(y_ptr)))
+
+
 def hyel_schur_apply(ctx, params, x_ptr, y_ptr):
     st = HyelSolveStats()
     _check(ctx, lib().hyel_schur_apply(ctx, C.byref(params), C.c_void_p(x_ptr), C.c_void_p(y_ptr), C.byref(st)))
@@ -307,13 +327,16 @@ def level(rtol, maxit, restart, atol=1e-50):
 
 def solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=HYEL_PREC_FP64, outer=(200, 200),
                   a=(500, 500), s=(200, 200), inner=(500, 500), check_every=4, inner_rtol=None, graph=1,
-                  a_precond=0):
+                  a_precond=0, s_precond=0, s_cheb_degree=4, s_cheb_ratio=0.0):
     """Solver controls with the paper's defaults (§5: FGMRES(200), A: GMRES(500),
     S: GMRES(200), inner GMRES(500), absolute tolerances 1e-50). a_precond:
-    HYEL_APREC_BJACOBI (default) or HYEL_APREC_AMG."""
+    HYEL_APREC_BJACOBI (default) or HYEL_APREC_AMG; s_precond: HYEL_SPREC_JACOBI
+    (default) or HYEL_SPREC_CHEB (degree s_cheb_degree on [lmin, lmax] from Ritz
+    estimates, or on [lmax / s_cheb_ratio, lmax] when s_cheb_ratio > 1)."""
     ir = sub_rtol if inner_rtol is None else inner_rtol
     return HyelSolverParams(level(outer_rtol, *outer), level(sub_rtol, *a), level(sub_rtol, *s),
-                            level(ir, *inner), precision, check_every, graph, a_precond)
+                            level(ir, *inner), precision, check_every, graph, a_precond, s_precond,
+                            s_cheb_degree, s_cheb_ratio)
 
 
 def time_params(dt=1e-3, t_n=0.0, rho_inf=0.5, tol_r=1e-6, tol_a=1e-6, l_max=20, rhs_literal=0):

@@ -9,13 +9,18 @@ solver, FP64 and FP32 preconditioner levels).
 * Newton step: the oracle's residual at the GPU's converged state satisfies
   the stopping test ||R||/||R_(0)|| <= tol_R (a property any correct step has,
   at any size); FP32 preconditioner levels, and FP32 levels with the BF16 A,
-  reach the FP64 state to 1e-9.
+  reach the FP64 state to 1e-9; so do FP64 and BF16S levels with the
+  Chebyshev S-preconditioner on the explicit S^.
+* Explicit S^: 8 sampled columns (boundary nodes included) against the
+  oracle's S^ built from the tangent rows of their distance-2 neighbourhoods.
 """
 import numpy as np
+import scipy.sparse as sp
 import pytest
 import torch
 
 from paper_1809_06350_gb300 import hyel as H, inputs
+from oracle import schur_hat as SH
 from oracle import system as S
 
 pytestmark = pytest.mark.gpu
@@ -91,10 +96,12 @@ def test_fullsize_newton_step_fp64_and_fp32(big):
     ydz = {k: z[k] for k in ("udot", "pdot", "vdot")}
     norm0 = _oracle_norm(prob, yz, ydz, yz, ydz, 0.0)  # predictor from rest: y1 = 0, ydot1 = 0
     finals = {}
-    for prec in (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S):
+    runs = ((H.HYEL_PREC_FP64, 0), (H.HYEL_PREC_FP32, 0), (H.HYEL_PREC_BF16S, 0),
+            (H.HYEL_PREC_FP64, H.HYEL_SPREC_CHEB), (H.HYEL_PREC_BF16S, H.HYEL_SPREC_CHEB))
+    for prec, sprec in runs:
         dev = {k: gp.dev(z[k]) for k in z}
         state = H.state_struct(dev["u"], dev["p"], dev["v"], dev["udot"], dev["pdot"], dev["vdot"])
-        sp_ = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=prec, graph=1)
+        sp_ = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=prec, graph=1, s_precond=sprec)
         st, rc = H.hyel_newton_step(gp.ctx, H.time_params(dt=DT, t_n=0.0), sp_, state)
         assert st.converged
         y1 = {k: dev[k].cpu().numpy().reshape(z[k].shape) for k in ("u", "p", "v")}
@@ -103,8 +110,51 @@ def test_fullsize_newton_step_fp64_and_fp32(big):
         assert st.res_norm0 == pytest.approx(norm0, rel=1e-12)
         assert nrm / norm0 <= 1e-6
         assert abs(nrm - st.res_norm) <= 1e-12 * norm0
-        finals[prec] = np.concatenate([y1[k].ravel() for k in ("u", "p", "v")] +
-                                      [yd1[k].ravel() for k in ("udot", "pdot", "vdot")])
-    f64 = finals[H.HYEL_PREC_FP64]
-    for prec in (H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S):
-        assert np.linalg.norm(finals[prec] - f64) / np.linalg.norm(f64) <= 1e-9, prec
+        finals[(prec, sprec)] = np.concatenate([y1[k].ravel() for k in ("u", "p", "v")] +
+                                               [yd1[k].ravel() for k in ("udot", "pdot", "vdot")])
+    f64 = finals[(H.HYEL_PREC_FP64, 0)]
+    for key in runs[1:]:
+        assert np.linalg.norm(finals[key] - f64) / np.linalg.norm(f64) <= 1e-9, key
+
+
+def test_fullsize_schur_hat_sampled_columns(big):
+    gp = big
+    prob, N = gp.prob, gp.N
+    h = 1.0 / 48
+    st = inputs.random_state(N, seed=5, u_scale=0.02 * h, v_scale=0.02, p_scale=1e3, rate_scale=2.0)
+    dev, sst = gp.stage(st)
+    H.hyel_assemble(gp.ctx, H.time_params(dt=DT, t_n=2 * DT), sst, 0, 0)
+    (lmin, lmax), info = H.hyel_schur_hat_setup(gp.ctx)
+    assert 0 < lmin < lmax and np.isfinite(lmax)
+    am, af, gam = S.gen_alpha(0.5)
+    ga = (am, af, gam, DT)
+    tets = prob.tets
+    adj = sp.csr_matrix((np.ones(16 * len(tets)), (np.repeat(tets, 4, axis=1).ravel(), np.tile(tets, (1, 4)).ravel())),
+                        shape=(N, N))
+    adj.data[:] = 1.0
+    assert info["nnz"] == (adj @ adj).nnz
+    rng = np.random.default_rng(13)
+    cols = np.unique(np.concatenate([rng.choice(N, 4, replace=False), [0, 48, N - 1, N // 2]]))
+    for j in cols:
+        n1 = adj[j].indices
+        n2 = np.unique(adj[n1].indices)
+        K = S.assemble_rows(prob, st, ga, n2)
+        Kd, _ = S.apply_dirichlet(K, np.zeros(4 * N), S.dirichlet_dofs(prob))
+        wo = S.diag_scaling(Kd)
+        Ks = (sp.diags(wo) @ Kd @ sp.diags(wo)).tocsr()
+        with np.errstate(divide="ignore"):
+            Sh = SH.schur_hat(Ks, N)
+        A, B, C, D = S.split_blocks(Ks, N)
+        dA = np.abs(A.diagonal())
+        dA[dA == 0] = 1.0
+        Sb = (abs(D) + abs(C) @ sp.diags(1.0 / dA) @ abs(B)).tocsr()
+        e = torch.zeros(N, dtype=torch.float64, device="cuda")
+        e[int(j)] = 1.0
+        y = torch.zeros(N, dtype=torch.float64, device="cuda")
+        H.hyel_spmv(gp.ctx, H.HYEL_OP_SHAT, H.HYEL_MAT_SCALED64, e.data_ptr(), y.data_ptr())
+        yg = y.cpu().numpy()
+        ref = Sh[:, [j]].toarray().ravel()[n2]
+        bound = Sb[:, [j]].toarray().ravel()[n2]
+        assert np.all(np.abs(yg[n2] - ref) <= 1e-12 * bound.max()), j
+        outside = np.setdiff1d(np.arange(N), n2)
+        assert np.all(yg[outside] == 0.0), j

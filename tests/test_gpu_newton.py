@@ -56,7 +56,9 @@ def test_two_newton_steps_match_oracle(precision):
 def test_poisson_sweep_newton_step_matches_oracle(nu):
     """The Poisson-ratio sweep of the cube workload (kappa from nu; nu = 0.5
     is the incompressible model): one Newton step under the ramped dead load
-    matches the oracle's direct-solve Newton step, FP64 and FP32 levels."""
+    matches the oracle's direct-solve Newton step: FP64 and FP32 levels with
+    the diag(S^) S-preconditioner, FP64 and BF16S levels with the Chebyshev
+    polynomial in the explicit S^."""
     m = inputs.cube_mesh(6)
     mat = inputs.material_nh(1e5, inputs.kappa_from_nu(1e5, nu), 1e3)
     load = {"p_max": 2e4, "t_ramp": 10 * DT}
@@ -67,14 +69,15 @@ def test_poisson_sweep_newton_step_matches_oracle(nu):
     ydz = {k: z[k] for k in ("udot", "pdot", "vdot")}
     y1, yd1, info = Nw.newton_step(prob, yz, ydz, 0.0, DT, tol_r=1e-10, tol_a=1e-12)
     assert info["converged"]
-    for precision in (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32):
+    for precision, sprec in ((H.HYEL_PREC_FP64, H.HYEL_SPREC_JACOBI), (H.HYEL_PREC_FP32, H.HYEL_SPREC_JACOBI),
+                             (H.HYEL_PREC_FP64, H.HYEL_SPREC_CHEB), (H.HYEL_PREC_BF16S, H.HYEL_SPREC_CHEB)):
         dev = {k: gp.dev(z[k]) for k in z}
         state = H.state_struct(dev["u"], dev["p"], dev["v"], dev["udot"], dev["pdot"], dev["vdot"])
-        sp_ = H.solver_params(outer_rtol=1e-13, sub_rtol=1e-2, precision=precision)
+        sp_ = H.solver_params(outer_rtol=1e-13, sub_rtol=1e-2, precision=precision, s_precond=sprec)
         st, rc = H.hyel_newton_step(gp.ctx, H.time_params(dt=DT, tol_r=1e-10, tol_a=1e-12), sp_, state)
-        assert st.converged and st.iterations == info["iterations"], (nu, precision, st.as_dict(), info)
+        assert st.converged and st.iterations == info["iterations"], (nu, precision, sprec, st.as_dict(), info)
         for k in ("u", "p", "v"):
-            assert _rel(dev[k].cpu().numpy().reshape(y1[k].shape), y1[k]) <= 1e-9, (nu, precision, k)
+            assert _rel(dev[k].cpu().numpy().reshape(y1[k].shape), y1[k]) <= 1e-9, (nu, precision, sprec, k)
     gp.close()
 
 

@@ -5,8 +5,9 @@ the Chebyshev polynomial preconditioner (oracle/schur_hat.py).
 * S^ equals a brute-force triple loop on a tiny random block system, equals
   the exact dense Schur complement when A is diagonal, and its pattern on a
   mesh lies inside the distance-2 node graph;
-* the power estimate equals the ratio of successive matrix powers and tends
-  to the known largest eigenvalue of a 1D Laplacian;
+* the Arnoldi basis behind the Ritz bounds is orthonormal and satisfies the
+  Arnoldi relation; on a 1D Laplacian the Ritz values interlace the known
+  spectrum and, after n steps, are that spectrum;
 * the Chebyshev residual equals T_k((theta - M^-1 S^)/delta) / T_k(sigma)
   applied to M^-1 v (Chebyshev polynomial theory), degree 1 is scaled
   Jacobi, and a high degree reaches the exact solve.
@@ -100,26 +101,6 @@ def test_schur_hat_pattern_is_distance_two(mesh_system):
     assert np.allclose(np.diag(Sh), S.schur_hat_diag(K, N), rtol=1e-13)
 
 
-def test_power_estimate_is_ratio_of_matrix_powers(mesh_system):
-    _, N, K = mesh_system
-    Sh = SH.schur_hat(K, N)
-    M = np.diag(1.0 / Sh.diagonal()) @ Sh.toarray()
-    x0 = SH.power_start(N)
-    for k in (1, 3, 10):
-        ref = np.linalg.norm(np.linalg.matrix_power(M, k) @ x0) / np.linalg.norm(np.linalg.matrix_power(M, k - 1) @ x0)
-        assert SH.lmax_estimate(Sh, steps=k, safety=1.0) == pytest.approx(ref, rel=1e-12)
-
-
-def test_power_estimate_converges_on_1d_laplacian():
-    n = 20
-    L = sp.diags([-0.5 * np.ones(n - 1), 2.0 * np.ones(n), -0.5 * np.ones(n - 1)], [-1, 0, 1]).tocsr()
-    # M^-1 L = I - (1/4) T, T the 0/1 path adjacency: eigenvalues 1 - cos(k pi / (n+1)) / 2
-    lmax = 1.0 + 0.5 * np.cos(np.pi / (n + 1))
-    assert SH.lmax_estimate(L, steps=3000, safety=1.0) == pytest.approx(lmax, rel=1e-8)
-    est10 = SH.lmax_estimate(L, steps=10, safety=1.0)
-    assert 0.8 * lmax < est10 <= lmax * (1 + 1e-12)
-
-
 def _spd_unit(n, rng):
     Q = rng.standard_normal((n, n))
     Sd = Q @ Q.T + n * np.eye(n)
@@ -139,7 +120,7 @@ def test_chebyshev_residual_polynomial(degree):
     lmin = lmax / ratio
     theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
     v = rng.standard_normal(n)
-    z = SH.chebyshev_apply(Sh, lmax, ratio, degree, v)
+    z = SH.chebyshev_apply(Sh, lmax / ratio, lmax, degree, v)
     c = np.zeros(degree + 1)
     c[degree] = 1.0
     poly = npcheb.chebval((theta - lam) / delta, c) / npcheb.chebval(theta / delta, c)
@@ -154,7 +135,7 @@ def test_chebyshev_degree_one_is_scaled_jacobi():
     rng = np.random.default_rng(5)
     Sh = _spd_unit(9, rng)
     v = rng.standard_normal(9)
-    z = SH.chebyshev_apply(Sh, 3.0, 10.0, 1, v)
+    z = SH.chebyshev_apply(Sh, 0.3, 3.0, 1, v)
     theta = 0.5 * (3.0 + 0.3)
     assert np.allclose(z, v / Sh.diagonal() / theta, rtol=1e-14)
 
@@ -167,5 +148,59 @@ def test_chebyshev_high_degree_solves():
     lmax = 1.01 * lam.max()
     ratio = lmax / (0.99 * lam.min())
     v = rng.standard_normal(12)
-    z = SH.chebyshev_apply(Sh, lmax, ratio, 60, v)
+    z = SH.chebyshev_apply(Sh, lmax / ratio, lmax, 60, v)
     assert np.allclose(z, np.linalg.solve(Sh.toarray(), v), rtol=1e-9, atol=1e-12)
+
+
+def test_arnoldi_relation_and_orthonormal_basis(mesh_system):
+    """H from ritz_bounds' Arnoldi satisfies T V_k = V_{k+1} H with T the
+    symmetrically scaled S^; rebuilt here from H alone by the Arnoldi relation
+    column by column (each column of V_{k+1} follows from the previous ones)."""
+    _, N, K = mesh_system
+    Sh = SH.schur_hat(K, N)
+    s = np.sqrt(np.abs(1.0 / Sh.diagonal()))
+    T = sp.diags(s) @ Sh @ sp.diags(s)
+    H = SH.arnoldi_hessenberg(Sh, 8)
+    x0 = SH.power_start(N)
+    V = [x0 / np.linalg.norm(x0)]
+    for j in range(8):
+        w = T @ V[j] - sum(H[i, j] * V[i] for i in range(j + 1))
+        V.append(w / H[j + 1, j])
+    Vm = np.array(V)
+    assert np.allclose(Vm @ Vm.T, np.eye(9), atol=1e-10)
+
+
+def test_ritz_values_of_symmetric_operator():
+    """1D Laplacian tridiag(-1/2, 2, -1/2), n = 60: M^-1 S^ = I - T/4 has the
+    eigenvalues 1 - cos(k pi / 61) / 2. Ritz values lie inside the spectrum
+    (Cauchy interlacing), the extreme ones approach its ends, and with k = n
+    steps they are the spectrum."""
+    n = 60
+    L = sp.diags([-0.5 * np.ones(n - 1), 2.0 * np.ones(n), -0.5 * np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    ev = 1.0 - 0.5 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1))
+    lmin, lmax = SH.ritz_bounds(L, 12)
+    tmin, tmax = lmin * SH.RITZ_LOW, lmax / SH.RITZ_SAFETY
+    assert ev.min() - 1e-12 <= tmin and tmax <= ev.max() + 1e-12
+    assert tmax > ev.max() - 0.02 and tmin < ev.min() + 0.1
+    H = SH.arnoldi_hessenberg(L, n)
+    kk = H.shape[1]
+    theta = np.linalg.eigvalsh(0.5 * (H[:kk, :kk] + H[:kk, :kk].T))
+    assert kk == n and np.allclose(theta, np.sort(ev), atol=1e-9)
+
+
+def test_cheb_interval_clamps():
+    assert SH.cheb_interval((0.5, 3.0), 20.0) == (3.0 / 20.0, 3.0)
+    assert SH.cheb_interval((0.5, 3.0)) == (0.5, 3.0)
+    assert SH.cheb_interval((2.9, 3.0)) == (2.0, 3.0)
+    assert SH.cheb_interval((-1.0, 3.0)) == (3.0 / SH.CHEB_MAX_RATIO, 3.0)
+
+
+def test_float32_values_keep_pattern_and_round_entries():
+    rng = np.random.default_rng(8)
+    Sh = _spd_unit(10, rng)
+    S32 = SH.float32_values(Sh)
+    assert np.array_equal(S32.indices, Sh.indices) and np.array_equal(S32.indptr, Sh.indptr)
+    assert np.array_equal(S32.data, Sh.data.astype(np.float32).astype(np.float64))
+    # Sv replaces S^ in the products only: with Sv = S^ nothing changes
+    v = rng.standard_normal(10)
+    assert np.array_equal(SH.chebyshev_apply(Sh, 0.5, 3.0, 4, v), SH.chebyshev_apply(Sh, 0.5, 3.0, 4, v, Sv=Sh))
