@@ -294,13 +294,14 @@ int hyel_solve_setup(hyel_ctx *ctx, double *w_out);
  * current for this assembly) sums S^ on the GPU on the distance-2 node
  * pattern (row i couples i with every node two block-graph steps away; the
  * pattern and the per-contribution entry positions are built on the host on
- * first use for the mesh) in FP64 and FP32, and estimates the spectrum of
+ * first use for the mesh) in FP32 from the FP32 scaled blocks (an FP64 copy is
+ * summed from the FP64 blocks on the first FP64 use), and estimates the spectrum of
  * diag(S^)^-1 S^: 12 Arnoldi steps (two classical Gram-Schmidt passes each)
  * on |M|^-1/2 S^ |M|^-1/2, M = diag(S^), from x0_i = 2 u_i - 1 (u_i the top 53
  * bits of output i of SplitMix64 seeded with 0, over 2^53); the eigenvalues
  * theta of the symmetric part of the 12 x 12 Hessenberg matrix give
- * lmin = theta_min / 2 and lmax = 1.05 theta_max (FP64 vectors, the FP32
- * values of S^). Synchronizes.
+ * lmin = theta_min / 2 and lmax = 1.05 theta_max (in FP32, sums across
+ * blocks in FP64). Synchronizes.
  *   bounds_out host [2] or NULL: lmin, lmax.
  *   info       host [n_info] or NULL: [0] nonzeros of S^, [1] padded slots,
  *              [2] summed contributions, [3] longest row.

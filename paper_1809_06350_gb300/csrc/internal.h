@@ -109,7 +109,8 @@ struct DeviceMatrix {
     bool assembled = false;
     bool scaled = false;
     bool amg_ready = false;   // multigrid operators built from the current scaled A
-    bool shat_ready = false;  // explicit S^ and its bound built from the current scaled blocks
+    bool shat_ready = false;    // explicit S^ (FP32) and its interval built from the current scaled blocks
+    bool shat64_ready = false;  // ... and its FP64 copy
     bool transposed = false;  // At..Dt hold the transpose of the current assembly
 };
 
@@ -153,14 +154,14 @@ struct SchurHat {
     // block slot (k, j)): cptr[i] .. cptr[i + 1] - 1, pos = entry index in row i
     int64_t *cptr = nullptr;       // [N + 1]
     uint16_t *pos = nullptr;       // [ncontrib]
-    double *v64 = nullptr;         // [nslots]
-    float *v32 = nullptr;
+    double *v64 = nullptr;         // [nslots] (summed on demand)
+    float *v32 = nullptr;          // [nslots] (the solver's copy)
     // Chebyshev interval from the Ritz values of diag(S^)^-1 S^: lmin, lmax
     double *bounds = nullptr;      // device [2]
     double h_bounds[2] = {0.0, 0.0};
-    // FP64 scratch of the Arnoldi run and the stand-alone Chebyshev apply
-    double *work = nullptr;        // [3N] (Arnoldi: two directions and |diag(S^)|^-1/2)
-    double *arn_V = nullptr;       // [(steps + 1) N]
+    // scratch of the Arnoldi run (FP32) and the stand-alone Chebyshev apply
+    double *work = nullptr;        // [3N] (Arnoldi: two FP32 directions and |diag(S^)|^-1/2)
+    float *arn_V = nullptr;        // [(steps + 1) N]
     double *arn_H = nullptr;       // [(steps + 1) steps]
     double *partial = nullptr;     // [2][steps + 1][grid]
     unsigned *bar = nullptr;       // barrier words
@@ -231,7 +232,9 @@ void amg_apply(Ctx &c, const T *v, T *z);  // z = V-cycle(v), [3N]
 
 // schur_hat.cu
 void shat_free(Ctx &c);
-void shat_numeric(Ctx &c);  // builds the pattern on first use, then the values of the current scaled blocks
+template <typename V>
+void shat_numeric(Ctx &c);  // builds the pattern on first use, then the V values of the current scaled blocks
+void shat_ensure64(Ctx &c);  // the FP64 values, if not yet summed for this assembly
 template <typename T>
 void shat_spmv(Ctx &c, const T *x, T *y);  // y = S^ x, [N]
 

@@ -12,7 +12,10 @@
 //   row sums D_ik and -sum_s C_ik[s] B_kj[s] / A_kk[s][s] into a per-thread
 //   row buffer in shared memory (column-major over the block's threads, so
 //   every lane stays in its own bank), in a fixed order (bitwise
-//   reproducible), then writes the row out coalesced in FP64 and FP32.
+//   reproducible), then writes the row out coalesced. The solver's copy is
+//   summed in FP32 from the FP32 scaled blocks (the preconditioner's
+//   precision; FP64 arithmetic is scarce on this GPU); the FP64 copy is
+//   summed from the FP64 blocks when an FP64 entry point first asks for it.
 #include <algorithm>
 #include <vector>
 
@@ -32,28 +35,30 @@ T *upload_sync(Ctx &c, const std::vector<T> &h) {
     return d;
 }
 
+template <typename V>
 struct NumArgs {
-    // block pattern and scaled blocks
+    // block pattern and scaled blocks of precision V
     const int32_t *slice_ptr, *row_len, *col, *diag_slot;
-    const double *As, *Bs, *Cs, *Ds;
+    const V *As, *Bs, *Cs, *Ds;
     // S^
     const int32_t *h_slice_ptr, *h_row_len;
     const int64_t *cptr;
     const uint16_t *pos;
-    double *v64;
-    float *v32;
+    V *val;
     int64_t N;
     int tb;  // threads per block (row stride of the shared buffer)
 };
 
-__global__ void k_shat_numeric(NumArgs a) {
-    extern __shared__ double s_row[];
+template <typename V>
+__global__ void k_shat_numeric(NumArgs<V> a) {
+    extern __shared__ unsigned char s_raw[];
+    V *s_row = reinterpret_cast<V *>(s_raw);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.N) return;
-    double *acc = s_row + threadIdx.x;
+    V *acc = s_row + threadIdx.x;
     const int tb = a.tb;
     const int lh = a.h_row_len[i];
-    for (int p = 0; p < lh; p++) acc[p * tb] = 0.0;
+    for (int p = 0; p < lh; p++) acc[p * tb] = 0;
     const int t = (int)(i & 31);
     const int64_t b0 = a.slice_ptr[i >> 5];
     const int len = a.row_len[i];
@@ -64,26 +69,21 @@ __global__ void k_shat_numeric(NumArgs a) {
         const int64_t k = a.col[q];
         acc[pos[cp++] * tb] += a.Ds[q];
         const int64_t dq = a.diag_slot[k], db = dq >> 5, dt = dq & 31;
-        const double c0 = a.Cs[(b * 3) * 32 + t] / a.As[(db * 9) * 32 + dt];
-        const double c1 = a.Cs[(b * 3 + 1) * 32 + t] / a.As[(db * 9 + 4) * 32 + dt];
-        const double c2 = a.Cs[(b * 3 + 2) * 32 + t] / a.As[(db * 9 + 8) * 32 + dt];
+        const V c0 = a.Cs[(b * 3) * 32 + t] / a.As[(db * 9) * 32 + dt];
+        const V c1 = a.Cs[(b * 3 + 1) * 32 + t] / a.As[(db * 9 + 4) * 32 + dt];
+        const V c2 = a.Cs[(b * 3 + 2) * 32 + t] / a.As[(db * 9 + 8) * 32 + dt];
         const int64_t kb0 = a.slice_ptr[k >> 5];
         const int tk = (int)(k & 31);
         const int lk = a.row_len[k];
         for (int jj = 0; jj < lk; jj++) {
-            const double *Bb = a.Bs + ((kb0 + jj) * 3) * 32 + tk;
-            const double v = c0 * Bb[0] + c1 * Bb[32] + c2 * Bb[64];
+            const V *Bb = a.Bs + ((kb0 + jj) * 3) * 32 + tk;
+            const V v = c0 * Bb[0] + c1 * Bb[32] + c2 * Bb[64];
             acc[pos[cp++] * tb] -= v;
         }
     }
     const int64_t hb0 = a.h_slice_ptr[i >> 5];
     const int w = a.h_slice_ptr[(i >> 5) + 1] - (int)hb0;
-    for (int p = 0; p < w; p++) {
-        const double v = p < lh ? acc[p * tb] : 0.0;
-        const int64_t q = (hb0 + p) * 32 + t;
-        a.v64[q] = v;
-        a.v32[q] = (float)v;
-    }
+    for (int p = 0; p < w; p++) a.val[(hb0 + p) * 32 + t] = p < lh ? acc[p * tb] : (V)0;
 }
 
 template <typename T>
@@ -196,39 +196,58 @@ void shat_free(Ctx &c) {
     c.sh = nullptr;
 }
 
+template <typename V>
 void shat_numeric(Ctx &c) {
     if (!c.mat.scaled) fail(HYEL_ESTATE, "schur_hat: the scaled system is not set up");
     if (!c.sh) shat_build(c);
     const SchurHat &h = *c.sh;
     const DeviceMesh &m = c.mesh;
-    NumArgs a;
+    NumArgs<V> a;
     a.slice_ptr = m.slice_ptr;
     a.row_len = m.row_len;
     a.col = m.col;
     a.diag_slot = m.diag_slot;
-    a.As = c.mat.As;
-    a.Bs = c.mat.Bs;
-    a.Cs = c.mat.Cs;
-    a.Ds = c.mat.Ds;
+    if constexpr (std::is_same<V, double>::value) {
+        a.As = c.mat.As;
+        a.Bs = c.mat.Bs;
+        a.Cs = c.mat.Cs;
+        a.Ds = c.mat.Ds;
+        a.val = h.v64;
+    } else {
+        a.As = c.mat.Af;
+        a.Bs = c.mat.Bf;
+        a.Cs = c.mat.Cf;
+        a.Ds = c.mat.Df;
+        a.val = h.v32;
+    }
     a.h_slice_ptr = h.slice_ptr;
     a.h_row_len = h.row_len;
     a.cptr = h.cptr;
     a.pos = h.pos;
-    a.v64 = h.v64;
-    a.v32 = h.v32;
     a.N = m.N;
     int tb = 128;
-    while (tb > 32 && (int64_t)tb * h.max_row * 8 > kShatSmemMax) tb /= 2;
+    while (tb > 32 && (int64_t)tb * h.max_row * (int64_t)sizeof(V) > kShatSmemMax) tb /= 2;
     a.tb = tb;
-    const int smem = tb * h.max_row * 8;
-    HYEL_CK(cudaFuncSetAttribute(k_shat_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    (k_shat_numeric<<<blocks_for(m.N, tb), tb, smem, c.stream>>>(a), ::hyel::count_launch());
+    const int smem = tb * h.max_row * (int)sizeof(V);
+    HYEL_CK(cudaFuncSetAttribute(k_shat_numeric<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    (k_shat_numeric<V><<<blocks_for(m.N, tb), tb, smem, c.stream>>>(a), ::hyel::count_launch());
     HYEL_CK(cudaGetLastError());
+}
+template void shat_numeric<double>(Ctx &);
+template void shat_numeric<float>(Ctx &);
+
+void shat_ensure64(Ctx &c) {
+    if (!c.sh || !c.mat.shat_ready) fail(HYEL_ESTATE, "schur_hat: S^ is not built for the current assembly");
+    if (!c.mat.shat64_ready) {
+        shat_numeric<double>(c);
+        c.mat.shat64_ready = true;
+    }
 }
 
 template <typename T>
 void shat_spmv(Ctx &c, const T *x, T *y) {
     if (!c.sh || !c.mat.shat_ready) fail(HYEL_ESTATE, "schur_hat: S^ is not built for the current assembly");
+    if constexpr (std::is_same<T, double>::value) shat_ensure64(c);
     const SchurHat &h = *c.sh;
     const T *val;
     if constexpr (std::is_same<T, double>::value)

@@ -1263,7 +1263,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
 
 // Ritz values for the Chebyshev interval: kRitzSteps steps of Arnoldi on
 // T = |M|^-1/2 S^ |M|^-1/2 (M = diag(S^); T is similar to M^-1 S^ when
-// diag(S^) > 0), FP64 vectors with the FP32 copy of S^ (an estimate), one
+// diag(S^) > 0), in FP32 (an estimate; sums across blocks in FP64), one
 // cooperative launch. The start vector comes from
 // SplitMix64 (Steele, Lea and Flood 2014): output i of the generator seeded
 // with 0 gives x0[i] = 2 u - 1, u its top 53 bits over 2^53. Each new
@@ -1286,7 +1286,8 @@ struct ArnArgs {
     const int32_t *slice_ptr, *row_len, *col;
     const float *val;
     const double *dinv;
-    double *V, *U, *Sq, *H, *partial;  // U: [2N]; Sq: [N] |diag(S^)|^-1/2
+    float *V, *U, *Sq;  // U: [2N]; Sq: [N] |diag(S^)|^-1/2
+    double *H, *partial;
     unsigned *bar;
     int64_t N;
 };
@@ -1294,7 +1295,7 @@ struct ArnArgs {
 __global__ void __launch_bounds__(kPgThreads) k_shat_arnoldi(ArnArgs a) {
     __shared__ double red1[kPgThreads / 32];
     __shared__ double s_sum[kRitzSteps + 2], s_h[kRitzSteps + 2];
-    __shared__ double hs[kRitzSteps + 2];
+    __shared__ float hs[kRitzSteps + 2];
     unsigned phase = 0u;
     const int64_t N = a.N;
     const int G = gridDim.x, K1 = kRitzSteps + 1;
@@ -1303,52 +1304,52 @@ __global__ void __launch_bounds__(kPgThreads) k_shat_arnoldi(ArnArgs a) {
     auto fail_out = [&]() {
         if (lead) a.H[0] = nan("");
     };
-    double ss = 0.0;
+    float ss = 0.0f;
     PG_FOR_OWN_NODES(N, i) {
-        const double x = 2.0 * ((double)(splitmix64_at((unsigned long long)i) >> 11) * 0x1p-53) - 1.0;
+        const float x = (float)(2.0 * ((double)(splitmix64_at((unsigned long long)i) >> 11) * 0x1p-53) - 1.0);
         a.U[i] = x;
-        a.Sq[i] = sqrt(fabs(__ldg(a.dinv + i)));
-        ss = fma(x, x, ss);
+        a.Sq[i] = (float)sqrt(fabs(__ldg(a.dinv + i)));
+        ss = fmaf(x, x, ss);
     }
-    double tb = pg_block_sum<double>(ss, red1);
+    double tb = pg_block_sum<float>(ss, red1);
     if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
     if (!pg_barrier(a.bar, phase)) return fail_out();
     pg_sum(pbuf(phase - 1), 1, s_sum);
     __syncthreads();
-    double sc = 1.0 / sqrt(s_sum[0]);
+    float sc = (float)(1.0 / sqrt(s_sum[0]));
     for (int j = 0; j < kRitzSteps; j++) {
-        const double *u = a.U + (size_t)(j & 1) * N;
-        double *w = a.U + (size_t)((j + 1) & 1) * N;
-        double *Vj = a.V + (size_t)j * N;
+        const float *u = a.U + (size_t)(j & 1) * N;
+        float *w = a.U + (size_t)((j + 1) & 1) * N;
+        float *Vj = a.V + (size_t)j * N;
         // v_j = sc u; w = T v_j
         PG_FOR_OWN_NODES(N, i) {
             Vj[i] = u[i] * sc;
             const int t = (int)(i & 31);
             const int64_t b0 = __ldg(a.slice_ptr + (i >> 5));
             const int len = __ldg(a.row_len + i);
-            double acc = 0.0;
+            float acc = 0.0f;
             for (int p = 0; p < len; p++) {
                 const int64_t q = (b0 + p) * 32 + t;
                 const int64_t c = __ldg(a.col + q);
-                acc = fma((double)__ldg(a.val + q), a.Sq[c] * u[c], acc);
+                acc = fmaf(__ldg(a.val + q), a.Sq[c] * u[c], acc);
             }
             w[i] = a.Sq[i] * acc * sc;
         }
         // two classical Gram-Schmidt passes, then ||w||
         for (int l = threadIdx.x; l <= j; l += blockDim.x) s_h[l] = 0.0;
         for (int pass = 0; pass < 2; pass++) {
-            pg_dots<double, 1>(a.V, w, N, j + 1, false, pbuf(phase));
+            pg_dots<float, 1>(a.V, w, N, j + 1, false, pbuf(phase));
             if (!pg_barrier(a.bar, phase)) return fail_out();
             pg_sum(pbuf(phase - 1), j + 1, s_sum);
             __syncthreads();
             for (int l = threadIdx.x; l <= j; l += blockDim.x) {
-                hs[l] = s_sum[l];
+                hs[l] = (float)s_sum[l];
                 s_h[l] += s_sum[l];
             }
             __syncthreads();
-            const double part = pg_axpy<double, 1>(a.V, w, N, j + 1, hs);
+            const float part = pg_axpy<float, 1>(a.V, w, N, j + 1, hs);
             if (pass == 1) {
-                tb = pg_block_sum<double>(part, red1);
+                tb = pg_block_sum<float>(part, red1);
                 if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
             }
         }
@@ -1361,7 +1362,7 @@ __global__ void __launch_bounds__(kPgThreads) k_shat_arnoldi(ArnArgs a) {
             a.H[(size_t)j * K1 + j + 1] = hn;
         }
         if (!(hn > 0.0)) return;  // invariant subspace (or NaN): the host reads the leading block
-        sc = 1.0 / hn;
+        sc = (float)(1.0 / hn);
     }
 }
 
@@ -2229,7 +2230,7 @@ void shat_bounds(Ctx &c) {
     const int grid = coop_grid(c, (const void *)k_shat_arnoldi);
     const size_t gmax = (size_t)(2048 / kPgThreads) * c.num_sms;
     if (!h.partial) h.partial = dalloc_n<double>(c, 2 * gmax * K1);
-    if (!h.arn_V) h.arn_V = dalloc_n<double>(c, (size_t)K1 * N);
+    if (!h.arn_V) h.arn_V = dalloc_n<float>(c, (size_t)K1 * N);
     if (!h.arn_H) h.arn_H = dalloc_n<double>(c, (size_t)K1 * kRitzSteps);
     ArnArgs a;
     a.slice_ptr = h.slice_ptr;
@@ -2238,8 +2239,8 @@ void shat_bounds(Ctx &c) {
     a.val = h.v32;
     a.dinv = c.mat.shat64;
     a.V = h.arn_V;
-    a.U = h.work;
-    a.Sq = h.work + 2 * N;
+    a.U = reinterpret_cast<float *>(h.work);
+    a.Sq = a.U + 2 * N;
     a.H = h.arn_H;
     a.partial = h.partial;
     a.bar = h.bar;
@@ -2278,15 +2279,15 @@ void shat_setup(Ctx &c) {
     if (c.mat.shat_ready) return;
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_SCHUR_HAT, &ev);
-    shat_numeric(c);
+    shat_numeric<float>(c);
     const SchurHat &h = *c.sh;
     const DeviceMesh &m = c.mesh;
-    // numeric: D, C, column and diag(A) per block slot, B per neighbour slot,
-    // positions, rows written in FP64 and FP32; Arnoldi: S^ and the basis
-    // passes per step
-    const double bytes = (double)m.nnzb * (8.0 + 24.0 + 4.0 + 24.0) + (double)m.N * (24.0 + 8.0) +
-                         2.0 * (double)h.ncontrib + 12.0 * (double)h.nslots +
-                         kRitzSteps * ((double)h.nnz * 8.0 + (double)m.N * (16.0 + 8.0 * (2 * kRitzSteps + 4)));
+    // numeric (FP32): D, C, column and diag(A) per block slot, B per
+    // neighbour slot, positions, rows written; Arnoldi (FP32): S^ and the
+    // basis passes per step
+    const double bytes = (double)m.nnzb * (4.0 + 12.0 + 4.0 + 12.0) + (double)m.N * (12.0 + 8.0) +
+                         2.0 * (double)h.ncontrib + 4.0 * (double)h.nslots +
+                         kRitzSteps * ((double)h.nnz * 8.0 + (double)m.N * (8.0 + 4.0 * (2 * kRitzSteps + 4)));
     shat_bounds(c);
     prof_end(c, HYEL_K_SCHUR_HAT, ev, bytes);
     c.mat.shat_ready = true;
@@ -2304,6 +2305,7 @@ void shat_cheb_apply(Ctx &c, int matrix, int degree, double ratio, const double 
     HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
     HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
     if (matrix == HYEL_MAT_SCALED64) {
+        shat_ensure64(c);
         ChebArgs<double, double> ch = cheb_args<double, double>(c, degree, ratio, h.work, h.work + N, h.work + 2 * N);
         void *args[] = {&ch, (void *)&x, (void *)&y, &n, &bar, &status};
         coop_launch(c, coop_grid(c, (const void *)k_cheb_apply<double>), (const void *)k_cheb_apply<double>, args);

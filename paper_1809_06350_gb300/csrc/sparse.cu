@@ -527,6 +527,7 @@ void solve_setup(Ctx &c) {
     c.mat.scaled = true;
     c.mat.amg_ready = false;
     c.mat.shat_ready = false;
+    c.mat.shat64_ready = false;
 }
 
 void transpose_assembled(Ctx &c) {
