@@ -10,7 +10,10 @@ the 48^3-hex cube (663,552 P1 tets, 117,649 nodes, 470,596 linear unknowns),
 compressible neo-Hookean Gibbs material mu = 1e5 Pa, nu = 0.3 (kappa from
 nu), rho0 = 1e3, dead load 2e4 Pa on the top face ramped over 10 steps,
 dt = 1e-3, rho_inf = 0.5, sub-solver tolerances 1e-2. K timed steps run
-t = 0, dt, ..., (K-1) dt from rest (K = 10 is the whole 10-step run).
+t = 0, dt, ..., (K-1) dt from rest (K = 10 is the whole 10-step run). The
+S-solve is preconditioned by the degree-8 Chebyshev polynomial in the explicit
+S^ = D - C diag(A)^-1 B (its values and interval rebuilt every Newton
+iteration, inside the timed region); --s-precond jacobi selects diag(S^)^-1.
 
 metric value = linear unknowns x Newton linear solves per second over all
 ranks (replicas: every rank solves its own copy; no collective in the path).
@@ -51,9 +54,10 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16s"],
                    help="preconditioner-level precision of the main timed run (fp64 is the headline; "
                         "the mixed forms are also timed beside it unless --no-mixed)")
-    p.add_argument("--s-precond", default="jacobi", choices=["jacobi", "cheb"],
-                   help="S-solve preconditioner: diag(S^)^-1, or the Chebyshev polynomial in the explicit S^")
-    p.add_argument("--cheb-degree", type=int, default=4)
+    p.add_argument("--s-precond", default="cheb", choices=["jacobi", "cheb"],
+                   help="S-solve preconditioner: the Chebyshev polynomial in the explicit S^ (default), "
+                        "or diag(S^)^-1")
+    p.add_argument("--cheb-degree", type=int, default=8)
     p.add_argument("--cheb-ratio", type=float, default=0.0,
                    help="0: interval from Ritz estimates; > 1: fixed lmax / lmin")
     return p.parse_args()
@@ -395,8 +399,10 @@ def run_hyel(args, rank, world, local_rank):
     kdesc = {"gmres_A": "k_gmres_a" + tname + " (persistent A-solve, one cooperative launch per intermediate "
                         "A-solve: SELL-32 SpMV of A M^-1, Gram-Schmidt, Givens, solution update)",
              "gmres_S": "k_gmres_s" + tname + " (persistent S-solve, one cooperative launch per S-solve: "
-                        "Schur products with their inner A-solves, Gram-Schmidt, Givens)"}
-    traffic_ratio = profile_traffic("gmres_" + dom[-1].lower() + "_cube48", "solver.cu", "dram_over_algorithmic")
+                        "Schur products with their inner A-solves, Gram-Schmidt, Givens" +
+                        (", Chebyshev polynomial in S^" if args.s_precond == "cheb" else "") + ")"}
+    prof_name = "gmres_" + dom[-1].lower() + ("_cheb" if dom == "gmres_S" and args.s_precond == "cheb" else "")
+    traffic_ratio = profile_traffic(prof_name + "_cube48", "solver.cu", "dram_over_algorithmic")
     roof = {"kernel": kdesc[dom],
             "bound": "hbm", "achieved": gbs_live, "peak": peak, "unit": "GB/s",
             "frac": gbs_live / peak if gbs_live else None,
@@ -405,8 +411,11 @@ def run_hyel(args, rank, world, local_rank):
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy burst)" if peak_kind == "measured"
             else "fallback 6.8 TB/s",
             "bytes_per_launch": by_live, "avg_launch_us": us_live, "launches": pl["launches"],
-            "algorithmic_bytes": "per iteration j: A M^-1 values + indices + 4(N+1), and 4(j+1)+9 passes over "
-                                 "3N-vectors (counted on the device, summed over the launch's iterations)",
+            "algorithmic_bytes": ("per A-iteration j: A M^-1 values + indices + 4(N+1), and 2(j+1)+6 passes "
+                                  "over 3N-vectors (4(j+1)+10 with a second Gram-Schmidt pass); per S-iteration: "
+                                  "B, C, D values + indices twice, the Chebyshev S^ products (FP32 values + "
+                                  "indices) and vector passes, and its inner A-solve's bytes (counted on the "
+                                  "device, summed over the launch's iterations)"),
             "measured": "CUDA events around every launch on the library stream, in a host-driven replay of the "
                         "timed K steps (the graph-mode run has no per-kernel events)",
             "fp64_pipe_note": "9 DFMA per 76-byte block: GB300's 1.2 TFLOP/s FP64 pipe caps the SpMV phase near "
