@@ -293,3 +293,50 @@ def direct_solve(K, rhs):
         return np.linalg.solve(K.toarray(), rhs)
     lu = spla.splu(K.tocsc(), permc_spec="COLAMD")
     return lu.solve(rhs)
+
+
+BLOCK_KINDS = ("LDU", "DU", "D", "SIMPLE")
+
+
+def block_precond_matrix(K, N, kind):
+    """The block preconditioner P as a dense matrix, in the expanded forms of
+    §4.3–4.4 (small systems only): LDU = the full factorization, i.e. K itself;
+    DU = [[A, B], [O, S]]; D = [[A, O], [O, S]]; SIMPLE (H1 = H2 = diag(A)^-1) =
+    [[A, A diag(A)^-1 B], [C, D]]; S = D - C A^-1 B."""
+    A, B, C, D = (m.toarray() for m in split_blocks(K, N))
+    if kind == "LDU":
+        return K.toarray()
+    if kind == "SIMPLE":
+        return np.block([[A, A @ (B / np.diag(A)[:, None])], [C, D]])
+    S = explicit_schur(K, N)
+    if kind == "DU":
+        return np.block([[A, B], [np.zeros((N, 3 * N)), S]])
+    if kind == "D":
+        return np.block([[A, np.zeros((3 * N, N))], [np.zeros((N, 3 * N)), S]])
+    raise ValueError(kind)
+
+
+def block_precond_apply(K, N, kind, r):
+    """z = P^-1 r by the block steps, every sub-system solved exactly (dense
+    LAPACK; small systems only). LDU is Algorithm 1: A xhat = r_v,
+    r_p' = r_p - C xhat, S x_p = r_p', A x_v = r_v - B x_p. DU: S x_p = r_p,
+    A x_v = r_v - B x_p. D: A x_v = r_v, S x_p = r_p. SIMPLE: A xhat = r_v,
+    S^ x_p = r_p - C xhat, x_v = xhat - diag(A)^-1 B x_p."""
+    A, B, C, D = (m.toarray() for m in split_blocks(K, N))
+    rv, rp = r[:3 * N], r[3 * N:]
+    if kind == "SIMPLE":
+        xhat = np.linalg.solve(A, rv)
+        Sh = D - C @ (B / np.diag(A)[:, None])
+        xp = np.linalg.solve(Sh, rp - C @ xhat)
+        return np.concatenate([xhat - (B @ xp) / np.diag(A), xp])
+    S = explicit_schur(K, N)
+    if kind == "LDU":
+        xhat = np.linalg.solve(A, rv)
+        xp = np.linalg.solve(S, rp - C @ xhat)
+    elif kind == "DU":
+        xp = np.linalg.solve(S, rp)
+    elif kind == "D":
+        return np.concatenate([np.linalg.solve(A, rv), np.linalg.solve(S, rp)])
+    else:
+        raise ValueError(kind)
+    return np.concatenate([np.linalg.solve(A, rv - B @ xp), xp])

@@ -314,3 +314,46 @@ def test_ldu_identity_schur_and_scaling():
     for a in range(N):
         blk = A[3 * a:3 * a + 3, 3 * a:3 * a + 3]
         assert np.allclose(bj[a] @ blk, np.eye(3), atol=1e-12)
+
+
+# ------------------------------------------------------------ block preconditioners
+
+@pytest.mark.parametrize("kind", S.BLOCK_KINDS)
+def test_block_preconditioner_steps_invert_the_printed_matrix(kind):
+    """The block steps (Algorithm 1 and its DU / D / SIMPLE variants) invert
+    the preconditioner matrix as printed in expanded form (§4.3: SIMPLE =
+    [[A, A diag(A)^-1 B], [C, D]]; the DU and D parts of the LDU
+    factorization of eq. a_ldu_block_factorization)."""
+    rng = np.random.default_rng(40)
+    N = 6
+    n = 4 * N
+    K = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.6)
+    K[np.arange(n), np.arange(n)] += 6.0
+    K = sp.csr_matrix(K)
+    P = S.block_precond_matrix(K, N, kind)
+    x = rng.standard_normal(n)
+    assert np.allclose(S.block_precond_apply(K, N, kind, P @ x), x, rtol=1e-10, atol=1e-10)
+
+
+def test_block_preconditioner_structure():
+    """LDU is the matrix itself; DU is block upper triangular with the Schur
+    complement in the corner; SIMPLE keeps C and D and perturbs the upper right
+    block by A diag(A)^-1 B - B."""
+    rng = np.random.default_rng(41)
+    N = 5
+    n = 4 * N
+    K = rng.standard_normal((n, n))
+    K[np.arange(n), np.arange(n)] += 8.0
+    K = sp.csr_matrix(K)
+    A, B, C, D = (m.toarray() for m in S.split_blocks(K, N))
+    assert np.array_equal(S.block_precond_matrix(K, N, "LDU"), K.toarray())
+    Pdu = S.block_precond_matrix(K, N, "DU")
+    assert np.allclose(Pdu[3 * N:, :3 * N], 0) and np.allclose(Pdu[3 * N:, 3 * N:], D - C @ np.linalg.solve(A, B))
+    Ps = S.block_precond_matrix(K, N, "SIMPLE")
+    assert np.array_equal(Ps[3 * N:], K.toarray()[3 * N:])
+    assert np.allclose(Ps[:3 * N, 3 * N:], A @ np.diag(1 / np.diag(A)) @ B)
+    # with A diagonal, SIMPLE is exact
+    K2 = K.toarray()
+    K2[:3 * N, :3 * N] = np.diag(np.diag(A))
+    K2 = sp.csr_matrix(K2)
+    assert np.allclose(S.block_precond_matrix(K2, N, "SIMPLE"), K2.toarray())
