@@ -177,6 +177,21 @@ enum { HYEL_APREC_BJACOBI = 0, HYEL_APREC_AMG = 1 };
  *   is algebraic multigrid built from S^ (§5). Needs a_precond =
  *   HYEL_APREC_BJACOBI. */
 enum { HYEL_SPREC_JACOBI = 0, HYEL_SPREC_CHEB = 1 };
+/* The block preconditioner of the outer FGMRES (§4.2–4.4; the factorization
+ * of eq. a_ldu_block_factorization):
+ * HYEL_BLOCK_LDU: Algorithm 1 (P_SCR, the default): A xhat = r_v,
+ *   S x_p = r_p - C xhat (the S-solve), A x_v = r_v - B x_p;
+ * HYEL_BLOCK_DU: the upper triangular part [[A, B], [O, S]]: S x_p = r_p,
+ *   A x_v = r_v - B x_p;
+ * HYEL_BLOCK_D: the block diagonal [[A, O], [O, S]]: A x_v = r_v, S x_p = r_p;
+ * HYEL_BLOCK_SIMPLE: H1 = H2 = diag(A)^-1, the paper's comparison baseline:
+ *   A xhat = r_v, S^ x_p = r_p - C xhat with the explicit S^ (GMRES on S^ with
+ *   the s-level controls, preconditioned by s_precond, one persistent launch;
+ *   FP64 S^ values in FP64 levels, FP32 in mixed ones), x_v = xhat -
+ *   diag(A)^-1 B x_p.
+ * A-solves use the a-level controls, S-solves (matrix-free S, inner A-solves)
+ * the s- and inner-level controls. */
+enum { HYEL_BLOCK_LDU = 0, HYEL_BLOCK_DU = 1, HYEL_BLOCK_D = 2, HYEL_BLOCK_SIMPLE = 3 };
 
 typedef struct {
     hyel_krylov_level outer, a, s, inner;
@@ -187,6 +202,8 @@ typedef struct {
     int32_t s_precond;      /* HYEL_SPREC_* */
     int32_t s_cheb_degree;  /* HYEL_SPREC_CHEB: polynomial degree, 1..16 */
     double  s_cheb_ratio;   /* HYEL_SPREC_CHEB: 0 (estimated lmin) or lmax / lmin > 1 */
+    int32_t block_precond;  /* HYEL_BLOCK_* */
+    int32_t reserved_;      /* must be 0 */
 } hyel_solver_params;
 
 typedef struct {
@@ -325,10 +342,19 @@ int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio,
 int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params,
                      const double *x, double *y, hyel_solve_stats *stats);
 
+/* z = P^-1 r once, P the block preconditioner of params->block_precond on the
+ * scaled system (§4.2–4.4), its sub-solves controlled by params (precision,
+ * levels, A- and S-preconditioners) exactly as inside hyel_solve_nested.
+ * r, z: device [4N] double ([v ; p] ordering). stats: host or NULL (a, s and
+ * inner counts). Synchronizes. */
+int hyel_block_precond_apply(hyel_ctx *ctx, const hyel_solver_params *params,
+                             const double *r, double *z, hyel_solve_stats *stats);
+
 /* ---------------------------------------------------------------- solve */
 
 /* Solve A x = rhs for the last assembled matrix (§4): symmetric diagonal
- * scaling, FGMRES with the nested SCR preconditioner, unscaling.
+ * scaling, FGMRES with the nested SCR preconditioner (or the block variant
+ * params->block_precond selects), unscaling.
  * rhs, x: device [4N] double. stats: host or NULL. Returns HYEL_ENOCONV if the
  * outer solver reached its iteration cap (x then holds the last iterate). */
 int hyel_solve_nested(hyel_ctx *ctx, const hyel_solver_params *params,

@@ -309,6 +309,14 @@ int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params, const doub
     });
 }
 
+int hyel_block_precond_apply(hyel_ctx *ctx, const hyel_solver_params *params, const double *r, double *z,
+                             hyel_solve_stats *stats) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!params || !r || !z) hyel::fail(HYEL_EINVAL, "block_precond_apply: null argument");
+        hyel::block_precond_apply(c, *params, r, z, stats);
+    });
+}
+
 int hyel_solve_nested(hyel_ctx *ctx, const hyel_solver_params *params, const double *rhs, double *x,
                       hyel_solve_stats *stats) {
     return guarded(ctx, [&](hyel::Ctx &c) {

@@ -268,6 +268,7 @@ void spmv_DC_ind(Ctx &c, const T *D, const T *C, const T *xp, const T *xv, T *yp
 // solver.cu
 void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double *x, hyel_solve_stats *st);
 void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y, hyel_solve_stats *st);
+void block_precond_apply(Ctx &c, const hyel_solver_params &p, const double *r, double *z, hyel_solve_stats *st);
 void free_workspace(Ctx &c);
 void shat_bounds(Ctx &c);  // Chebyshev interval of diag(S^)^-1 S^ from Arnoldi Ritz values (host-checked)
 void shat_setup(Ctx &c);  // solve_setup, then S^ and its bound unless current

@@ -1261,6 +1261,69 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
     }
 }
 
+// GMRES on the explicit S^ (the S^-solve of the SIMPLE preconditioner) as one
+// cooperative launch: operator S^ P^-1 with P^-1 = diag(S^)^-1 (applied while
+// gathering) or the Chebyshev polynomial in S^ (grid phases of its own);
+// x = P^-1 V y. S^ values of the level's precision.
+template <typename T>
+struct ShArgs {
+    const int32_t *slice_ptr, *row_len, *col;  // S^ pattern (SELL-32)
+    const T *val;
+    const T *dinv;  // [N] 1 / diag(S^)
+    T *zc;          // [N] P^-1 v (Chebyshev only)
+    ChebArgs<T> ch;
+    GmArgs<T> g;
+};
+
+template <typename T, bool CHEB>
+__global__ void __launch_bounds__(kPgThreads, 2) k_gmres_shat(ShArgs<T> s) {
+    unsigned phase = 0u;  // the barrier words are cleared before every launch
+    const int64_t N = s.g.N;
+    auto op = [&](const T *u, T sc, T *w, unsigned &ph) {
+        if constexpr (CHEB) {
+            if (!pg_cheb(s.ch, N, u, (T)1, s.zc, false, s.g.bar, ph)) return false;
+        }
+        PG_FOR_OWN_NODES(N, i) {
+            const int t = (int)(i & 31);
+            const int64_t b0 = __ldg(s.slice_ptr + (i >> 5));
+            const int len = __ldg(s.row_len + i);
+            T acc = 0;
+            for (int p = 0; p < len; p++) {
+                const int64_t q = (b0 + p) * 32 + t;
+                const int64_t c = __ldg(s.col + q);
+                T zc;
+                if constexpr (CHEB)
+                    zc = s.zc[c];
+                else
+                    zc = __ldg(s.dinv + c) * u[c];
+                acc = fma(__ldg(s.val + q), zc, acc);
+            }
+            w[i] = acc * sc;
+        }
+        return true;
+    };
+    if constexpr (CHEB) {
+        auto xupd = [&](int64_t i, const T (&u)[1]) { s.ch.r[i] = u[0]; };
+        auto xend = [&](unsigned &ph) { return pg_cheb(s.ch, N, s.ch.r, (T)1, s.g.x, true, s.g.bar, ph); };
+        pg_gmres<T, 1>(s.g, phase, op, xupd, xend);
+    } else {
+        auto xupd = [&](int64_t i, const T (&u)[1]) { s.g.x[i] += __ldg(s.dinv + i) * u[0]; };
+        pg_gmres<T, 1>(s.g, phase, op, xupd);
+    }
+}
+
+// SIMPLE's last step: x_v = xhat - diag(A)^-1 (B x_p), diag(A) the scalar
+// diagonal of the scaled A (Av in the SELL-32 block layout)
+template <typename T>
+__global__ void k_simple_update(const int32_t *__restrict__ diag_slot, const T *__restrict__ Av,
+                                const T *__restrict__ xhat, const T *__restrict__ bx, T *__restrict__ xv, int64_t N) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t dq = diag_slot[i], db = dq >> 5, dt = dq & 31;
+#pragma unroll
+    for (int r = 0; r < 3; r++) xv[3 * i + r] = xhat[3 * i + r] - bx[3 * i + r] / Av[(db * 9 + 4 * r) * 32 + dt];
+}
+
 // Ritz values for the Chebyshev interval: kRitzSteps steps of Arnoldi on
 // T = |M|^-1/2 S^ |M|^-1/2 (M = diag(S^); T is similar to M^-1 S^ when
 // diag(S^) > 0), in FP32 (an estimate; sums across blocks in FP64), one
@@ -1476,6 +1539,7 @@ struct Level {
     unsigned *bar = nullptr;
     int pg_grid = 0, pg_grid16 = 0;
     int pg_gridc = 0, pg_grid16c = 0;  // S-level with the Chebyshev preconditioner
+    int pg_grid_sh = 0, pg_grid_shc = 0;  // GMRES on the explicit S^ (SIMPLE), diag / Chebyshev
 };
 
 }  // namespace
@@ -1586,6 +1650,14 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
         L.pg_grid16 = (int)std::min<int64_t>((int64_t)occ16 * c.num_sms, need);
         L.pg_gridc = (int)std::min<int64_t>((int64_t)occc * c.num_sms, need);
         L.pg_grid16c = (int)std::min<int64_t>((int64_t)occ16c * c.num_sms, need);
+        if (kind == 1) {
+            int o1 = 0, o2 = 0;
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_gmres_shat<T, false>, kPgThreads, 0));
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_gmres_shat<T, true>, kPgThreads, 0));
+            if (o1 < 1 || o2 < 1) fail(HYEL_ECUDA, "persistent S^ solve kernel does not fit on an SM");
+            L.pg_grid_sh = (int)std::min<int64_t>((int64_t)o1 * c.num_sms, need);
+            L.pg_grid_shc = (int)std::min<int64_t>((int64_t)o2 * c.num_sms, need);
+        }
         const int64_t gmax = (int64_t)(2048 / kPgThreads) * c.num_sms;  // any co-resident grid
         L.pg_partial = (double *)walloc(c, w, sizeof(double) * 2 * (size_t)gmax * (m + 1));
     }
@@ -1648,6 +1720,8 @@ void check_params(const hyel_solver_params &p) {
         fail(HYEL_EINVAL, "solver params: bad a_precond");
     if (p.s_precond != HYEL_SPREC_JACOBI && p.s_precond != HYEL_SPREC_CHEB)
         fail(HYEL_EINVAL, "solver params: bad s_precond");
+    if (p.block_precond < HYEL_BLOCK_LDU || p.block_precond > HYEL_BLOCK_SIMPLE)
+        fail(HYEL_EINVAL, "solver params: bad block_precond");
     if (p.s_precond == HYEL_SPREC_CHEB) {
         if (p.a_precond != HYEL_APREC_BJACOBI)
             fail(HYEL_EINVAL, "solver params: the Chebyshev S-preconditioner needs block-Jacobi A-solves");
@@ -1962,7 +2036,91 @@ void schur_op(Rec &R, Workspace &w, const hyel_solver_params &p, const T *x, T *
     spmv_DC_ind<T>(c, Sys<T>::D(c), Sys<T>::C(c), x, xtil, y, ystride, yk);
 }
 
-// Algorithm 1 (SCR) as the preconditioner: (rv, rp) -> (xv, xp)
+// The S^-solve of SIMPLE: one cooperative launch of k_gmres_shat on the S-level
+// buffers and state
+template <typename T>
+void shat_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x) {
+    Ctx &c = *R.c;
+    const int64_t N = c.mesh.N;
+    Level<T> &Ls = Sys<T>::ls(w);
+    const SchurHat &h = *c.sh;
+    ShArgs<T> sa;
+    sa.slice_ptr = h.slice_ptr;
+    sa.row_len = h.row_len;
+    sa.col = h.col;
+    if constexpr (std::is_same<T, double>::value)
+        sa.val = h.v64;
+    else
+        sa.val = h.v32;
+    sa.dinv = Sys<T>::shat(c);
+    const bool cheb = p.s_precond == HYEL_SPREC_CHEB;
+    sa.zc = nullptr;
+    sa.ch = ChebArgs<T>{};
+    if (cheb) {
+        T *cb = Sys<T>::vec(w, 11, N);
+        float *db = reinterpret_cast<float *>(cb + 2 * N);
+        sa.zc = cb;
+        sa.ch = cheb_args<T>(c, p.s_cheb_degree, p.s_cheb_ratio, cb + N, db, db + N);
+    }
+    GmArgs<T> &g = sa.g;
+    g.N = N;
+    g.b = b;
+    g.x = x;
+    g.V = Ls.V;
+    g.U0 = Ls.z;
+    g.U1 = Ls.z2;
+    g.H = Ls.H;
+    g.partial = Ls.pg_partial;
+    g.bar = Ls.bar;
+    g.st = w.states + ST_S;
+    g.m = std::min(p.s.restart, Ls.m);
+    g.maxit = p.s.maxit;
+    g.rtol = p.s.rtol;
+    g.atol = p.s.atol;
+    g.eta2 = p.s.rtol >= kPgLoose<T> ? kPgEta2<T> : 0.5;
+    // one iteration: S^ values and columns, the gathered vector, and (Chebyshev)
+    // the polynomial's FP32 products and passes
+    g.it_fixed = (double)h.nnz * (sizeof(T) + 4.0) + (double)N * (2.0 * sizeof(T) + 8.0);
+    if (cheb) {
+        const int d = p.s_cheb_degree;
+        g.it_fixed += (d - 1) * ((double)h.nnz * 8.0 + (double)N * (sizeof(T) + 8.0)) +
+                      (3.0 + 6.0 * (d - 1)) * (double)N * sizeof(T);
+    }
+    g.it_unit = (double)N * sizeof(T);
+    HYEL_CK(cudaMemsetAsync(Ls.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    cudaLaunchConfig_t cfg = coop_config(c, cheb ? Ls.pg_grid_shc : Ls.pg_grid_sh);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaEvent_t ev;
+    prof_begin(c, HYEL_K_GMRES_S, &ev);
+    if (cheb)
+        HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_shat<T, true>, sa));
+    else
+        HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_shat<T, false>, sa));
+    count_launch();
+    prof_end(c, HYEL_K_GMRES_S, ev, 0.0);
+}
+
+// S x_p = r_p (Algorithm 1 step 3): the persistent S-solve with block-Jacobi
+// A-solves; a kernel-per-step loop with multigrid ones
+template <typename T>
+void s_level(Rec &R, Workspace &w, const hyel_solver_params &p, const T *rp, T *xp) {
+    Ctx &c = *R.c;
+    if (!w.a_amg) {
+        s_solve<T>(R, w, p, rp, xp);
+    } else {
+        Level<T> &Ls = Sys<T>::ls(w);
+        LevelState *sst = w.states + ST_S;
+        gm_solve<T, 1>(R, Ls, sst, p.s, rp, xp, Sys<T>::shat(c), nullptr,
+                       [&]() { schur_op<T>(R, w, p, Ls.z, Ls.V, &sst->k, Ls.n); }, true);
+    }
+}
+
+// The block preconditioner: (rv, rp) -> (xv, xp). LDU is Algorithm 1 (SCR);
+// DU, D and SIMPLE are the variants of §4.3–4.4.
 template <typename T>
 void pscr(Rec &R, Workspace &w, const hyel_solver_params &p, const T *rv, const T *rp, T *xv, T *xp) {
     Ctx &c = *R.c;
@@ -1970,20 +2128,37 @@ void pscr(Rec &R, Workspace &w, const hyel_solver_params &p, const T *rv, const 
     T *xhat = Sys<T>::vec(w, 0, N);
     T *rp2 = Sys<T>::vec(w, 1, N);
     T *rv2 = Sys<T>::vec(w, 2, N);
+    switch (p.block_precond) {
+        case HYEL_BLOCK_DU:
+            // S x_p = r_p; A x_v = r_v - B x_p
+            s_level<T>(R, w, p, rp, xp);
+            spmv_B<T>(c, Sys<T>::B(c), xp, rv2, rv);
+            a_solve<T>(R, w, w.states + ST_A2, p.a, rv2, xv);
+            return;
+        case HYEL_BLOCK_D:
+            // A x_v = r_v; S x_p = r_p
+            a_solve<T>(R, w, w.states + ST_A1, p.a, rv, xv);
+            s_level<T>(R, w, p, rp, xp);
+            return;
+        case HYEL_BLOCK_SIMPLE:
+            // A xhat = r_v; S^ x_p = r_p - C xhat; x_v = xhat - diag(A)^-1 B x_p
+            a_solve<T>(R, w, w.states + ST_A1, p.a, rv, xhat);
+            spmv_C<T>(c, Sys<T>::C(c), xhat, rp2, rp);
+            shat_solve<T>(R, w, p, rp2, xp);
+            spmv_B<T>(c, Sys<T>::B(c), xp, rv2, nullptr);
+            LAUNCH(k_simple_update<T><<<blocks_for(N, 256), 256, 0, c.stream>>>(c.mesh.diag_slot, Sys<T>::A(c), xhat,
+                                                                                rv2, xv, N));
+            return;
+        default:
+            break;
+    }
     // 1: A xhat = r_v
     a_solve<T>(R, w, w.states + ST_A1, p.a, rv, xhat);
     // 2: r_p <- r_p - C xhat
     spmv_C<T>(c, Sys<T>::C(c), xhat, rp2, rp);
-    // 3: S x_p = r_p, right-preconditioned by diag(S^)^-1: one persistent
-    // kernel with block-Jacobi A-solves; kernel-per-step loop with multigrid ones
-    if (!w.a_amg) {
-        s_solve<T>(R, w, p, rp2, xp);
-    } else {
-        Level<T> &Ls = Sys<T>::ls(w);
-        LevelState *sst = w.states + ST_S;
-        gm_solve<T, 1>(R, Ls, sst, p.s, rp2, xp, Sys<T>::shat(c), nullptr,
-                       [&]() { schur_op<T>(R, w, p, Ls.z, Ls.V, &sst->k, Ls.n); }, true);
-    }
+    // 3: S x_p = r_p, right-preconditioned by diag(S^)^-1 or the Chebyshev
+    // polynomial in S^: one persistent kernel with block-Jacobi A-solves
+    s_level<T>(R, w, p, rp2, xp);
     // 4: r_v <- r_v - B x_p
     spmv_B<T>(c, Sys<T>::B(c), xp, rv2, rv);
     // 5: A x_v = r_v
@@ -2073,6 +2248,18 @@ void ensure_graph(Ctx &c, Workspace &w, const hyel_solver_params &p) {
     w.have_key = true;
 }
 
+// Scaling, and the operators the parameters need: multigrid levels, the
+// explicit S^ and its interval (FP64 copy for SIMPLE's FP64 S^-solve).
+void prepare(Ctx &c, const hyel_solver_params &p) {
+    solve_setup(c);
+    if (p.a_precond == HYEL_APREC_AMG && !c.mat.amg_ready) {
+        amg_numeric(c);
+        c.mat.amg_ready = true;
+    }
+    if (p.s_precond == HYEL_SPREC_CHEB || p.block_precond == HYEL_BLOCK_SIMPLE) shat_setup(c);
+    if (p.block_precond == HYEL_BLOCK_SIMPLE && p.precision == HYEL_PREC_FP64) shat_ensure64(c);
+}
+
 // Kernel executions of the last solve from the level statistics.
 int64_t executed_kernels(Workspace &w) {
     int64_t total = w.top_nodes;
@@ -2089,12 +2276,7 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
     check_params(p);
     if (!c.mat.assembled) fail(HYEL_ESTATE, "solve: nothing assembled");
     auto t0 = std::chrono::steady_clock::now();
-    solve_setup(c);
-    if (p.a_precond == HYEL_APREC_AMG && !c.mat.amg_ready) {
-        amg_numeric(c);
-        c.mat.amg_ready = true;
-    }
-    if (p.s_precond == HYEL_SPREC_CHEB) shat_setup(c);
+    prepare(c, p);
     Workspace &w = workspace(c, p);
     if (p.graph) ensure_graph(c, w, p);
     HYEL_CK(cudaStreamSynchronize(c.stream));
@@ -2144,7 +2326,8 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
         if (hs[q].status_any & 1) st = HYEL_ENAN;
     }
     if (!std::isfinite(rel)) st = HYEL_ENAN;
-    const bool barrier_timeout = ((hs[ST_A1].status_any | hs[ST_A2].status_any | hs[ST_INNER].status_any) & 8) != 0;
+    const bool barrier_timeout =
+        ((hs[ST_A1].status_any | hs[ST_A2].status_any | hs[ST_S].status_any | hs[ST_INNER].status_any) & 8) != 0;
     if (barrier_timeout) st = HYEL_ECUDA;
     if (out) {
         out->status = st;
@@ -2160,7 +2343,7 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
         out->ms_solve = 1e3 * seconds_since(t1);
     }
     if (st != HYEL_OK) {
-        const char *what = barrier_timeout      ? "a grid barrier of the persistent A-solve timed out"
+        const char *what = barrier_timeout      ? "a grid barrier of a persistent solve kernel timed out"
                            : st == HYEL_ENOCONV ? "outer FGMRES reached its iteration cap"
                            : st == HYEL_ENAN    ? "NaN or Inf in the solve"
                            : st == HYEL_EBREAKDOWN ? "GMRES breakdown without convergence"
@@ -2323,11 +2506,7 @@ void shat_cheb_apply(Ctx &c, int matrix, int degree, double ratio, const double 
 void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y, hyel_solve_stats *out) {
     check_params(p);
     if (!c.mat.assembled) fail(HYEL_ESTATE, "schur_apply: nothing assembled");
-    solve_setup(c);
-    if (p.a_precond == HYEL_APREC_AMG && !c.mat.amg_ready) {
-        amg_numeric(c);
-        c.mat.amg_ready = true;
-    }
+    prepare(c, p);
     Workspace &w = workspace(c, p);
     const int64_t N = c.mesh.N;
     HYEL_CK(cudaMemsetAsync(w.states, 0, sizeof(LevelState) * 5, c.stream));
@@ -2354,6 +2533,47 @@ void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y
         out->inner_its = w.h_states[ST_INNER].its;
         out->inner_solves = w.h_states[ST_INNER].solves;
     }
+}
+
+void block_precond_apply(Ctx &c, const hyel_solver_params &p, const double *r, double *z, hyel_solve_stats *out) {
+    check_params(p);
+    if (!c.mat.assembled) fail(HYEL_ESTATE, "block_precond_apply: nothing assembled");
+    prepare(c, p);
+    Workspace &w = workspace(c, p);
+    const int64_t N = c.mesh.N, n = 4 * N;
+    HYEL_CK(cudaMemsetAsync(w.states, 0, sizeof(LevelState) * 5, c.stream));
+    Rec R;
+    R.c = &c;
+    R.graph = false;
+    R.check_every = p.check_every;
+    if (p.precision == HYEL_PREC_FP64) {
+        pscr<double>(R, w, p, r, r + 3 * N, z, z + 3 * N);
+    } else {
+        float *vf = Sys<float>::vec(w, 6, N), *zf = Sys<float>::vec(w, 7, N);
+        LAUNCH(k_copy_ind<double, float><<<blocks_for(n, 256), 256, 0, c.stream>>>(r, vf, n, nullptr, 0, 0));
+        pscr<float>(R, w, p, vf, vf + 3 * N, zf, zf + 3 * N);
+        LAUNCH(k_copy_ind<float, double><<<blocks_for(n, 256), 256, 0, c.stream>>>(zf, z, n, nullptr, 0, 0));
+    }
+    HYEL_CK(cudaGetLastError());
+    HYEL_CK(cudaMemcpyAsync(w.h_states, w.states, sizeof(LevelState) * 5, cudaMemcpyDeviceToHost, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    const LevelState *hs = w.h_states;
+    int st = HYEL_OK;
+    for (int q = 1; q < 5; q++) {
+        if (hs[q].status_any & 8) st = HYEL_ECUDA;
+        else if ((hs[q].status_any & 1) && st == HYEL_OK) st = HYEL_ENAN;
+    }
+    if (out) {
+        *out = hyel_solve_stats{};
+        out->status = st;
+        out->a_its = hs[ST_A1].its + hs[ST_A2].its;
+        out->s_its = hs[ST_S].its;
+        out->inner_its = hs[ST_INNER].its;
+        out->a_solves = hs[ST_A1].solves + hs[ST_A2].solves;
+        out->s_solves = hs[ST_S].solves;
+        out->inner_solves = hs[ST_INNER].solves;
+    }
+    if (st != HYEL_OK) fail(st, "block_precond_apply: a sub-solve failed (NaN/Inf or a barrier timeout)");
 }
 
 }  // namespace hyel
