@@ -340,3 +340,42 @@ def block_precond_apply(K, N, kind, r):
     else:
         raise ValueError(kind)
     return np.concatenate([np.linalg.solve(A, rv - B @ xp), xp])
+
+
+def symmetrized_schur(K, N):
+    """Dense S_sym = D - C A_sym^-1 B with A_sym = (A + A^T) / 2: the Schur
+    product when the inner A-solve of Algorithm 2 runs on the symmetrized
+    velocity block (the paper's conclusion: symmetrize and use CG as the inner
+    solver). Small systems only."""
+    A, B, C, D = split_blocks(K, N)
+    Asym = 0.5 * (A + A.T).toarray()
+    return D.toarray() - C.toarray() @ np.linalg.solve(Asym, B.toarray())
+
+
+def block_jacobi_pcg(Asym, Minv_blocks, b, rtol, maxit=10000):
+    """Preconditioned CG for Asym x = b from x = 0 with the 3x3 block-Jacobi
+    preconditioner (Minv_blocks [N, 3, 3]), in the textbook form (Saad,
+    Iterative Methods for Sparse Linear Systems, Algorithm 9.1); stops when
+    ||r|| <= rtol ||b||. Returns (x, iterations)."""
+    N = Minv_blocks.shape[0]
+    prec = lambda v: np.einsum("nij,nj->ni", Minv_blocks, v.reshape(N, 3)).ravel()
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = prec(r)
+    p = z.copy()
+    rz = r @ z
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return x, 0
+    for k in range(1, maxit + 1):
+        q = Asym @ p
+        alpha = rz / (p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        if np.linalg.norm(r) <= rtol * nb:
+            return x, k
+        z = prec(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, maxit

@@ -357,3 +357,43 @@ def test_block_preconditioner_structure():
     K2[:3 * N, :3 * N] = np.diag(np.diag(A))
     K2 = sp.csr_matrix(K2)
     assert np.allclose(S.block_precond_matrix(K2, N, "SIMPLE"), K2.toarray())
+
+
+# ------------------------------------------------------------ symmetrized inner solve
+
+def test_symmetrized_schur_equals_schur_for_symmetric_A():
+    rng = np.random.default_rng(60)
+    N = 5
+    n = 4 * N
+    K = rng.standard_normal((n, n))
+    A = K[:3 * N, :3 * N]
+    A[:] = A @ A.T + 3 * N * np.eye(3 * N)
+    Ks = sp.csr_matrix(K)
+    assert np.allclose(S.symmetrized_schur(Ks, N), S.explicit_schur(Ks, N), rtol=1e-11, atol=1e-11)
+    # a skew part changes it; the symmetric part alone decides
+    K2 = K.copy()
+    Sk = rng.standard_normal((3 * N, 3 * N))
+    K2[:3 * N, :3 * N] += Sk - Sk.T
+    K2 = sp.csr_matrix(K2)
+    assert np.allclose(S.symmetrized_schur(K2, N), S.symmetrized_schur(Ks, N), rtol=1e-11, atol=1e-11)
+    assert not np.allclose(S.explicit_schur(K2, N), S.explicit_schur(Ks, N), rtol=1e-6)
+
+
+def test_block_jacobi_pcg():
+    """PCG solves an SPD system; with M = A (block-diagonal A) it takes one
+    iteration; in exact arithmetic it ends within n iterations."""
+    rng = np.random.default_rng(61)
+    N = 10
+    n = 3 * N
+    Q = rng.standard_normal((n, n))
+    A = Q @ Q.T + n * np.eye(n)
+    blocks = np.array([A[3 * i:3 * i + 3, 3 * i:3 * i + 3] for i in range(N)])
+    Minv = np.linalg.inv(blocks)
+    b = rng.standard_normal(n)
+    x, k = S.block_jacobi_pcg(A, Minv, b, 1e-12)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9) and k <= n + 5
+    Ab = np.zeros((n, n))
+    for i in range(N):
+        Ab[3 * i:3 * i + 3, 3 * i:3 * i + 3] = blocks[i]
+    x1, k1 = S.block_jacobi_pcg(Ab, Minv, b, 1e-12)
+    assert k1 == 1 and np.allclose(x1, np.linalg.solve(Ab, b), rtol=1e-12)
