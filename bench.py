@@ -58,6 +58,8 @@ def parse():
                    help="S-solve preconditioner: the Chebyshev polynomial in the explicit S^ (default), "
                         "or diag(S^)^-1")
     p.add_argument("--cheb-degree", type=int, default=8)
+    p.add_argument("--inner", default="gmres", choices=["gmres", "cg"],
+                   help="inner A-solve of the S product: GMRES on A (default) or CG on (A + A^T)/2")
     p.add_argument("--block", default="ldu", choices=["ldu", "du", "d", "simple"],
                    help="block preconditioner of the outer FGMRES: Algorithm 1 (ldu, default), its DU and D "
                         "parts, or SIMPLE (the paper's comparison baseline)")
@@ -83,6 +85,7 @@ def config_dict(args, mesh):
         (f"lmax/lmin {args.cheb_ratio:g}" if args.cheb_ratio > 0 else "interval from Ritz values")
     return {"workload": f"cube{args.n}^3 compression, nu={args.nu}", "levels": args.precision,
             "s_precond": sprec, "block_precond": args.block.upper(),
+            "inner_solver": "CG on (A + A^T)/2" if args.inner == "cg" else "GMRES on A",
             "tets": int(mesh["tets"].shape[0]),
             "nodes": int(N), "unknowns": int(4 * N), "dt": 1e-3, "rho_inf": 0.5, "outer_rtol": 1e-10,
             "sub_rtol": 1e-2, "steps_per_run": "t = 0..K-1 from rest, load ramp over 10 steps",
@@ -307,7 +310,8 @@ def run_hyel(args, rank, world, local_rank):
     sprec_kw = {"s_precond": H.HYEL_SPREC_JACOBI if args.s_precond == "jacobi" else H.HYEL_SPREC_CHEB,
                 "s_cheb_degree": args.cheb_degree, "s_cheb_ratio": args.cheb_ratio,
                 "block_precond": {"ldu": H.HYEL_BLOCK_LDU, "du": H.HYEL_BLOCK_DU, "d": H.HYEL_BLOCK_D,
-                                  "simple": H.HYEL_BLOCK_SIMPLE}[args.block]}
+                                  "simple": H.HYEL_BLOCK_SIMPLE}[args.block],
+                "inner_solver": H.HYEL_INNER_CG_SYM if args.inner == "cg" else H.HYEL_INNER_GMRES}
     main_prec = {"fp64": H.HYEL_PREC_FP64, "fp32": H.HYEL_PREC_FP32, "bf16s": H.HYEL_PREC_BF16S}[args.precision]
     sp64 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=graph, **sprec_kw)
     sp32 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, graph=graph, **sprec_kw)

@@ -192,6 +192,16 @@ enum { HYEL_SPREC_JACOBI = 0, HYEL_SPREC_CHEB = 1 };
  * A-solves use the a-level controls, S-solves (matrix-free S, inner A-solves)
  * the s- and inner-level controls. */
 enum { HYEL_BLOCK_LDU = 0, HYEL_BLOCK_DU = 1, HYEL_BLOCK_D = 2, HYEL_BLOCK_SIMPLE = 3 };
+/* The inner A-solve of Algorithm 2 (the matrix-free S product):
+ * HYEL_INNER_GMRES: GMRES on A M^-1 with the inner-level controls (default);
+ * HYEL_INNER_CG_SYM: preconditioned CG on the symmetrized A_sym = (A + A^T)/2
+ *   with the 3x3 block-Jacobi preconditioner of A_sym (the paper's conclusion:
+ *   symmetrize the inner system and use CG), in the single-reduction form of
+ *   Chronopoulos and Gear, stopping at ||r|| <= max(rtol ||b||, atol) with the
+ *   inner-level controls (restart unused). The S product then applies
+ *   S_sym = D - C A_sym^-1 B, an approximation of S that the outer FGMRES
+ *   corrects. Needs a_precond = HYEL_APREC_BJACOBI. */
+enum { HYEL_INNER_GMRES = 0, HYEL_INNER_CG_SYM = 1 };
 
 typedef struct {
     hyel_krylov_level outer, a, s, inner;
@@ -203,7 +213,7 @@ typedef struct {
     int32_t s_cheb_degree;  /* HYEL_SPREC_CHEB: polynomial degree, 1..16 */
     double  s_cheb_ratio;   /* HYEL_SPREC_CHEB: 0 (estimated lmin) or lmax / lmin > 1 */
     int32_t block_precond;  /* HYEL_BLOCK_* */
-    int32_t reserved_;      /* must be 0 */
+    int32_t inner_solver;   /* HYEL_INNER_* */
 } hyel_solver_params;
 
 typedef struct {
@@ -337,8 +347,8 @@ int hyel_schur_hat_setup(hyel_ctx *ctx, double *bounds_out, int64_t *info, int n
 int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio, const double *x, double *y);
 
 /* y = S x for the scaled system (Algorithm 2: D x - C A^-1 (B x)), the inner
- * A-solve controlled by params->inner and params->precision. x, y: device
- * [N] double. */
+ * A-solve controlled by params->inner, params->inner_solver (A_sym with CG)
+ * and params->precision. x, y: device [N] double. */
 int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params,
                      const double *x, double *y, hyel_solve_stats *stats);
 

@@ -103,6 +103,12 @@ struct DeviceMatrix {
     float *jac32 = nullptr;
     double *shat64 = nullptr;   // [N] 1 / diag(S^) of the scaled system
     float *shat32 = nullptr;
+    // symmetrized scaled A, A_sym = (A + A^T)/2, in the layout of As, and the
+    // inverses of its 3x3 diagonal blocks (the CG inner solve), built on demand
+    double *Asym64 = nullptr;
+    float *Asym32 = nullptr;
+    double *jsym64 = nullptr;   // [9][N]
+    float *jsym32 = nullptr;
     // transposed operator [[A^T, C^T], [B^T, D^T]] in the same pattern: block
     // (i, c) holds A(c, i)^T, C(c, i), B(c, i), D(c, i)
     double *At = nullptr, *Bt = nullptr, *Ct = nullptr, *Dt = nullptr;
@@ -111,6 +117,7 @@ struct DeviceMatrix {
     bool amg_ready = false;   // multigrid operators built from the current scaled A
     bool shat_ready = false;    // explicit S^ (FP32) and its interval built from the current scaled blocks
     bool shat64_ready = false;  // ... and its FP64 copy
+    bool asym_ready = false;    // A_sym and its block-Jacobi inverses built from the current scaled A
     bool transposed = false;  // At..Dt hold the transpose of the current assembly
 };
 
@@ -241,6 +248,7 @@ void shat_spmv(Ctx &c, const T *x, T *y);  // y = S^ x, [N]
 // sparse.cu
 void solve_setup(Ctx &c);
 void transpose_assembled(Ctx &c);  // fills At..Dt from A..D (mirror slots)
+void asym_setup(Ctx &c);  // A_sym = (As + As^T)/2 and its diagonal-block inverses, unless current
 // SpMVs. The *_ind forms take kd = (k, done) of a Krylov level (the first two
 // ints of its device state): they write basis column k+1 (column stride given)
 // and do nothing once the level is done; kd == nullptr means plain pointers.

@@ -547,6 +547,23 @@ struct PgArgs {
     GmArgs<T> g;
 };
 
+// Arguments of the CG inner solve on A_sym (pg_cg_a below)
+template <typename T>
+struct CgArgs {
+    const int32_t *slice_ptr, *row_len, *col;
+    const T *Av;   // A_sym values
+    const T *jac;  // [9][N] inverses of A_sym's diagonal blocks
+    const T *b;
+    T *x, *r, *u, *p, *s, *w;  // [3N]
+    double *partial;           // 2 x [3][grid]
+    unsigned *bar;
+    LevelState *st;
+    int64_t N;
+    int maxit;
+    double rtol, atol;
+    double it_bytes;  // algorithmic bytes of one iteration
+};
+
 // Chebyshev polynomial preconditioner on the explicit S^: z = p(M^-1 S^) M^-1 v,
 // M = diag(S^), the interval [lmax / ratio, lmax]
 template <typename T, typename V = float>
@@ -570,6 +587,7 @@ struct SgArgs {
     T *xbar, *xtil;  // [3N] right-hand side and solution of the inner A-solve
     T *zc;           // [N] P^-1 v (Chebyshev only)
     ChebArgs<T> ch;
+    CgArgs<T> cg;    // the inner A-solve by CG on A_sym (HYEL_INNER_CG_SYM only)
     GmArgs<T> g;
 };
 
@@ -1193,14 +1211,177 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
     pg_gmres_a<T, H16>(a, phase);
 }
 
+// The inner A-solve on the symmetrized block (row-major 3x3 blocks of
+// A_sym = (A + A^T)/2 in the SELL-32 layout): preconditioned CG with the
+// block-Jacobi M = diag blocks of A_sym, in the single-reduction form of
+// Chronopoulos and Gear (1989): per iteration u = M^-1 r (row-local), a grid
+// barrier, w = A_sym u with the three dots (r, u), (w, u), (r, r) reduced
+// together, a grid barrier; then
+//   beta = g' / g, alpha = g' / (d - beta g' / alpha),
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s.
+// Stops at ||r|| <= max(rtol ||b||, atol) or maxit. Every block computes the
+// scalars from the same sums, so all take the same decisions.
+template <typename T>
+__device__ __forceinline__ void cg_minv(const CgArgs<T> &a, int64_t i) {
+    const int64_t N = a.N;
+    const T r0 = a.r[3 * i], r1 = a.r[3 * i + 1], r2 = a.r[3 * i + 2];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        a.u[3 * i + k] = __ldg(a.jac + (3 * k) * N + i) * r0 + __ldg(a.jac + (3 * k + 1) * N + i) * r1 +
+                         __ldg(a.jac + (3 * k + 2) * N + i) * r2;
+}
+
+// w_i = (A_sym u)_i; returns the row's contributions to (r, u), (w, u), (r, r)
+template <typename T>
+__device__ __forceinline__ void cg_row(const CgArgs<T> &a, int64_t i, T &g, T &d, T &q) {
+    const int t = (int)(i & 31);
+    const int64_t b0 = __ldg(a.slice_ptr + (i >> 5));
+    const int len = __ldg(a.row_len + i);
+    T y0 = 0, y1 = 0, y2 = 0;
+    for (int jb = 0; jb < len; jb++) {
+        const int64_t b = b0 + jb;
+        const int64_t c = __ldg(a.col + b * 32 + t);
+        const T u0 = a.u[3 * c], u1 = a.u[3 * c + 1], u2 = a.u[3 * c + 2];
+        const T *Ab = a.Av + (b * 9) * 32 + t;
+        y0 = fma(__ldg(Ab), u0, fma(__ldg(Ab + 32), u1, fma(__ldg(Ab + 64), u2, y0)));
+        y1 = fma(__ldg(Ab + 96), u0, fma(__ldg(Ab + 128), u1, fma(__ldg(Ab + 160), u2, y1)));
+        y2 = fma(__ldg(Ab + 192), u0, fma(__ldg(Ab + 224), u1, fma(__ldg(Ab + 256), u2, y2)));
+    }
+    a.w[3 * i] = y0;
+    a.w[3 * i + 1] = y1;
+    a.w[3 * i + 2] = y2;
+    const T r0 = a.r[3 * i], r1 = a.r[3 * i + 1], r2 = a.r[3 * i + 2];
+    const T v0 = a.u[3 * i], v1 = a.u[3 * i + 1], v2 = a.u[3 * i + 2];
+    g = fma(r0, v0, fma(r1, v1, fma(r2, v2, g)));
+    d = fma(y0, v0, fma(y1, v1, fma(y2, v2, d)));
+    q = fma(r0, r0, fma(r1, r1, fma(r2, r2, q)));
+}
+
+template <typename T>
+__device__ bool pg_cg_a(const CgArgs<T> &a, unsigned &phase) {
+    __shared__ double red1[kPgThreads / 32];
+    __shared__ double s_red[3];
+    const int64_t N = a.N;
+    const int G = gridDim.x;
+    LevelState *st = a.st;
+    auto pbuf = [&](unsigned ph) { return a.partial + (size_t)(ph & 1u) * 3 * G; };
+    auto abort_out = [&]() {
+        if (threadIdx.x == 0) {
+            atomicOr(&st->flags, 8);
+            atomicOr(&st->status_any, 8);
+            st->stop = 1;
+        }
+        return false;
+    };
+    // one grid reduction of three values (then every block holds the sums in s_red)
+    auto reduce3 = [&](T v0, T v1, T v2) {
+        const double t0 = pg_block_sum<T>(v0, red1);
+        if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = t0;
+        const double t1 = pg_block_sum<T>(v1, red1);
+        if (threadIdx.x == 0) pbuf(phase)[G + blockIdx.x] = t1;
+        const double t2 = pg_block_sum<T>(v2, red1);
+        if (threadIdx.x == 0) pbuf(phase)[2 * G + blockIdx.x] = t2;
+        if (!pg_barrier(a.bar, phase)) return false;
+        pg_sum(pbuf(phase - 1), 3, s_red);
+        __syncthreads();
+        return true;
+    };
+    // x = 0, r = b, u = M^-1 r
+    PG_FOR_OWN_NODES(N, i) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            a.x[3 * i + k] = 0;
+            a.r[3 * i + k] = a.b[3 * i + k];
+        }
+        cg_minv(a, i);
+    }
+    if (!pg_barrier(a.bar, phase)) return abort_out();
+    {
+        T g = 0, d = 0, q = 0;
+        PG_FOR_OWN_NODES(N, i) cg_row(a, i, g, d, q);
+        if (!reduce3(g, d, q)) return abort_out();
+    }
+    double gam = s_red[0], del = s_red[1];
+    const double bnorm = sqrt(s_red[2]);
+    const double tol = fmax(a.rtol * bnorm, a.atol);
+    int k = 0, flags = 0, conv = 0;
+    double alpha = 0.0, beta = 0.0;
+    if (!isfinite(bnorm) || !isfinite(gam) || !isfinite(del))
+        flags = 1;
+    else if (bnorm <= tol)
+        conv = 1;
+    else if (!(del != 0.0))
+        flags = 2;
+    else
+        alpha = gam / del;
+    while (!flags && !conv) {
+        const T ta = (T)alpha, tb = (T)beta;
+        const bool first = k == 0;
+        PG_FOR_OWN_NODES(N, i) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const int64_t o = 3 * i + q;
+                const T pv = first ? a.u[o] : fma(tb, a.p[o], a.u[o]);
+                const T sv = first ? a.w[o] : fma(tb, a.s[o], a.w[o]);
+                a.p[o] = pv;
+                a.s[o] = sv;
+                a.x[o] = fma(ta, pv, a.x[o]);
+                a.r[o] = fma(-ta, sv, a.r[o]);
+            }
+            cg_minv(a, i);
+        }
+        k += 1;
+        if (!pg_barrier(a.bar, phase)) return abort_out();  // u complete before it is gathered
+        T g = 0, d = 0, q = 0;
+        PG_FOR_OWN_NODES(N, i) cg_row(a, i, g, d, q);
+        if (!reduce3(g, d, q)) return abort_out();
+        const double gn = s_red[0], res = sqrt(s_red[2]);
+        del = s_red[1];
+        if (!isfinite(res) || !isfinite(gn) || !isfinite(del)) {
+            flags = 1;
+            break;
+        }
+        if (res <= tol) {
+            conv = 1;
+            break;
+        }
+        if (k >= a.maxit) break;
+        beta = gn / gam;
+        const double den = del - beta * gn / alpha;
+        if (!(den != 0.0) || !(gn != 0.0)) {
+            flags = 2;
+            break;
+        }
+        alpha = gn / den;
+        gam = gn;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->its += k;
+        st->solves += 1;
+        st->total = k;
+        st->converged = conv;
+        st->flags = flags;
+        st->status_any |= flags | ((!conv && !flags) ? 4 : 0);
+        st->alg_bytes += (k + 1) * a.it_bytes;
+        st->stop = 2;
+    }
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPgThreads, 2) k_cg_a(CgArgs<T> a) {
+    unsigned phase = 0u;  // the barrier words are cleared before every launch
+    pg_cg_a<T>(a, phase);
+}
+
 // The S-solve of Algorithm 1 (step 3) as one cooperative kernel: GMRES on
 // S P^-1 with the matrix-free product of Algorithm 2 inside,
 //   z = P^-1 v (diag(S^)^-1: applied while gathering; Chebyshev in S^: a few
 //   grid phases of its own), xbar = B z,
-//   xtil = A^-1 xbar (the A-solve above, on the same grid), barrier,
-//   w = D z - C xtil;
+//   xtil = A^-1 xbar (the A-solve above, or CG on A_sym, on the same grid),
+//   barrier, w = D z - C xtil;
 // x = P^-1 V y.
-template <typename T, bool H16, bool CHEB>
+template <typename T, bool H16, bool CHEB, bool ICG>
 __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T> a) {
     unsigned phase = 0u;  // the barrier words are cleared before every launch
     const int64_t N = s.g.N;
@@ -1232,7 +1413,11 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
             s.xbar[3 * i + 1] = a1 * sc;
             s.xbar[3 * i + 2] = a2 * sc;
         }
-        if (!pg_gmres_a<T, H16>(a, ph)) return false;
+        if constexpr (ICG) {
+            if (!pg_cg_a<T>(s.cg, ph)) return false;
+        } else {
+            if (!pg_gmres_a<T, H16>(a, ph)) return false;
+        }
         if (!pg_barrier(s.g.bar, ph)) return false;  // xtil complete before it is gathered
         PG_FOR_OWN_NODES(N, i) {
             const int t = (int)(i & 31);
@@ -1630,20 +1815,20 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
         if (kind == 0)
             HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_a<T, false>, kPgThreads, 0));
         else
-            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_s<T, false, false>, kPgThreads, 0));
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_s<T, false, false, false>, kPgThreads, 0));
         occ16 = occ;
         if constexpr (std::is_same<T, float>::value) {
             if (kind == 0)
                 HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_a<float, true>, kPgThreads, 0));
             else
-                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_s<float, true, false>, kPgThreads, 0));
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_s<float, true, false, false>, kPgThreads, 0));
         }
         int occc = occ, occ16c = occ16;
         if (kind == 1) {
-            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occc, k_gmres_s<T, false, true>, kPgThreads, 0));
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occc, k_gmres_s<T, false, true, false>, kPgThreads, 0));
             occ16c = occc;
             if constexpr (std::is_same<T, float>::value)
-                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16c, k_gmres_s<float, true, true>, kPgThreads, 0));
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16c, k_gmres_s<float, true, true, false>, kPgThreads, 0));
         }
         if (occ < 1 || occ16 < 1 || occc < 1 || occ16c < 1) fail(HYEL_ECUDA, "persistent solve kernel does not fit on an SM");
         L.pg_grid = (int)std::min<int64_t>((int64_t)occ * c.num_sms, need);
@@ -1722,6 +1907,14 @@ void check_params(const hyel_solver_params &p) {
         fail(HYEL_EINVAL, "solver params: bad s_precond");
     if (p.block_precond < HYEL_BLOCK_LDU || p.block_precond > HYEL_BLOCK_SIMPLE)
         fail(HYEL_EINVAL, "solver params: bad block_precond");
+    if (p.inner_solver != HYEL_INNER_GMRES && p.inner_solver != HYEL_INNER_CG_SYM)
+        fail(HYEL_EINVAL, "solver params: bad inner_solver");
+    if (p.inner_solver == HYEL_INNER_CG_SYM) {
+        if (p.a_precond != HYEL_APREC_BJACOBI)
+            fail(HYEL_EINVAL, "solver params: the CG inner solve needs block-Jacobi A-solves");
+        if (std::max(p.a.restart, p.inner.restart) < 2)
+            fail(HYEL_EINVAL, "solver params: the CG inner solve needs an A-level restart of at least 2");
+    }
     if (p.s_precond == HYEL_SPREC_CHEB) {
         if (p.a_precond != HYEL_APREC_BJACOBI)
             fail(HYEL_EINVAL, "solver params: the Chebyshev S-preconditioner needs block-Jacobi A-solves");
@@ -1858,6 +2051,16 @@ PgArgs<T> pg_args(Ctx &c, Workspace &w, LevelState *st, const hyel_krylov_level 
     return a;
 }
 
+// Co-resident grid of a persistent kernel (512-thread blocks), at most one
+// block per 32-row slice
+int resident_grid(Ctx &c, const void *kernel) {
+    int occ = 0;
+    HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kPgThreads, 0));
+    if (occ < 1) fail(HYEL_ECUDA, "persistent solve kernel does not fit on an SM");
+    const int64_t need = std::max<int64_t>(1, (c.mesh.N + 31) / 32);
+    return (int)std::min<int64_t>((int64_t)occ * c.num_sms, need);
+}
+
 cudaLaunchConfig_t coop_config(Ctx &c, int grid) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -1912,6 +2115,46 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
     prof_end(c, HYEL_K_GMRES_A, ev, 0.0);  // bytes are added from the level states after the solve
 }
 
+// CG arguments of the inner A-solve on A_sym (built by asym_setup), on the
+// A-level buffers: r, p, s in the first three basis columns, u and w in the
+// two direction buffers
+template <typename T>
+CgArgs<T> cg_args(Ctx &c, Workspace &w, const hyel_solver_params &p, const T *b, T *x) {
+    Level<T> &L = Sys<T>::la(w);
+    const DeviceMesh &msh = c.mesh;
+    const int64_t n = 3 * msh.N;
+    CgArgs<T> a;
+    a.slice_ptr = msh.slice_ptr;
+    a.row_len = msh.row_len;
+    a.col = msh.col;
+    if constexpr (std::is_same<T, double>::value) {
+        a.Av = c.mat.Asym64;
+        a.jac = c.mat.jsym64;
+    } else {
+        a.Av = c.mat.Asym32;
+        a.jac = c.mat.jsym32;
+    }
+    a.b = b;
+    a.x = x;
+    a.r = L.V;
+    a.p = L.V + n;
+    a.s = L.V + 2 * n;
+    a.u = L.z;
+    a.w = L.z2;
+    a.partial = L.pg_partial;
+    a.bar = L.bar;
+    a.st = w.states + ST_INNER;
+    a.N = msh.N;
+    a.maxit = p.inner.maxit;
+    a.rtol = p.inner.rtol;
+    a.atol = p.inner.atol;
+    // A_sym values + column indices + row data, M^-1, and the [3N] passes
+    // (u, w written; r, u read twice; p, s, x, r updated)
+    a.it_bytes = (double)msh.nnzb * (9.0 * sizeof(T) + 4.0) + 4.0 * (msh.N + 1) + 9.0 * msh.N * sizeof(T) +
+                 16.0 * n * sizeof(T);
+    return a;
+}
+
 // Chebyshev arguments on the explicit S^ (built by shat_setup): vectors of
 // precision T, values V (FP32 in the solver, either in the stand-alone apply)
 template <typename T, typename V = float>
@@ -1958,6 +2201,9 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
     sg.xbar = xbar;
     sg.xtil = xtil;
     const bool cheb = p.s_precond == HYEL_SPREC_CHEB;
+    const bool icg = p.inner_solver == HYEL_INNER_CG_SYM;
+    sg.cg = CgArgs<T>{};
+    if (icg) sg.cg = cg_args<T>(c, w, p, xbar, xtil);
     sg.zc = nullptr;
     sg.ch = ChebArgs<T>{};
     if (cheb) {
@@ -1996,7 +2242,10 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
                       (3.0 + 6.0 * (d - 1)) * (double)N * sizeof(T);
     }
     HYEL_CK(cudaMemsetAsync(La.bar, 0, kBarWords * sizeof(unsigned), c.stream));
-    cudaLaunchConfig_t cfg = coop_config(c, cheb ? (h16 ? Ls.pg_grid16c : Ls.pg_gridc) : (h16 ? Ls.pg_grid16 : Ls.pg_grid));
+    const void *kicg = cheb ? (const void *)k_gmres_s<T, false, true, true> : (const void *)k_gmres_s<T, false, false, true>;
+    cudaLaunchConfig_t cfg = coop_config(c, icg ? resident_grid(c, kicg)
+                                         : cheb ? (h16 ? Ls.pg_grid16c : Ls.pg_gridc)
+                                                : (h16 ? Ls.pg_grid16 : Ls.pg_grid));
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
     at[0].val.cooperative = 1;
@@ -2005,20 +2254,28 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_GMRES_S, &ev);
     bool launched = false;
+    if (icg) {
+        // the inner solve reads A_sym in the level's precision (no BF16 copy)
+        if (cheb)
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true, true>, sg, a));
+        else
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false, true>, sg, a));
+        launched = true;
+    }
     if constexpr (std::is_same<T, float>::value) {
-        if (h16) {
+        if (h16 && !launched) {
             if (cheb)
-                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, true>, sg, a));
+                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, true, false>, sg, a));
             else
-                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, false>, sg, a));
+                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, false, false>, sg, a));
             launched = true;
         }
     }
     if (!launched) {
         if (cheb)
-            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true>, sg, a));
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true, false>, sg, a));
         else
-            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false>, sg, a));
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false, false>, sg, a));
     }
     count_launch();
     prof_end(c, HYEL_K_GMRES_S, ev, 0.0);
@@ -2032,7 +2289,22 @@ void schur_op(Rec &R, Workspace &w, const hyel_solver_params &p, const T *x, T *
     T *xbar = Sys<T>::vec(w, 4, N);
     T *xtil = Sys<T>::vec(w, 5, N);
     spmv_B<T>(c, Sys<T>::B(c), x, xbar, nullptr);
-    a_solve<T>(R, w, w.states + ST_INNER, p.inner, xbar, xtil);
+    if (p.inner_solver == HYEL_INNER_CG_SYM) {
+        // one cooperative launch of the CG inner solve on A_sym
+        CgArgs<T> cg = cg_args<T>(c, w, p, xbar, xtil);
+        Level<T> &La = Sys<T>::la(w);
+        HYEL_CK(cudaMemsetAsync(La.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+        cudaLaunchConfig_t cfg = coop_config(c, resident_grid(c, (const void *)k_cg_a<T>));
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        HYEL_CK(cudaLaunchKernelEx(&cfg, k_cg_a<T>, cg));
+        count_launch();
+    } else {
+        a_solve<T>(R, w, w.states + ST_INNER, p.inner, xbar, xtil);
+    }
     spmv_DC_ind<T>(c, Sys<T>::D(c), Sys<T>::C(c), x, xtil, y, ystride, yk);
 }
 
@@ -2258,6 +2530,7 @@ void prepare(Ctx &c, const hyel_solver_params &p) {
     }
     if (p.s_precond == HYEL_SPREC_CHEB || p.block_precond == HYEL_BLOCK_SIMPLE) shat_setup(c);
     if (p.block_precond == HYEL_BLOCK_SIMPLE && p.precision == HYEL_PREC_FP64) shat_ensure64(c);
+    if (p.inner_solver == HYEL_INNER_CG_SYM) asym_setup(c);
 }
 
 // Kernel executions of the last solve from the level statistics.

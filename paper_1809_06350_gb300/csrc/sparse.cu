@@ -528,6 +528,94 @@ void solve_setup(Ctx &c) {
     c.mat.amg_ready = false;
     c.mat.shat_ready = false;
     c.mat.shat64_ready = false;
+    c.mat.asym_ready = false;
+}
+
+namespace {
+
+// A_sym = (A + A^T)/2 block by block: block (i, c) is (A_(i,c) + A_(c,i)^T)/2,
+// A_(c,i) at the mirror slot; padding slots get 0
+__global__ void k_symmetrize(const int32_t *__restrict__ mirror, const double *__restrict__ As,
+                             double *__restrict__ S64, float *__restrict__ S32, int64_t nslots) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nslots) return;
+    const int64_t b = q >> 5, t = q & 31, mq = mirror[q];
+    const int64_t mb = mq >> 5, mt = mq & 31;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s = 0; s < 3; s++) {
+            const double v = mq < 0 ? 0.0 : 0.5 * (As[(b * 9 + 3 * r + s) * 32 + t] + As[(mb * 9 + 3 * s + r) * 32 + mt]);
+            S64[(b * 9 + 3 * r + s) * 32 + t] = v;
+            S32[(b * 9 + 3 * r + s) * 32 + t] = (float)v;
+        }
+}
+
+// inverses of the 3x3 diagonal blocks of Av (adjugate over determinant)
+__global__ void k_block_inv3(const int32_t *__restrict__ diag_slot, const double *__restrict__ Av, double *j64,
+                             float *j32, int64_t N, unsigned *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t q = diag_slot[i], b = q >> 5, t = q & 31;
+    double m[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s = 0; s < 3; s++) m[r][s] = Av[(b * 9 + 3 * r + s) * 32 + t];
+    double inv[3][3];
+    inv[0][0] = m[1][1] * m[2][2] - m[1][2] * m[2][1];
+    inv[0][1] = m[0][2] * m[2][1] - m[0][1] * m[2][2];
+    inv[0][2] = m[0][1] * m[1][2] - m[0][2] * m[1][1];
+    inv[1][0] = m[1][2] * m[2][0] - m[1][0] * m[2][2];
+    inv[1][1] = m[0][0] * m[2][2] - m[0][2] * m[2][0];
+    inv[1][2] = m[0][2] * m[1][0] - m[0][0] * m[1][2];
+    inv[2][0] = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+    inv[2][1] = m[0][1] * m[2][0] - m[0][0] * m[2][1];
+    inv[2][2] = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+    const double det = m[0][0] * inv[0][0] + m[0][1] * inv[1][0] + m[0][2] * inv[2][0];
+    double scale = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s = 0; s < 3; s++) scale = fmax(scale, fabs(m[r][s]));
+    if (!(fabs(det) > 1e-300 && fabs(det) > 1e-14 * scale * scale * scale)) {
+        atomicOr(err, ERR_SINGULAR);
+        return;
+    }
+    const double id = 1.0 / det;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s = 0; s < 3; s++) {
+            const double v = inv[r][s] * id;
+            j64[(3 * r + s) * N + i] = v;
+            j32[(3 * r + s) * N + i] = (float)v;
+        }
+}
+
+}  // namespace
+
+void asym_setup(Ctx &c) {
+    solve_setup(c);
+    if (c.mat.asym_ready) return;
+    const DeviceMesh &m = c.mesh;
+    DeviceMatrix &M = c.mat;
+    if (!M.Asym64) {
+        M.Asym64 = dalloc_n<double>(c, 9 * (size_t)m.nslots);
+        M.Asym32 = dalloc_n<float>(c, 9 * (size_t)m.nslots);
+        M.jsym64 = dalloc_n<double>(c, 9 * (size_t)m.N);
+        M.jsym32 = dalloc_n<float>(c, 9 * (size_t)m.N);
+    }
+    HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
+    (k_symmetrize<<<blocks_for(m.nslots, 256), 256, 0, c.stream>>>(m.mirror, M.As, M.Asym64, M.Asym32, m.nslots),
+     ::hyel::count_launch());
+    (k_block_inv3<<<blocks_for(m.N, 256), 256, 0, c.stream>>>(m.diag_slot, M.Asym64, M.jsym64, M.jsym32, m.N, c.err),
+     ::hyel::count_launch());
+    HYEL_CK(cudaGetLastError());
+    HYEL_CK(cudaMemcpyAsync(c.h_err, c.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    if (*c.h_err & ERR_SINGULAR) fail(HYEL_ESINGULAR, "asym_setup: a 3x3 diagonal block of (A + A^T)/2 is singular");
+    M.asym_ready = true;
 }
 
 void transpose_assembled(Ctx &c) {

@@ -23,6 +23,7 @@ HYEL_PREC_FP64, HYEL_PREC_FP32, HYEL_PREC_BF16S = 0, 1, 2
 HYEL_APREC_BJACOBI, HYEL_APREC_AMG = 0, 1
 HYEL_SPREC_JACOBI, HYEL_SPREC_CHEB = 0, 1
 HYEL_BLOCK_LDU, HYEL_BLOCK_DU, HYEL_BLOCK_D, HYEL_BLOCK_SIMPLE = 0, 1, 2, 3
+HYEL_INNER_GMRES, HYEL_INNER_CG_SYM = 0, 1
 HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D, HYEL_OP_AM, HYEL_OP_SHAT = 0, 1, 2, 3, 4, 5, 6
 HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32, HYEL_MAT_TRANSPOSED, HYEL_MAT_SCALED_BF16S = 0, 1, 2, 3, 4
 (HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER, HYEL_K_SPMV_A16,
@@ -76,7 +77,7 @@ class HyelSolverParams(C.Structure):
                 ("inner", HyelKrylovLevel), ("precision", C.c_int32), ("check_every", C.c_int32),
                 ("graph", C.c_int32), ("a_precond", C.c_int32), ("s_precond", C.c_int32),
                 ("s_cheb_degree", C.c_int32), ("s_cheb_ratio", C.c_double), ("block_precond", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("inner_solver", C.c_int32)]
 
 
 class HyelSolveStats(C.Structure):
@@ -338,17 +339,19 @@ def level(rtol, maxit, restart, atol=1e-50):
 
 def solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=HYEL_PREC_FP64, outer=(200, 200),
                   a=(500, 500), s=(200, 200), inner=(500, 500), check_every=4, inner_rtol=None, graph=1,
-                  a_precond=0, s_precond=0, s_cheb_degree=4, s_cheb_ratio=0.0, block_precond=0):
+                  a_precond=0, s_precond=0, s_cheb_degree=4, s_cheb_ratio=0.0, block_precond=0,
+                  inner_solver=0):
     """Solver controls with the paper's defaults (§5: FGMRES(200), A: GMRES(500),
     S: GMRES(200), inner GMRES(500), absolute tolerances 1e-50). a_precond:
     HYEL_APREC_BJACOBI (default) or HYEL_APREC_AMG; s_precond: HYEL_SPREC_JACOBI
     (default) or HYEL_SPREC_CHEB (degree s_cheb_degree on [lmin, lmax] from Ritz
     estimates, or on [lmax / s_cheb_ratio, lmax] when s_cheb_ratio > 1);
-    block_precond: HYEL_BLOCK_LDU (Algorithm 1, default), _DU, _D or _SIMPLE."""
+    block_precond: HYEL_BLOCK_LDU (Algorithm 1, default), _DU, _D or _SIMPLE;
+    inner_solver: HYEL_INNER_GMRES (default) or HYEL_INNER_CG_SYM (CG on (A + A^T)/2)."""
     ir = sub_rtol if inner_rtol is None else inner_rtol
     return HyelSolverParams(level(outer_rtol, *outer), level(sub_rtol, *a), level(sub_rtol, *s),
                             level(ir, *inner), precision, check_every, graph, a_precond, s_precond,
-                            s_cheb_degree, s_cheb_ratio, block_precond, 0)
+                            s_cheb_degree, s_cheb_ratio, block_precond, inner_solver)
 
 
 def time_params(dt=1e-3, t_n=0.0, rho_inf=0.5, tol_r=1e-6, tol_a=1e-6, l_max=20, rhs_literal=0):
