@@ -17,6 +17,10 @@ Plain definitions, in float64:
   they interlace the spectrum, the Lanczos bounds) give the interval of the
   Chebyshev preconditioner: [theta_min / RITZ_LOW, RITZ_SAFETY theta_max]
   (``cheb_interval`` clamps it, or fixes lmin = lmax / ratio on request).
+* ``arnoldi_hessenberg_m`` / ``ritz_bounds_m`` / ``chebyshev_apply_block`` --
+  the same interval and polynomial for the velocity block A with the 3x3
+  block-Jacobi M (A's diagonal blocks): Arnoldi on M^-1 A in the M-inner
+  product (H symmetric when A is), z = p(M^-1 A) M^-1 v.
 * ``chebyshev_apply`` -- z = p(M^-1 S^) M^-1 v: a fixed number of steps of the
   Chebyshev iteration for S^ z = v, zero start, Jacobi-preconditioned, on the
   interval [lmin, lmax] (the three-term recurrence of the classical
@@ -126,6 +130,61 @@ def cheb_interval(bounds, ratio=0.0):
     return min(max(lmin, lmax / CHEB_MAX_RATIO), lmax / CHEB_MIN_RATIO), lmax
 
 
+def block_diag_inverse(A, N):
+    """Inverses [N, 3, 3] of the 3x3 diagonal blocks of A (3N x 3N)."""
+    A = A.tocsr()
+    blocks = np.array([A[3 * i:3 * i + 3, 3 * i:3 * i + 3].toarray() for i in range(N)])
+    return blocks, np.linalg.inv(blocks)
+
+
+def arnoldi_hessenberg_m(A, N, k=RITZ_STEPS):
+    """H (k+1 x k) of k Arnoldi steps on T = M^-1 A (M the 3x3 block diagonal
+    of A) in the M-inner product <x, y> = x^T M y, from the normalised
+    power_start(3N) vector, each new direction orthogonalised twice (classical
+    Gram-Schmidt). For symmetric A and SPD M, T is self-adjoint in this inner
+    product and H is symmetric."""
+    A = A.tocsr()
+    Mb, Mi = block_diag_inverse(A, N)
+    M = lambda v: np.einsum("nij,nj->ni", Mb, v.reshape(N, 3)).ravel()
+    Minv = lambda v: np.einsum("nij,nj->ni", Mi, v.reshape(N, 3)).ravel()
+    x = power_start(3 * N)
+    V = np.zeros((k + 1, 3 * N))
+    H = np.zeros((k + 1, k))
+    V[0] = x / np.sqrt(x @ M(x))
+    for j in range(k):
+        w = Minv(A @ V[j])
+        for _ in range(2):
+            h = V[:j + 1] @ M(w)
+            w = w - V[:j + 1].T @ h
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.sqrt(max(w @ M(w), 0.0))
+        if H[j + 1, j] == 0.0:
+            return H[:j + 2, :j + 1]
+        V[j + 1] = w / H[j + 1, j]
+    return H
+
+
+def ritz_bounds_m(A, N, k=RITZ_STEPS, Av=None):
+    """(lmin, lmax) for the Chebyshev interval of M^-1 A from the Ritz values of
+    arnoldi_hessenberg_m (eigenvalues of the symmetric part of H_k), with the
+    same safety factors as ritz_bounds. Av, if given, replaces A in the
+    products (M stays the block diagonal of A)."""
+    H = arnoldi_hessenberg_m(A if Av is None else _with_diag_blocks(Av, A, N), N, k)
+    kk = H.shape[1]
+    Hk = H[:kk, :kk]
+    theta = np.linalg.eigvalsh(0.5 * (Hk + Hk.T))
+    return theta[0] / RITZ_LOW, RITZ_SAFETY * theta[-1]
+
+
+def _with_diag_blocks(Av, A, N):
+    """Av with A's exact 3x3 diagonal blocks (so that M is A's block diagonal)."""
+    out = Av.tolil()
+    A = A.tocsr()
+    for i in range(N):
+        out[3 * i:3 * i + 3, 3 * i:3 * i + 3] = A[3 * i:3 * i + 3, 3 * i:3 * i + 3].toarray()
+    return out.tocsr()
+
+
 def chebyshev_apply(Sh, lmin, lmax, degree, v, Sv=None):
     """degree steps of the Chebyshev iteration for S^ z = v from z = 0 with the
     Jacobi preconditioner M = diag(S^), on [lmin, lmax]:
@@ -137,21 +196,35 @@ def chebyshev_apply(Sh, lmin, lmax, degree, v, Sv=None):
     The residual after `degree` steps is T_degree((theta - M^-1 S^) / delta) /
     T_degree(sigma) applied to v in the M^-1-preconditioned sense. Sv, if
     given, replaces S^ in the products (M stays diag(S^))."""
-    Sv = Sh if Sv is None else Sv
     dinv = jacobi_inverse(Sh)
+    return chebyshev_iteration(Sh if Sv is None else Sv, lambda r: dinv * r, lmin, lmax, degree, v)
+
+
+def chebyshev_apply_block(A, N, lmin, lmax, degree, v, Av=None):
+    """The same Chebyshev iteration for A z = v with the 3x3 block-Jacobi
+    preconditioner M (A's diagonal blocks): z = p(M^-1 A) M^-1 v. Av, if given,
+    replaces A in the products."""
+    _, Mi = block_diag_inverse(A, N)
+    minv = lambda r: np.einsum("nij,nj->ni", Mi, r.reshape(N, 3)).ravel()
+    return chebyshev_iteration(A if Av is None else Av, minv, lmin, lmax, degree, v)
+
+
+def chebyshev_iteration(Op, minv, lmin, lmax, degree, v):
+    """degree steps of the Chebyshev iteration for Op z = v from z = 0 with the
+    preconditioner minv (the recurrence of chebyshev_apply)."""
     theta = 0.5 * (lmax + lmin)
     delta = 0.5 * (lmax - lmin)
     sigma = theta / delta
     z = np.zeros_like(v)
     r = v.astype(np.float64).copy()
     rho = 1.0 / sigma
-    d = dinv * r / theta
+    d = minv(r) / theta
     for k in range(degree):
         z = z + d
         if k == degree - 1:
             break
-        r = r - Sv @ d
+        r = r - Op @ d
         rho_n = 1.0 / (2.0 * sigma - rho)
-        d = rho_n * rho * d + (2.0 * rho_n / delta) * (dinv * r)
+        d = rho_n * rho * d + (2.0 * rho_n / delta) * minv(r)
         rho = rho_n
     return z

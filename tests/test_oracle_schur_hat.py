@@ -204,3 +204,58 @@ def test_float32_values_keep_pattern_and_round_entries():
     # Sv replaces S^ in the products only: with Sv = S^ nothing changes
     v = rng.standard_normal(10)
     assert np.array_equal(SH.chebyshev_apply(Sh, 0.5, 3.0, 4, v), SH.chebyshev_apply(Sh, 0.5, 3.0, 4, v, Sv=Sh))
+
+
+def _spd_block_system(N, rng):
+    n = 3 * N
+    Q = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.3)
+    A = Q @ Q.T + n * np.eye(n) * 0.2
+    return sp.csr_matrix(A)
+
+
+def test_m_inner_product_arnoldi_symmetric_and_interlacing():
+    """For SPD A the M-inner-product Arnoldi on M^-1 A gives a symmetric H
+    (M^-1 A is self-adjoint in <x, y> = x^T M y) whose eigenvalues interlace
+    the spectrum of M^-1 A; with k = n steps they are that spectrum."""
+    rng = np.random.default_rng(90)
+    N = 8
+    A = _spd_block_system(N, rng)
+    Mb, Mi = SH.block_diag_inverse(A, N)
+    Mfull = np.zeros((3 * N, 3 * N))
+    for i in range(N):
+        Mfull[3 * i:3 * i + 3, 3 * i:3 * i + 3] = Mb[i]
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(Mfull, A.toarray())).real)
+    H = SH.arnoldi_hessenberg_m(A, N, 10)
+    Hk = H[:10, :10]
+    assert np.allclose(Hk, Hk.T, atol=1e-10 * np.abs(Hk).max())
+    theta = np.linalg.eigvalsh(0.5 * (Hk + Hk.T))
+    assert ev[0] - 1e-10 <= theta[0] and theta[-1] <= ev[-1] + 1e-10
+    Hn = SH.arnoldi_hessenberg_m(A, N, 3 * N)
+    kk = Hn.shape[1]
+    assert kk == 3 * N
+    assert np.allclose(np.linalg.eigvalsh(0.5 * (Hn + Hn.T)[:kk, :kk]), ev, atol=1e-8 * ev[-1])
+
+
+@pytest.mark.parametrize("degree", [1, 3, 5])
+def test_block_chebyshev_residual_polynomial(degree):
+    """z = p(M^-1 A) M^-1 v with M the 3x3 block diagonal: the residual
+    M^-1 (v - A z) is T_k((theta - M^-1 A)/delta) / T_k(sigma) M^-1 v."""
+    rng = np.random.default_rng(91 + degree)
+    N = 6
+    A = _spd_block_system(N, rng)
+    _, Mi = SH.block_diag_inverse(A, N)
+    Minv = np.zeros((3 * N, 3 * N))
+    for i in range(N):
+        Minv[3 * i:3 * i + 3, 3 * i:3 * i + 3] = Mi[i]
+    T = Minv @ A.toarray()
+    lam, X = np.linalg.eig(T)
+    lam, X = lam.real, X.real
+    lmin, lmax = 0.9 * lam.min(), 1.05 * lam.max()
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    v = rng.standard_normal(3 * N)
+    z = SH.chebyshev_apply_block(A, N, lmin, lmax, degree, v)
+    c = np.zeros(degree + 1)
+    c[degree] = 1.0
+    poly = npcheb.chebval((theta - lam) / delta, c) / npcheb.chebval(theta / delta, c)
+    ref = X @ (poly * np.linalg.solve(X, Minv @ v))
+    assert np.allclose(Minv @ (v - A @ z), ref, rtol=1e-9, atol=1e-11 * np.abs(Minv @ v).max())
