@@ -58,6 +58,10 @@ def parse():
                    help="S-solve preconditioner: the Chebyshev polynomial in the explicit S^ (default), "
                         "or diag(S^)^-1")
     p.add_argument("--cheb-degree", type=int, default=8)
+    p.add_argument("--a-precond", default="bjacobi", choices=["bjacobi", "cheb", "amg"],
+                   help="A-solve preconditioner: 3x3 block-Jacobi (default), the Chebyshev polynomial in "
+                        "M^-1 A, or aggregation multigrid")
+    p.add_argument("--dt", type=float, default=1e-3, help="time step (the paper's cube runs 1e-1 and 1e-5)")
     p.add_argument("--inner", default="gmres", choices=["gmres", "cg"],
                    help="inner A-solve of the S product: GMRES on A (default) or CG on (A + A^T)/2")
     p.add_argument("--block", default="ldu", choices=["ldu", "du", "d", "simple"],
@@ -70,7 +74,7 @@ def parse():
 
 def workload(args):
     from paper_1809_06350_gb300 import inputs
-    dt = 1e-3
+    dt = args.dt
     mesh = inputs.cube_mesh(args.n, jitter=0.05, seed=0)
     mu = 1e5
     mat = inputs.material_nh(mu, inputs.kappa_from_nu(mu, args.nu), 1e3)
@@ -86,8 +90,9 @@ def config_dict(args, mesh):
     return {"workload": f"cube{args.n}^3 compression, nu={args.nu}", "levels": args.precision,
             "s_precond": sprec, "block_precond": args.block.upper(),
             "inner_solver": "CG on (A + A^T)/2" if args.inner == "cg" else "GMRES on A",
+            "a_precond": args.a_precond,
             "tets": int(mesh["tets"].shape[0]),
-            "nodes": int(N), "unknowns": int(4 * N), "dt": 1e-3, "rho_inf": 0.5, "outer_rtol": 1e-10,
+            "nodes": int(N), "unknowns": int(4 * N), "dt": args.dt, "rho_inf": 0.5, "outer_rtol": 1e-10,
             "sub_rtol": 1e-2, "steps_per_run": "t = 0..K-1 from rest, load ramp over 10 steps",
             "l2": "working set larger than L2 (FP64 blocks 218 MB, Krylov bases > 1 GB); no flush",
             "parallelism": "replicas"}
@@ -184,7 +189,7 @@ def cpu_sample(n_sample=12, steps=2, args=None):
     mu = 1e5
     nu = args.nu if args else 0.3
     mat = inputs.material_nh(mu, inputs.kappa_from_nu(mu, nu), 1e3)
-    dt = 1e-3
+    dt = args.dt if args else 1e-3
     prob = S.Problem(mesh, mat, load={"p_max": 2e4, "t_ramp": 10 * dt})
     z = inputs.zero_state(prob.N)
     yn = {k: z[k] for k in ("u", "p", "v")}
@@ -311,7 +316,9 @@ def run_hyel(args, rank, world, local_rank):
                 "s_cheb_degree": args.cheb_degree, "s_cheb_ratio": args.cheb_ratio,
                 "block_precond": {"ldu": H.HYEL_BLOCK_LDU, "du": H.HYEL_BLOCK_DU, "d": H.HYEL_BLOCK_D,
                                   "simple": H.HYEL_BLOCK_SIMPLE}[args.block],
-                "inner_solver": H.HYEL_INNER_CG_SYM if args.inner == "cg" else H.HYEL_INNER_GMRES}
+                "inner_solver": H.HYEL_INNER_CG_SYM if args.inner == "cg" else H.HYEL_INNER_GMRES,
+                "a_precond": {"bjacobi": H.HYEL_APREC_BJACOBI, "cheb": H.HYEL_APREC_CHEB,
+                              "amg": H.HYEL_APREC_AMG}[args.a_precond]}
     main_prec = {"fp64": H.HYEL_PREC_FP64, "fp32": H.HYEL_PREC_FP32, "bf16s": H.HYEL_PREC_BF16S}[args.precision]
     sp64 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=graph, **sprec_kw)
     sp32 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, graph=graph, **sprec_kw)

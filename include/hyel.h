@@ -161,8 +161,18 @@ typedef struct {
  *   paper's algebraic multigrid, §4.4): unsmoothed-aggregation Galerkin levels
  *   with 3x3 blocks, damped block-Jacobi smoothing, as the right preconditioner
  *   of an FGMRES A-level. The hierarchy's pattern is built once per mesh, its
- *   operators once per assembly (after the scaling). */
-enum { HYEL_APREC_BJACOBI = 0, HYEL_APREC_AMG = 1 };
+ *   operators once per assembly (after the scaling);
+ * HYEL_APREC_CHEB: the polynomial p(M^-1 A) M^-1 of degree a_cheb_degree
+ *   (1..16), M the 3x3 block diagonal of A: that many steps of the Chebyshev
+ *   iteration for A z = v from z = 0 on [lmin, lmax] from Ritz values of
+ *   M^-1 A (12 Arnoldi steps in the M-inner product, FP32; lmax = 1.05
+ *   theta_max, lmin = theta_min / 2 clamped to [lmax / 1000, lmax / 1.5]),
+ *   rebuilt after every scaling of a new assembly. The polynomial reads A in
+ *   FP32 with FP32 directions; the A-solves (GMRES on A p(M^-1 A) M^-1, one
+ *   persistent launch each, the inner ones inside the S-solve) multiply by A
+ *   in the level's precision (FP32 for HYEL_PREC_BF16S: no BF16 copy). For
+ *   stiffness-dominated A, where block-Jacobi alone needs long GMRES cycles. */
+enum { HYEL_APREC_BJACOBI = 0, HYEL_APREC_AMG = 1, HYEL_APREC_CHEB = 2 };
 /* Preconditioner of the S-solve (§4.2):
  * HYEL_SPREC_JACOBI: diag(S^)^-1, S^ = D - C diag(A)^-1 B (the default);
  * HYEL_SPREC_CHEB: the polynomial p(diag(S^)^-1 S^) diag(S^)^-1 of degree
@@ -214,6 +224,8 @@ typedef struct {
     double  s_cheb_ratio;   /* HYEL_SPREC_CHEB: 0 (estimated lmin) or lmax / lmin > 1 */
     int32_t block_precond;  /* HYEL_BLOCK_* */
     int32_t inner_solver;   /* HYEL_INNER_* */
+    int32_t a_cheb_degree;  /* HYEL_APREC_CHEB: polynomial degree, 1..16 */
+    int32_t reserved_;      /* must be 0 */
 } hyel_solver_params;
 
 typedef struct {
@@ -351,6 +363,18 @@ int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio,
  * and params->precision. x, y: device [N] double. */
 int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params,
                      const double *x, double *y, hyel_solve_stats *stats);
+
+/* The HYEL_APREC_CHEB interval of M^-1 A for the current scaled system (runs
+ * hyel_solve_setup if needed; built unless current). bounds_out: host [2]
+ * (lmin, lmax) or NULL. Synchronizes. */
+int hyel_a_cheb_setup(hyel_ctx *ctx, double *bounds_out);
+
+/* y = p(M^-1 A) M^-1 x, the HYEL_APREC_CHEB polynomial of the given degree
+ * (1..16) on the interval of hyel_a_cheb_setup, as inside the A-solves: FP32
+ * A values and directions, FP64 residual and result. x, y: device [3N]
+ * double, distinct. HYEL_ESTATE before hyel_a_cheb_setup on the current
+ * assembly. Synchronizes. */
+int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y);
 
 /* z = P^-1 r once, P the block preconditioner of params->block_precond on the
  * scaled system (§4.2–4.4), its sub-solves controlled by params (precision,

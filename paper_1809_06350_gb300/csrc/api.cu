@@ -159,6 +159,7 @@ int hyel_destroy(hyel_ctx *ctx) {
     hyel::free_workspace(ctx->c);
     hyel::amg_free(ctx->c);
     hyel::shat_free(ctx->c);
+    hyel::acheb_free(ctx->c);
     hyel::dfree_all(ctx->c);
     for (auto &r : ctx->c.prof.pending) {
         cudaEventDestroy(r.a);
@@ -306,6 +307,23 @@ int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params, const doub
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!params || !x || !y) hyel::fail(HYEL_EINVAL, "schur_apply: null argument");
         hyel::schur_apply(c, *params, x, y, stats);
+    });
+}
+
+int hyel_a_cheb_setup(hyel_ctx *ctx, double *bounds_out) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        hyel::acheb_setup(c);
+        if (bounds_out) {
+            bounds_out[0] = c.ach->h_bounds[0];
+            bounds_out[1] = c.ach->h_bounds[1];
+        }
+    });
+}
+
+int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!x || !y) hyel::fail(HYEL_EINVAL, "a_cheb_apply: null vector");
+        hyel::acheb_apply(c, degree, x, y);
     });
 }
 

@@ -118,6 +118,7 @@ struct DeviceMatrix {
     bool shat_ready = false;    // explicit S^ (FP32) and its interval built from the current scaled blocks
     bool shat64_ready = false;  // ... and its FP64 copy
     bool asym_ready = false;    // A_sym and its block-Jacobi inverses built from the current scaled A
+    bool acheb_ready = false;   // the A-Chebyshev interval of the current scaled A
     bool transposed = false;  // At..Dt hold the transpose of the current assembly
 };
 
@@ -141,6 +142,20 @@ struct Profile {
     double ms[HYEL_K_NCLASSES] = {0};
     int64_t launches[HYEL_K_NCLASSES] = {0};
     double bytes[HYEL_K_NCLASSES] = {0};
+};
+
+// Chebyshev interval of M^-1 A (HYEL_APREC_CHEB) and the FP32 scratch of its
+// Arnoldi run and of the stand-alone apply (solver.cu)
+struct AChebState {
+    double *bounds = nullptr;   // device [2]: lmin, lmax
+    double h_bounds[2] = {0.0, 0.0};
+    float *V = nullptr;         // [(steps + 1) 3N]
+    float *U = nullptr;         // [3 x 3N]: two directions and M w
+    double *H = nullptr;        // [(steps + 1) steps]
+    double *partial = nullptr;  // [2][steps + 1][grid]
+    unsigned *bar = nullptr;
+    double *work = nullptr;     // [3N] residual of the stand-alone apply
+    float *dwork = nullptr;     // [2 x 3N] its directions
 };
 
 struct Workspace;  // Krylov workspaces (solver.cu)
@@ -191,6 +206,7 @@ struct Ctx {
     Workspace *ws = nullptr;
     Amg *amg = nullptr;
     SchurHat *sh = nullptr;
+    AChebState *ach = nullptr;
     Profile prof;
     size_t bytes_held = 0;
     int num_sms = 152;
@@ -281,6 +297,9 @@ void free_workspace(Ctx &c);
 void shat_bounds(Ctx &c);  // Chebyshev interval of diag(S^)^-1 S^ from Arnoldi Ritz values (host-checked)
 void shat_setup(Ctx &c);  // solve_setup, then S^ and its bound unless current
 void shat_cheb_apply(Ctx &c, int matrix, int degree, double ratio, const double *x, double *y);
+void acheb_setup(Ctx &c);  // solve_setup, then the A-Chebyshev interval unless current
+void acheb_apply(Ctx &c, int degree, const double *x, double *y);
+void acheb_free(Ctx &c);
 
 // adjoint.cu
 void solve_nested_transpose(Ctx &c, const hyel_solver_params &p, const double *rhs, double *x,

@@ -48,6 +48,7 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     free_workspace(c);
     amg_free(c);
     shat_free(c);
+    acheb_free(c);
     dfree_all(c);
     c.mesh = DeviceMesh();
     c.mat = DeviceMatrix();
@@ -391,6 +392,7 @@ void mesh_upload(Ctx &c, int64_t N, const double *X, int64_t E, const int32_t *t
         free_workspace(c);
         amg_free(c);
         shat_free(c);
+        acheb_free(c);
         dfree_all(c);
         c.mesh = DeviceMesh();
         c.mat = DeviceMatrix();

@@ -535,7 +535,19 @@ struct GmArgs {
     double eta2;               // single Gram-Schmidt pass when ||w - V h||^2 >= eta2 ||w||^2
 };
 
-// The A-solve: GMRES on A M^-1 (3 values per node)
+// Chebyshev polynomial preconditioner of the A-solves (HYEL_APREC_CHEB):
+// z = p(M^-1 A) M^-1 v, M the 3x3 block diagonal of A
+template <typename T>
+struct AChArgs {
+    const float *Af;       // FP32 scaled A: the polynomial's products
+    const T *A;            // scaled A of precision T: the A-solve's product
+    const double *bounds;  // device [2]: estimated lmin, lmax
+    int degree;
+    T *zc, *r;             // [3N]
+    float *d0, *d1;        // [3N]
+};
+
+// The A-solve: GMRES on A M^-1 (3 values per node), or on A p(M^-1 A) M^-1
 template <typename T>
 struct PgArgs {
     const int32_t *slice_ptr, *row_len, *col;
@@ -544,6 +556,7 @@ struct PgArgs {
     const uint16_t *Am1;
     const float *Ams;
     const T *jac;                             // [9][N] M^-1
+    AChArgs<T> ac;                            // HYEL_APREC_CHEB only
     GmArgs<T> g;
 };
 
@@ -1181,34 +1194,141 @@ __device__ bool pg_gmres(const GmArgs<T> &a, unsigned &phase, Op &&op, XUpd &&xu
     }
 }
 
+// Row i of V-valued 3x3 blocks (SELL-32 layout of As) times u: y = (Av u)_i
+template <typename V, typename X, typename Y>
+__device__ __forceinline__ void block_row(const int32_t *slice_ptr, const int32_t *row_len, const int32_t *col,
+                                          const V *Av, int64_t i, const X *u, Y &y0, Y &y1, Y &y2) {
+    const int t = (int)(i & 31);
+    const int64_t b0 = __ldg(slice_ptr + (i >> 5));
+    const int len = __ldg(row_len + i);
+    Y a0 = 0, a1 = 0, a2 = 0;
+    for (int jb = 0; jb < len; jb++) {
+        const int64_t b = b0 + jb;
+        const int64_t c = __ldg(col + b * 32 + t);
+        const Y x0 = (Y)u[3 * c], x1 = (Y)u[3 * c + 1], x2 = (Y)u[3 * c + 2];
+        const V *Ab = Av + (b * 9) * 32 + t;
+        a0 = fma((Y)__ldg(Ab), x0, fma((Y)__ldg(Ab + 32), x1, fma((Y)__ldg(Ab + 64), x2, a0)));
+        a1 = fma((Y)__ldg(Ab + 96), x0, fma((Y)__ldg(Ab + 128), x1, fma((Y)__ldg(Ab + 160), x2, a1)));
+        a2 = fma((Y)__ldg(Ab + 192), x0, fma((Y)__ldg(Ab + 224), x1, fma((Y)__ldg(Ab + 256), x2, a2)));
+    }
+    y0 = a0;
+    y1 = a1;
+    y2 = a2;
+}
+
+// z = p(M^-1 A) M^-1 v over the grid (the recurrence of pg_cheb with the 3x3
+// block-Jacobi M): the directions and the A d products in FP32 with the FP32
+// copy of A, r and z in T. v may alias a.ac.r. Ends with a grid barrier.
+template <typename T>
+__device__ bool pg_cheb3(const PgArgs<T> &a, const T *v, T *z, bool add, unsigned &phase) {
+    const AChArgs<T> &ch = a.ac;
+    const int64_t N = a.g.N;
+    const double lmax = ch.bounds[1];
+    const double lmin = fmin(fmax(ch.bounds[0], lmax / kChebMaxRatio), lmax / kChebMinRatio);
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    auto minv = [&](int64_t i, const T (&r)[3], T (&m)[3]) {
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            m[k] = __ldg(a.jac + (3 * k) * N + i) * r[0] + __ldg(a.jac + (3 * k + 1) * N + i) * r[1] +
+                   __ldg(a.jac + (3 * k + 2) * N + i) * r[2];
+    };
+    {
+        const T it = (T)(1.0 / theta);
+        PG_FOR_OWN_NODES(N, i) {
+            T r[3], m[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) r[k] = v[3 * i + k];
+            minv(i, r, m);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                ch.r[3 * i + k] = r[k];
+                const float d = (float)(m[k] * it);
+                ch.d0[3 * i + k] = d;
+                z[3 * i + k] = add ? z[3 * i + k] + (T)d : (T)d;
+            }
+        }
+    }
+    if (!pg_barrier(a.g.bar, phase)) return false;
+    float *dc = ch.d0, *dn = ch.d1;
+    for (int k = 1; k < ch.degree; k++) {
+        const double rho_n = 1.0 / (2.0 * sigma - rho);
+        const T a1 = (T)(rho_n * rho), a2 = (T)(2.0 * rho_n / delta);
+        PG_FOR_OWN_NODES(N, i) {
+            float s0, s1, s2;
+            block_row<float, float, float>(a.slice_ptr, a.row_len, a.col, ch.Af, i, dc, s0, s1, s2);
+            T r[3], m[3];
+            r[0] = ch.r[3 * i] - (T)s0;
+            r[1] = ch.r[3 * i + 1] - (T)s1;
+            r[2] = ch.r[3 * i + 2] - (T)s2;
+            minv(i, r, m);
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                ch.r[3 * i + q] = r[q];
+                const float d = (float)(a1 * (T)dc[3 * i + q] + a2 * m[q]);
+                dn[3 * i + q] = d;
+                z[3 * i + q] += (T)d;
+            }
+        }
+        rho = rho_n;
+        if (!pg_barrier(a.g.bar, phase)) return false;
+        float *tmp = dc;
+        dc = dn;
+        dn = tmp;
+    }
+    return true;
+}
+
 // The A-solve on the calling grid: operator A M^-1 (phase 1 of an iteration is
-// the SELL-32 SpMV, gathering u), x += M^-1 V y.
-template <typename T, bool H16>
+// the SELL-32 SpMV, gathering u), x += M^-1 V y; with ACH the operator is
+// A p(M^-1 A) M^-1 (the polynomial's grid phases, then the SpMV with the
+// unfolded A on z) and x += p(M^-1 A) M^-1 V y.
+template <typename T, bool H16, bool ACH = false>
 __device__ bool pg_gmres_a(const PgArgs<T> &a, unsigned &phase) {
     const int64_t N = a.g.N;
-    auto op = [&](const T *u, T sc, T *w, unsigned &) {
-        PG_FOR_OWN_NODES(N, i) {
-            T y0, y1, y2;
-            pg_row<T, H16>(a, i, u, y0, y1, y2);
-            w[3 * i] = y0 * sc;
-            w[3 * i + 1] = y1 * sc;
-            w[3 * i + 2] = y2 * sc;
+    auto op = [&](const T *u, T sc, T *w, unsigned &ph) {
+        if constexpr (ACH) {
+            if (!pg_cheb3<T>(a, u, a.ac.zc, false, ph)) return false;
+            PG_FOR_OWN_NODES(N, i) {
+                T y0, y1, y2;
+                block_row<T, T, T>(a.slice_ptr, a.row_len, a.col, a.ac.A, i, a.ac.zc, y0, y1, y2);
+                w[3 * i] = y0 * sc;
+                w[3 * i + 1] = y1 * sc;
+                w[3 * i + 2] = y2 * sc;
+            }
+        } else {
+            PG_FOR_OWN_NODES(N, i) {
+                T y0, y1, y2;
+                pg_row<T, H16>(a, i, u, y0, y1, y2);
+                w[3 * i] = y0 * sc;
+                w[3 * i + 1] = y1 * sc;
+                w[3 * i + 2] = y2 * sc;
+            }
         }
         return true;
     };
-    auto xupd = [&](int64_t i, const T (&u)[3]) {
+    if constexpr (ACH) {
+        auto xupd = [&](int64_t i, const T (&u)[3]) {
 #pragma unroll
-        for (int r = 0; r < 3; r++)
-            a.g.x[3 * i + r] += __ldg(a.jac + (3 * r) * N + i) * u[0] + __ldg(a.jac + (3 * r + 1) * N + i) * u[1] +
-                                __ldg(a.jac + (3 * r + 2) * N + i) * u[2];
-    };
-    return pg_gmres<T, 3>(a.g, phase, op, xupd);
+            for (int r = 0; r < 3; r++) a.ac.r[3 * i + r] = u[r];
+        };
+        auto xend = [&](unsigned &ph) { return pg_cheb3<T>(a, a.ac.r, a.g.x, true, ph); };
+        return pg_gmres<T, 3>(a.g, phase, op, xupd, xend);
+    } else {
+        auto xupd = [&](int64_t i, const T (&u)[3]) {
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+                a.g.x[3 * i + r] += __ldg(a.jac + (3 * r) * N + i) * u[0] + __ldg(a.jac + (3 * r + 1) * N + i) * u[1] +
+                                    __ldg(a.jac + (3 * r + 2) * N + i) * u[2];
+        };
+        return pg_gmres<T, 3>(a.g, phase, op, xupd);
+    }
 }
 
-template <typename T, bool H16>
+template <typename T, bool H16, bool ACH>
 __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_a(PgArgs<T> a) {
     unsigned phase = 0u;  // the barrier words are cleared before every launch
-    pg_gmres_a<T, H16>(a, phase);
+    pg_gmres_a<T, H16, ACH>(a, phase);
 }
 
 // The inner A-solve on the symmetrized block (row-major 3x3 blocks of
@@ -1381,7 +1501,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_cg_a(CgArgs<T> a) {
 //   xtil = A^-1 xbar (the A-solve above, or CG on A_sym, on the same grid),
 //   barrier, w = D z - C xtil;
 // x = P^-1 V y.
-template <typename T, bool H16, bool CHEB, bool ICG>
+template <typename T, bool H16, bool CHEB, bool ICG, bool ACH>
 __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T> a) {
     unsigned phase = 0u;  // the barrier words are cleared before every launch
     const int64_t N = s.g.N;
@@ -1416,7 +1536,7 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
         if constexpr (ICG) {
             if (!pg_cg_a<T>(s.cg, ph)) return false;
         } else {
-            if (!pg_gmres_a<T, H16>(a, ph)) return false;
+            if (!pg_gmres_a<T, H16, ACH>(a, ph)) return false;
         }
         if (!pg_barrier(s.g.bar, ph)) return false;  // xtil complete before it is gathered
         PG_FOR_OWN_NODES(N, i) {
@@ -1614,6 +1734,120 @@ __global__ void __launch_bounds__(kPgThreads) k_shat_arnoldi(ArnArgs a) {
     }
 }
 
+// Ritz values for the A-Chebyshev interval: kRitzSteps steps of Arnoldi on
+// M^-1 A in the M-inner product <x, y> = x^T M y (M the 3x3 block diagonal of
+// A; M^-1 A is self-adjoint there when A is symmetric, so H is then
+// symmetric), in FP32 with the FP32 copy of A (sums across blocks in FP64),
+// one cooperative launch. Start vector: x0[k] = 2 u_k - 1 from output k of
+// SplitMix64 (k = 3 i + component). Each new direction is orthogonalised
+// twice (classical Gram-Schmidt); block 0 writes H[j * (k + 1) + i].
+struct AArnArgs {
+    const int32_t *slice_ptr, *row_len, *col, *diag_slot;
+    const float *Af, *jac;  // FP32 scaled A and M^-1 [9][N]
+    float *V, *U;           // V: [(k + 1) 3N]; U: [3 x 3N] two directions and M w
+    double *H, *partial;
+    unsigned *bar;
+    int64_t N;
+};
+
+// y = M_i x_i with M_i the diagonal block of row i
+__device__ __forceinline__ void diag_block_apply(const AArnArgs &a, int64_t i, const float *x, float *y) {
+    const int64_t q = __ldg(a.diag_slot + i), b = q >> 5, t = q & 31;
+    const float x0 = x[3 * i], x1 = x[3 * i + 1], x2 = x[3 * i + 2];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+        y[3 * i + r] = __ldg(a.Af + (b * 9 + 3 * r) * 32 + t) * x0 + __ldg(a.Af + (b * 9 + 3 * r + 1) * 32 + t) * x1 +
+                       __ldg(a.Af + (b * 9 + 3 * r + 2) * 32 + t) * x2;
+}
+
+__global__ void __launch_bounds__(kPgThreads) k_a_arnoldi(AArnArgs a) {
+    __shared__ double red1[kPgThreads / 32];
+    __shared__ double s_sum[kRitzSteps + 2], s_h[kRitzSteps + 2];
+    __shared__ float hs[kRitzSteps + 2];
+    unsigned phase = 0u;
+    const int64_t N = a.N, n = 3 * N;
+    const int G = gridDim.x, K1 = kRitzSteps + 1;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    float *Mw = a.U + 2 * n;
+    auto pbuf = [&](unsigned ph) { return a.partial + (size_t)(ph & 1u) * G * K1; };
+    auto fail_out = [&]() {
+        if (lead) a.H[0] = nan("");
+    };
+    float ss = 0.0f;
+    PG_FOR_OWN_NODES(N, i) {
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            a.U[3 * i + k] =
+                (float)(2.0 * ((double)(splitmix64_at((unsigned long long)(3 * i + k)) >> 11) * 0x1p-53) - 1.0);
+        diag_block_apply(a, i, a.U, Mw);
+#pragma unroll
+        for (int k = 0; k < 3; k++) ss = fmaf(a.U[3 * i + k], Mw[3 * i + k], ss);
+    }
+    double tb = pg_block_sum<float>(ss, red1);
+    if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
+    if (!pg_barrier(a.bar, phase)) return fail_out();
+    pg_sum(pbuf(phase - 1), 1, s_sum);
+    __syncthreads();
+    float sc = (float)(1.0 / sqrt(s_sum[0]));
+    for (int j = 0; j < kRitzSteps; j++) {
+        const float *u = a.U + (size_t)(j & 1) * n;
+        float *w = a.U + (size_t)((j + 1) & 1) * n;
+        float *Vj = a.V + (size_t)j * n;
+        // v_j = sc u; w = M^-1 A v_j
+        PG_FOR_OWN_NODES(N, i) {
+            float y0, y1, y2;
+            block_row<float, float, float>(a.slice_ptr, a.row_len, a.col, a.Af, i, u, y0, y1, y2);
+#pragma unroll
+            for (int k = 0; k < 3; k++) Vj[3 * i + k] = u[3 * i + k] * sc;
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                w[3 * i + k] = (__ldg(a.jac + (3 * k) * N + i) * y0 + __ldg(a.jac + (3 * k + 1) * N + i) * y1 +
+                                __ldg(a.jac + (3 * k + 2) * N + i) * y2) * sc;
+        }
+        for (int l = threadIdx.x; l <= j; l += blockDim.x) s_h[l] = 0.0;
+        for (int pass = 0; pass < 2; pass++) {
+            // h = V^T (M w), then w -= V h
+            PG_FOR_OWN_NODES(N, i) diag_block_apply(a, i, w, Mw);
+            pg_dots<float, 3>(a.V, Mw, N, j + 1, false, pbuf(phase));
+            if (!pg_barrier(a.bar, phase)) return fail_out();
+            pg_sum(pbuf(phase - 1), j + 1, s_sum);
+            __syncthreads();
+            for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+                hs[l] = (float)s_sum[l];
+                s_h[l] += s_sum[l];
+            }
+            __syncthreads();
+            pg_axpy<float, 3>(a.V, w, N, j + 1, hs);
+        }
+        // ||w||_M^2 = w . M w
+        ss = 0.0f;
+        PG_FOR_OWN_NODES(N, i) {
+            diag_block_apply(a, i, w, Mw);
+#pragma unroll
+            for (int k = 0; k < 3; k++) ss = fmaf(w[3 * i + k], Mw[3 * i + k], ss);
+        }
+        tb = pg_block_sum<float>(ss, red1);
+        if (threadIdx.x == 0) pbuf(phase)[blockIdx.x] = tb;
+        if (!pg_barrier(a.bar, phase)) return fail_out();
+        pg_sum(pbuf(phase - 1), 1, s_sum);
+        __syncthreads();
+        const double hn = sqrt(fmax(s_sum[0], 0.0));
+        if (lead) {
+            for (int l = 0; l <= j; l++) a.H[(size_t)j * K1 + l] = s_h[l];
+            a.H[(size_t)j * K1 + j + 1] = hn;
+        }
+        if (!(hn > 0.0)) return;
+        sc = (float)(1.0 / hn);
+    }
+}
+
+// y = p(M^-1 A) M^-1 x (FP64 vectors, FP32 A and directions), one cooperative launch
+__global__ void __launch_bounds__(kPgThreads) k_acheb_apply(PgArgs<double> a, const double *x, double *y,
+                                                            unsigned *status) {
+    unsigned phase = 0u;
+    if (!pg_cheb3<double>(a, x, y, false, phase) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 8u);
+}
+
 // y = p(M^-1 S^) M^-1 x (FP64, one cooperative launch); status 8 on a barrier timeout
 template <typename V>
 __global__ void __launch_bounds__(kPgThreads) k_cheb_apply(ChebArgs<double, V> ch, const double *x, double *y,
@@ -1725,12 +1959,16 @@ struct Level {
     int pg_grid = 0, pg_grid16 = 0;
     int pg_gridc = 0, pg_grid16c = 0;  // S-level with the Chebyshev preconditioner
     int pg_grid_sh = 0, pg_grid_shc = 0;  // GMRES on the explicit S^ (SIMPLE), diag / Chebyshev
+    // A-level (kind 0): the A-Chebyshev polynomial's buffers, zc and r [3N] of
+    // T, then d0 and d1 [3N] of float
+    unsigned char *ach = nullptr;
 };
 
 }  // namespace
 
 struct Workspace {
     int m_outer = 0, m_a = 0, m_s = 0, prec = -1, a_amg = 0;
+    int a_cheb = 0;  // degree of the A-Chebyshev polynomial of the current solve (0: block-Jacobi)
     Level<double> outer;
     Level<double> a64, s64;
     Level<float> a32, s32;
@@ -1809,26 +2047,27 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
         // every grid that can run it (its own and the S-solve's)
         const int64_t nodes = kind == 0 ? n / 3 : n;
         L.z2 = (T *)walloc(c, w, sizeof(T) * (size_t)n);
+        if (kind == 0) L.ach = (unsigned char *)walloc(c, w, (size_t)n * (2 * sizeof(T) + 2 * sizeof(float)));
         L.bar = (unsigned *)walloc(c, w, sizeof(unsigned) * kBarWords);
         const int64_t need = std::max<int64_t>(1, (nodes + 31) / 32);  // no block without a slice
         int occ = 0, occ16 = 0;
         if (kind == 0)
-            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_a<T, false>, kPgThreads, 0));
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_a<T, false, false>, kPgThreads, 0));
         else
-            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_s<T, false, false, false>, kPgThreads, 0));
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_s<T, false, false, false, false>, kPgThreads, 0));
         occ16 = occ;
         if constexpr (std::is_same<T, float>::value) {
             if (kind == 0)
-                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_a<float, true>, kPgThreads, 0));
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_a<float, true, false>, kPgThreads, 0));
             else
-                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_s<float, true, false, false>, kPgThreads, 0));
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, k_gmres_s<float, true, false, false, false>, kPgThreads, 0));
         }
         int occc = occ, occ16c = occ16;
         if (kind == 1) {
-            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occc, k_gmres_s<T, false, true, false>, kPgThreads, 0));
+            HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occc, k_gmres_s<T, false, true, false, false>, kPgThreads, 0));
             occ16c = occc;
             if constexpr (std::is_same<T, float>::value)
-                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16c, k_gmres_s<float, true, true, false>, kPgThreads, 0));
+                HYEL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16c, k_gmres_s<float, true, true, false, false>, kPgThreads, 0));
         }
         if (occ < 1 || occ16 < 1 || occc < 1 || occ16c < 1) fail(HYEL_ECUDA, "persistent solve kernel does not fit on an SM");
         L.pg_grid = (int)std::min<int64_t>((int64_t)occ * c.num_sms, need);
@@ -1901,8 +2140,10 @@ void check_params(const hyel_solver_params &p) {
     if (p.precision != HYEL_PREC_FP64 && p.precision != HYEL_PREC_FP32 && p.precision != HYEL_PREC_BF16S)
         fail(HYEL_EINVAL, "solver params: bad precision");
     if (p.check_every < 1) fail(HYEL_EINVAL, "solver params: check_every must be >= 1");
-    if (p.a_precond != HYEL_APREC_BJACOBI && p.a_precond != HYEL_APREC_AMG)
+    if (p.a_precond != HYEL_APREC_BJACOBI && p.a_precond != HYEL_APREC_AMG && p.a_precond != HYEL_APREC_CHEB)
         fail(HYEL_EINVAL, "solver params: bad a_precond");
+    if (p.a_precond == HYEL_APREC_CHEB && (p.a_cheb_degree < 1 || p.a_cheb_degree > kChebMaxDegree))
+        fail(HYEL_EINVAL, "solver params: a_cheb_degree must be in [1, 16]");
     if (p.s_precond != HYEL_SPREC_JACOBI && p.s_precond != HYEL_SPREC_CHEB)
         fail(HYEL_EINVAL, "solver params: bad s_precond");
     if (p.block_precond < HYEL_BLOCK_LDU || p.block_precond > HYEL_BLOCK_SIMPLE)
@@ -1916,8 +2157,8 @@ void check_params(const hyel_solver_params &p) {
             fail(HYEL_EINVAL, "solver params: the CG inner solve needs an A-level restart of at least 2");
     }
     if (p.s_precond == HYEL_SPREC_CHEB) {
-        if (p.a_precond != HYEL_APREC_BJACOBI)
-            fail(HYEL_EINVAL, "solver params: the Chebyshev S-preconditioner needs block-Jacobi A-solves");
+        if (p.a_precond == HYEL_APREC_AMG)
+            fail(HYEL_EINVAL, "solver params: the Chebyshev S-preconditioner needs persistent A-solves (not multigrid)");
         check_cheb(p.s_cheb_degree, p.s_cheb_ratio);
     }
 }
@@ -2039,7 +2280,7 @@ PgArgs<T> pg_args(Ctx &c, Workspace &w, LevelState *st, const hyel_krylov_level 
     g.eta2 = P.rtol >= kPgLoose<T> ? kPgEta2<T> : 0.5;
     h16 = false;
     if constexpr (std::is_same<T, float>::value) {
-        h16 = w.prec == HYEL_PREC_BF16S;
+        h16 = w.prec == HYEL_PREC_BF16S && w.a_cheb == 0;
         a.Am = h16 ? nullptr : M.Amf;
     } else {
         a.Am = M.Ams;
@@ -2048,6 +2289,25 @@ PgArgs<T> pg_args(Ctx &c, Workspace &w, LevelState *st, const hyel_krylov_level 
     // A~ values + column indices + row metadata, and the passes over 3N-vectors
     g.it_fixed = (double)msh.nnzb * ((h16 ? 22.0 : 9.0 * sizeof(T)) + 4.0) + 4.0 * (msh.N + 1);
     g.it_unit = 3.0 * msh.N * sizeof(T);
+    a.ac = AChArgs<T>{};
+    if (w.a_cheb > 0) {
+        const int64_t n = 3 * msh.N;
+        a.ac.Af = M.Af;
+        if constexpr (std::is_same<T, double>::value)
+            a.ac.A = M.As;
+        else
+            a.ac.A = M.Af;
+        a.ac.bounds = c.ach->bounds;
+        a.ac.degree = w.a_cheb;
+        a.ac.zc = reinterpret_cast<T *>(L.ach);
+        a.ac.r = a.ac.zc + n;
+        a.ac.d0 = reinterpret_cast<float *>(L.ach + 2 * n * sizeof(T));
+        a.ac.d1 = a.ac.d0 + n;
+        // per application: degree - 1 FP32 A products, M^-1 and the passes
+        const int d = w.a_cheb;
+        g.it_fixed += (d - 1) * ((double)msh.nnzb * 40.0 + 4.0 * (msh.N + 1) + 9.0 * msh.N * sizeof(T)) +
+                      (3.0 + 7.0 * (d - 1)) * n * sizeof(T);
+    }
     return a;
 }
 
@@ -2104,13 +2364,18 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_GMRES_A, &ev);
     bool launched = false;
+    if (w.a_cheb > 0) {
+        cfg.gridDim = dim3((unsigned)resident_grid(c, (const void *)k_gmres_a<T, false, true>));
+        HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_a<T, false, true>, a));
+        launched = true;
+    }
     if constexpr (std::is_same<T, float>::value) {
-        if (h16) {
-            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_a<float, true>, a));
+        if (h16 && !launched) {
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_a<float, true, false>, a));
             launched = true;
         }
     }
-    if (!launched) HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_a<T, false>, a));
+    if (!launched) HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_a<T, false, false>, a));
     count_launch();
     prof_end(c, HYEL_K_GMRES_A, ev, 0.0);  // bytes are added from the level states after the solve
 }
@@ -2242,8 +2507,13 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
                       (3.0 + 6.0 * (d - 1)) * (double)N * sizeof(T);
     }
     HYEL_CK(cudaMemsetAsync(La.bar, 0, kBarWords * sizeof(unsigned), c.stream));
-    const void *kicg = cheb ? (const void *)k_gmres_s<T, false, true, true> : (const void *)k_gmres_s<T, false, false, true>;
-    cudaLaunchConfig_t cfg = coop_config(c, icg ? resident_grid(c, kicg)
+    const bool ach = w.a_cheb > 0;
+    const void *kicg = cheb ? (const void *)k_gmres_s<T, false, true, true, false>
+                            : (const void *)k_gmres_s<T, false, false, true, false>;
+    const void *kach = cheb ? (const void *)k_gmres_s<T, false, true, false, true>
+                            : (const void *)k_gmres_s<T, false, false, false, true>;
+    cudaLaunchConfig_t cfg = coop_config(c, icg   ? resident_grid(c, kicg)
+                                         : ach  ? resident_grid(c, kach)
                                          : cheb ? (h16 ? Ls.pg_grid16c : Ls.pg_gridc)
                                                 : (h16 ? Ls.pg_grid16 : Ls.pg_grid));
     cudaLaunchAttribute at[1];
@@ -2257,25 +2527,31 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
     if (icg) {
         // the inner solve reads A_sym in the level's precision (no BF16 copy)
         if (cheb)
-            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true, true>, sg, a));
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true, true, false>, sg, a));
         else
-            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false, true>, sg, a));
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false, true, false>, sg, a));
+        launched = true;
+    } else if (ach) {
+        if (cheb)
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true, false, true>, sg, a));
+        else
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false, false, true>, sg, a));
         launched = true;
     }
     if constexpr (std::is_same<T, float>::value) {
         if (h16 && !launched) {
             if (cheb)
-                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, true, false>, sg, a));
+                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, true, false, false>, sg, a));
             else
-                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, false, false>, sg, a));
+                HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<float, true, false, false, false>, sg, a));
             launched = true;
         }
     }
     if (!launched) {
         if (cheb)
-            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true, false>, sg, a));
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, true, false, false>, sg, a));
         else
-            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false, false>, sg, a));
+            HYEL_CK(cudaLaunchKernelEx(&cfg, k_gmres_s<T, false, false, false, false>, sg, a));
     }
     count_launch();
     prof_end(c, HYEL_K_GMRES_S, ev, 0.0);
@@ -2531,6 +2807,12 @@ void prepare(Ctx &c, const hyel_solver_params &p) {
     if (p.s_precond == HYEL_SPREC_CHEB || p.block_precond == HYEL_BLOCK_SIMPLE) shat_setup(c);
     if (p.block_precond == HYEL_BLOCK_SIMPLE && p.precision == HYEL_PREC_FP64) shat_ensure64(c);
     if (p.inner_solver == HYEL_INNER_CG_SYM) asym_setup(c);
+    if (p.a_precond == HYEL_APREC_CHEB) acheb_setup(c);
+}
+
+// The parameters a recording or launch reads from the workspace
+void bind_params(Workspace &w, const hyel_solver_params &p) {
+    w.a_cheb = p.a_precond == HYEL_APREC_CHEB ? p.a_cheb_degree : 0;
 }
 
 // Kernel executions of the last solve from the level statistics.
@@ -2551,6 +2833,7 @@ void solve_nested(Ctx &c, const hyel_solver_params &p, const double *rhs, double
     auto t0 = std::chrono::steady_clock::now();
     prepare(c, p);
     Workspace &w = workspace(c, p);
+    bind_params(w, p);
     if (p.graph) ensure_graph(c, w, p);
     HYEL_CK(cudaStreamSynchronize(c.stream));
     const double ms_setup = 1e3 * seconds_since(t0);
@@ -2749,6 +3032,103 @@ void shat_setup(Ctx &c) {
     c.mat.shat_ready = true;
 }
 
+void acheb_free(Ctx &c) {
+    delete c.ach;  // device arrays belong to the context's allocation list
+    c.ach = nullptr;
+}
+
+void acheb_setup(Ctx &c) {
+    solve_setup(c);
+    if (c.mat.acheb_ready) return;
+    const DeviceMesh &m = c.mesh;
+    const int64_t N = m.N, n = 3 * N;
+    const int K1 = kRitzSteps + 1;
+    if (!c.ach) {
+        AChebState *h = new AChebState();
+        c.ach = h;
+        const size_t gmax = (size_t)(2048 / kPgThreads) * c.num_sms;
+        h->bounds = dalloc_n<double>(c, 2);
+        h->V = dalloc_n<float>(c, (size_t)K1 * n);
+        h->U = dalloc_n<float>(c, 3 * (size_t)n);
+        h->H = dalloc_n<double>(c, (size_t)K1 * kRitzSteps);
+        h->partial = dalloc_n<double>(c, 2 * gmax * K1);
+        h->bar = (unsigned *)dalloc(c, kBarWords * sizeof(unsigned));
+        h->work = dalloc_n<double>(c, (size_t)n);
+        h->dwork = dalloc_n<float>(c, 2 * (size_t)n);
+    }
+    AChebState &h = *c.ach;
+    AArnArgs a;
+    a.slice_ptr = m.slice_ptr;
+    a.row_len = m.row_len;
+    a.col = m.col;
+    a.diag_slot = m.diag_slot;
+    a.Af = c.mat.Af;
+    a.jac = c.mat.jac32;
+    a.V = h.V;
+    a.U = h.U;
+    a.H = h.H;
+    a.partial = h.partial;
+    a.bar = h.bar;
+    a.N = N;
+    HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    HYEL_CK(cudaMemsetAsync(h.H, 0, sizeof(double) * K1 * kRitzSteps, c.stream));
+    void *args[] = {&a};
+    coop_launch(c, coop_grid(c, (const void *)k_a_arnoldi), (const void *)k_a_arnoldi, args);
+    std::vector<double> H((size_t)K1 * kRitzSteps);
+    HYEL_CK(cudaMemcpyAsync(H.data(), h.H, sizeof(double) * H.size(), cudaMemcpyDeviceToHost, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    if (!std::isfinite(H[0])) fail(HYEL_ENAN, "a_cheb: Arnoldi on M^-1 A met NaN/Inf (or a grid barrier timed out)");
+    int k = kRitzSteps;
+    for (int j = 0; j < kRitzSteps; j++) {
+        for (int l = 0; l <= j + 1; l++)
+            if (!std::isfinite(H[(size_t)j * K1 + l])) fail(HYEL_ENAN, "a_cheb: Arnoldi on M^-1 A met NaN/Inf");
+        if (!(H[(size_t)j * K1 + j + 1] > 0.0)) {
+            k = j + 1;
+            break;
+        }
+    }
+    std::vector<double> S((size_t)k * k), ev;
+    for (int r = 0; r < k; r++)
+        for (int q = 0; q < k; q++) S[r * k + q] = 0.5 * (H[(size_t)q * K1 + r] + H[(size_t)r * K1 + q]);
+    sym_eigenvalues(S, k, ev);
+    if (!(ev.back() > 0.0)) fail(HYEL_ENAN, "a_cheb: M^-1 A has no positive Ritz value");
+    double b[2] = {ev.front() / kRitzLow, kRitzSafety * ev.back()};
+    h.h_bounds[0] = b[0];
+    h.h_bounds[1] = b[1];
+    HYEL_CK(cudaMemcpy(h.bounds, b, sizeof b, cudaMemcpyHostToDevice));
+    c.mat.acheb_ready = true;
+}
+
+void acheb_apply(Ctx &c, int degree, const double *x, double *y) {
+    if (degree < 1 || degree > kChebMaxDegree) fail(HYEL_EINVAL, "a_cheb_apply: degree must be in [1, 16]");
+    if (!c.ach || !c.mat.acheb_ready) fail(HYEL_ESTATE, "a_cheb_apply: no interval for the current assembly");
+    AChebState &h = *c.ach;
+    const DeviceMesh &m = c.mesh;
+    const int64_t n = 3 * m.N;
+    PgArgs<double> a{};
+    a.slice_ptr = m.slice_ptr;
+    a.row_len = m.row_len;
+    a.col = m.col;
+    a.jac = c.mat.jac64;
+    a.ac.Af = c.mat.Af;
+    a.ac.A = c.mat.As;
+    a.ac.bounds = h.bounds;
+    a.ac.degree = degree;
+    a.ac.r = h.work;
+    a.ac.d0 = h.dwork;
+    a.ac.d1 = h.dwork + n;
+    a.g.N = m.N;
+    a.g.bar = h.bar;
+    unsigned *status = c.err;
+    HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
+    void *args[] = {&a, (void *)&x, (void *)&y, &status};
+    coop_launch(c, coop_grid(c, (const void *)k_acheb_apply), (const void *)k_acheb_apply, args);
+    HYEL_CK(cudaMemcpyAsync(c.h_err, c.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+    HYEL_CK(cudaStreamSynchronize(c.stream));
+    if (*c.h_err & 8u) fail(HYEL_ECUDA, "a_cheb_apply: a grid barrier timed out");
+}
+
 void shat_cheb_apply(Ctx &c, int matrix, int degree, double ratio, const double *x, double *y) {
     check_cheb(degree, ratio);
     if (matrix != HYEL_MAT_SCALED64 && matrix != HYEL_MAT_SCALED32)
@@ -2781,6 +3161,7 @@ void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y
     if (!c.mat.assembled) fail(HYEL_ESTATE, "schur_apply: nothing assembled");
     prepare(c, p);
     Workspace &w = workspace(c, p);
+    bind_params(w, p);
     const int64_t N = c.mesh.N;
     HYEL_CK(cudaMemsetAsync(w.states, 0, sizeof(LevelState) * 5, c.stream));
     Rec R;
@@ -2813,6 +3194,7 @@ void block_precond_apply(Ctx &c, const hyel_solver_params &p, const double *r, d
     if (!c.mat.assembled) fail(HYEL_ESTATE, "block_precond_apply: nothing assembled");
     prepare(c, p);
     Workspace &w = workspace(c, p);
+    bind_params(w, p);
     const int64_t N = c.mesh.N, n = 4 * N;
     HYEL_CK(cudaMemsetAsync(w.states, 0, sizeof(LevelState) * 5, c.stream));
     Rec R;

@@ -529,6 +529,7 @@ void solve_setup(Ctx &c) {
     c.mat.shat_ready = false;
     c.mat.shat64_ready = false;
     c.mat.asym_ready = false;
+    c.mat.acheb_ready = false;
 }
 
 namespace {

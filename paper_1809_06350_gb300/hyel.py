@@ -20,7 +20,7 @@ HYEL_EINVAL, HYEL_ECUDA, HYEL_ENOMEM, HYEL_ENOCONV = -1, -2, -3, -4
 HYEL_EBREAKDOWN, HYEL_ENAN, HYEL_EINVERTED, HYEL_ESINGULAR, HYEL_ESTATE = -5, -6, -7, -8, -9
 HYEL_VOL_GIBBS, HYEL_VOL_INCOMPRESSIBLE = 0, 1
 HYEL_PREC_FP64, HYEL_PREC_FP32, HYEL_PREC_BF16S = 0, 1, 2
-HYEL_APREC_BJACOBI, HYEL_APREC_AMG = 0, 1
+HYEL_APREC_BJACOBI, HYEL_APREC_AMG, HYEL_APREC_CHEB = 0, 1, 2
 HYEL_SPREC_JACOBI, HYEL_SPREC_CHEB = 0, 1
 HYEL_BLOCK_LDU, HYEL_BLOCK_DU, HYEL_BLOCK_D, HYEL_BLOCK_SIMPLE = 0, 1, 2, 3
 HYEL_INNER_GMRES, HYEL_INNER_CG_SYM = 0, 1
@@ -39,7 +39,8 @@ EXPORTS = [
     "hyel_schur_apply", "hyel_solve_nested", "hyel_newton_step", "hyel_profile", "hyel_profile_read",
     "hyel_launch_count", "hyel_residual_norm_static", "hyel_update_material",
     "hyel_solve_nested_transpose", "hyel_param_sensitivity", "hyel_adjoint_step",
-    "hyel_schur_hat_setup", "hyel_schur_hat_cheb", "hyel_block_precond_apply",
+    "hyel_schur_hat_setup", "hyel_schur_hat_cheb", "hyel_block_precond_apply", "hyel_a_cheb_setup",
+    "hyel_a_cheb_apply",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -77,7 +78,7 @@ class HyelSolverParams(C.Structure):
                 ("inner", HyelKrylovLevel), ("precision", C.c_int32), ("check_every", C.c_int32),
                 ("graph", C.c_int32), ("a_precond", C.c_int32), ("s_precond", C.c_int32),
                 ("s_cheb_degree", C.c_int32), ("s_cheb_ratio", C.c_double), ("block_precond", C.c_int32),
-                ("inner_solver", C.c_int32)]
+                ("inner_solver", C.c_int32), ("a_cheb_degree", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class HyelSolveStats(C.Structure):
@@ -147,6 +148,8 @@ def lib():
                                             C.POINTER(HyelSolveStats)]),
             "hyel_schur_hat_setup": (C.c_int, [vp, _dp, C.POINTER(C.c_int64), C.c_int]),
             "hyel_schur_hat_cheb": (C.c_int, [vp, C.c_int, C.c_int32, C.c_double, vp, vp]),
+            "hyel_a_cheb_setup": (C.c_int, [vp, _dp]),
+            "hyel_a_cheb_apply": (C.c_int, [vp, C.c_int32, vp, vp]),
             "hyel_block_precond_apply": (C.c_int, [vp, C.POINTER(HyelSolverParams), vp, vp,
                                                    C.POINTER(HyelSolveStats)]),
         }
@@ -250,6 +253,17 @@ def hyel_schur_hat_cheb(ctx, degree, ratio, x_ptr, y_ptr, matrix=HYEL_MAT_SCALED
                                           C.c_void_p(y_ptr)))
 
 
+def hyel_a_cheb_setup(ctx):
+    """The A-Chebyshev interval (lmin, lmax) of the current scaled system."""
+    b = (C.c_double * 2)()
+    _check(ctx, lib().hyel_a_cheb_setup(ctx, b))
+    return b[0], b[1]
+
+
+def hyel_a_cheb_apply(ctx, degree, x_ptr, y_ptr):
+    _check(ctx, lib().hyel_a_cheb_apply(ctx, int(degree), C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
 def hyel_block_precond_apply(ctx, params, r_ptr, z_ptr):
     st = HyelSolveStats()
     _check(ctx, lib().hyel_block_precond_apply(ctx, C.byref(params), C.c_void_p(r_ptr), C.c_void_p(z_ptr),
@@ -340,18 +354,19 @@ def level(rtol, maxit, restart, atol=1e-50):
 def solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=HYEL_PREC_FP64, outer=(200, 200),
                   a=(500, 500), s=(200, 200), inner=(500, 500), check_every=4, inner_rtol=None, graph=1,
                   a_precond=0, s_precond=0, s_cheb_degree=4, s_cheb_ratio=0.0, block_precond=0,
-                  inner_solver=0):
+                  inner_solver=0, a_cheb_degree=8):
     """Solver controls with the paper's defaults (§5: FGMRES(200), A: GMRES(500),
     S: GMRES(200), inner GMRES(500), absolute tolerances 1e-50). a_precond:
-    HYEL_APREC_BJACOBI (default) or HYEL_APREC_AMG; s_precond: HYEL_SPREC_JACOBI
+    HYEL_APREC_BJACOBI (default), HYEL_APREC_AMG or HYEL_APREC_CHEB; s_precond: HYEL_SPREC_JACOBI
     (default) or HYEL_SPREC_CHEB (degree s_cheb_degree on [lmin, lmax] from Ritz
     estimates, or on [lmax / s_cheb_ratio, lmax] when s_cheb_ratio > 1);
     block_precond: HYEL_BLOCK_LDU (Algorithm 1, default), _DU, _D or _SIMPLE;
-    inner_solver: HYEL_INNER_GMRES (default) or HYEL_INNER_CG_SYM (CG on (A + A^T)/2)."""
+    inner_solver: HYEL_INNER_GMRES (default) or HYEL_INNER_CG_SYM (CG on (A + A^T)/2);
+    a_cheb_degree: the degree of the HYEL_APREC_CHEB polynomial."""
     ir = sub_rtol if inner_rtol is None else inner_rtol
     return HyelSolverParams(level(outer_rtol, *outer), level(sub_rtol, *a), level(sub_rtol, *s),
                             level(ir, *inner), precision, check_every, graph, a_precond, s_precond,
-                            s_cheb_degree, s_cheb_ratio, block_precond, inner_solver)
+                            s_cheb_degree, s_cheb_ratio, block_precond, inner_solver, a_cheb_degree, 0)
 
 
 def time_params(dt=1e-3, t_n=0.0, rho_inf=0.5, tol_r=1e-6, tol_a=1e-6, l_max=20, rhs_literal=0):
