@@ -187,7 +187,6 @@ struct SchurHat {
     double *arn_H = nullptr;       // [(steps + 1) steps]
     double *partial = nullptr;     // [2][steps + 1][grid]
     unsigned *bar = nullptr;       // barrier words
-    int grid = 0;                  // cooperative grid of the scratch kernels
 };
 
 struct Ctx {

@@ -185,8 +185,7 @@ void shat_build(Ctx &c) {
     h->v32 = dalloc_n<float>(c, (size_t)nslots);
     h->bounds = dalloc_n<double>(c, 2);
     h->work = dalloc_n<double>(c, 3 * (size_t)N);
-    h->bar = (unsigned *)dalloc(c, 96 * sizeof(unsigned));
-    h->grid = 0;  // set with the partials by the solver on first use
+    h->bar = (unsigned *)dalloc(c, 96 * sizeof(unsigned));  // the grid barrier's three 128-byte lines
 }
 
 }  // namespace

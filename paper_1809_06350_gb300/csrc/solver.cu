@@ -525,6 +525,9 @@ struct GmArgs {
     int64_t N;                 // nodes
     const T *b;
     T *x, *V, *U0, *U1;
+    // flexible form: the operator stores P^-1 v_j in column j of Zb and the
+    // solution update reads Zb instead of V (x += Z y); nullptr: x += P^-1 (V y)
+    T *Zb = nullptr;
     double *H;                 // rotated Hessenberg columns (written by block 0)
     double *partial;           // 2 x [m + 1][grid], by barrier parity
     unsigned *bar;             // barrier words (arrivals, release, abort), shared by nested levels
@@ -980,7 +983,7 @@ __device__ bool pg_gmres(const GmArgs<T> &a, unsigned &phase, Op &&op, XUpd &&xu
         PG_FOR_OWN_NODES(N, i)
 #pragma unroll
             for (int r = 0; r < NC; r++) Vj[NC * i + r] = uin[NC * i + r] * s;
-        if (!op(uin, s, uout, phase)) return abort_out();
+        if (!op(uin, s, uout, phase, j)) return abort_out();
         pg_dots<T, NC>(a.V, uout, N, j + 1, true, pbuf(phase));
         if (!pg_barrier(a.bar, phase)) return abort_out();
         pg_sum(pbuf(phase - 1), j + 2, s_col);  // h1, and ||w||^2 in s_col[j + 1]
@@ -1121,13 +1124,14 @@ __device__ bool pg_gmres(const GmArgs<T> &a, unsigned &phase, Op &&op, XUpd &&xu
             __syncthreads();
             for (int l = threadIdx.x; l < k; l += blockDim.x) hs[l] = (T)s_tmp[l];
             __syncthreads();
-            // x += M^-1 V y
+            // x += M^-1 V y (or x += Z y in the flexible form)
+            const T *XB = a.Zb ? a.Zb : a.V;
             PG_FOR_OWN_NODES(N, i) {
                 T u[NC];
 #pragma unroll
                 for (int r = 0; r < NC; r++) u[r] = 0;
                 for (int l = 0; l < k; l++) {
-                    const T *v = a.V + (int64_t)l * n + NC * i;
+                    const T *v = XB + (int64_t)l * n + NC * i;
 #pragma unroll
                     for (int r = 0; r < NC; r++) u[r] = fma(v[r], hs[l], u[r]);
                 }
@@ -1286,7 +1290,7 @@ __device__ bool pg_cheb3(const PgArgs<T> &a, const T *v, T *z, bool add, unsigne
 template <typename T, bool H16, bool ACH = false>
 __device__ bool pg_gmres_a(const PgArgs<T> &a, unsigned &phase) {
     const int64_t N = a.g.N;
-    auto op = [&](const T *u, T sc, T *w, unsigned &ph) {
+    auto op = [&](const T *u, T sc, T *w, unsigned &ph, int) {
         if constexpr (ACH) {
             if (!pg_cheb3<T>(a, u, a.ac.zc, false, ph)) return false;
             PG_FOR_OWN_NODES(N, i) {
@@ -1511,9 +1515,14 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
         else
             return __ldg(s.shat + c) * u[c];
     };
-    auto op = [&](const T *u, T sc, T *w, unsigned &ph) {
+    auto op = [&](const T *u, T sc, T *w, unsigned &ph, int j) {
         if constexpr (CHEB) {
             if (!pg_cheb(s.ch, N, u, (T)1, s.zc, false, s.g.bar, ph)) return false;
+            if (s.g.Zb) {
+                // Z_j = P^-1 v_j = sc P^-1 u (row-local; x = Z y at the end of a cycle)
+                T *Zj = s.g.Zb + (int64_t)j * N;
+                PG_FOR_OWN_NODES(N, i) Zj[i] = s.zc[i] * sc;
+            }
         }
         PG_FOR_OWN_NODES(N, i) {
             const int t = (int)(i & 31);
@@ -1556,10 +1565,16 @@ __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_s(SgArgs<T> s, PgArgs<T
         return true;
     };
     if constexpr (CHEB) {
-        // V y goes to the Chebyshev residual buffer, then x += P^-1 (V y)
-        auto xupd = [&](int64_t i, const T (&u)[1]) { s.ch.r[i] = u[0]; };
-        auto xend = [&](unsigned &ph) { return pg_cheb(s.ch, N, s.ch.r, (T)1, s.g.x, true, s.g.bar, ph); };
-        pg_gmres<T, 1>(s.g, phase, op, xupd, xend);
+        if (s.g.Zb) {
+            // flexible form: x += Z y
+            auto xupd = [&](int64_t i, const T (&u)[1]) { s.g.x[i] += u[0]; };
+            pg_gmres<T, 1>(s.g, phase, op, xupd);
+        } else {
+            // V y goes to the Chebyshev residual buffer, then x += P^-1 (V y)
+            auto xupd = [&](int64_t i, const T (&u)[1]) { s.ch.r[i] = u[0]; };
+            auto xend = [&](unsigned &ph) { return pg_cheb(s.ch, N, s.ch.r, (T)1, s.g.x, true, s.g.bar, ph); };
+            pg_gmres<T, 1>(s.g, phase, op, xupd, xend);
+        }
     } else {
         auto xupd = [&](int64_t i, const T (&u)[1]) { s.g.x[i] += __ldg(s.shat + i) * u[0]; };
         pg_gmres<T, 1>(s.g, phase, op, xupd);
@@ -1584,7 +1599,7 @@ template <typename T, bool CHEB>
 __global__ void __launch_bounds__(kPgThreads, 2) k_gmres_shat(ShArgs<T> s) {
     unsigned phase = 0u;  // the barrier words are cleared before every launch
     const int64_t N = s.g.N;
-    auto op = [&](const T *u, T sc, T *w, unsigned &ph) {
+    auto op = [&](const T *u, T sc, T *w, unsigned &ph, int) {
         if constexpr (CHEB) {
             if (!pg_cheb(s.ch, N, u, (T)1, s.zc, false, s.g.bar, ph)) return false;
         }
@@ -2030,7 +2045,7 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
     L.kind = kind;
     L.grid = (int)std::max<int64_t>(1, std::min<int64_t>(2 * c.num_sms, (n + 4 * kThreads - 1) / (4 * kThreads)));
     L.V = (T *)walloc(c, w, sizeof(T) * (size_t)(m + 1) * n);
-    if (kind == 2) L.Z = (T *)walloc(c, w, sizeof(T) * (size_t)m * n);
+    if (kind == 2 || kind == 1) L.Z = (T *)walloc(c, w, sizeof(T) * (size_t)m * n);  // kind 1: the flexible S-level
     L.z = (T *)walloc(c, w, sizeof(T) * (size_t)n);
     L.H = (double *)walloc(c, w, sizeof(double) * (size_t)(m + 1) * m);
     L.cs = (double *)walloc(c, w, sizeof(double) * m);
@@ -2494,6 +2509,7 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
     g.rtol = p.s.rtol;
     g.atol = p.s.atol;
     g.eta2 = p.s.rtol >= kPgLoose<T> ? kPgEta2<T> : 0.5;
+    g.Zb = cheb ? Ls.Z : nullptr;  // Chebyshev: flexible form, no polynomial at the end of a cycle
     // one S-iteration outside its inner A-solve: B, C, D values and column
     // indices (twice), and the vector passes over [N]-vectors
     g.it_fixed = (double)msh.nnzb * (7.0 * sizeof(T) + 8.0) + 4.0 * (N + 1);
