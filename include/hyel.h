@@ -446,7 +446,7 @@ int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solv
  * launch per S-solve, its inner A-solves included); their algorithmic bytes
  * are counted on the device per iteration (the operator's values and indices
  * plus the passes over the Krylov vectors) and added when the solve returns.
- * HYEL_K_SCHUR_HAT times the numeric S^ and its power-method bound together. */
+ * HYEL_K_SCHUR_HAT times the numeric S^ and its Ritz interval together. */
 enum { HYEL_K_SPMV_A64 = 0, HYEL_K_SPMV_A32 = 1, HYEL_K_SPMV_FULL64 = 2,
        HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_SPMV_A16 = 5, HYEL_K_GMRES_A = 6,
        HYEL_K_GMRES_S = 7, HYEL_K_SCHUR_HAT = 8, HYEL_K_NCLASSES = 9 };
