@@ -138,12 +138,14 @@ typedef struct {
 } hyel_krylov_level;
 
 /* Nested solver (§4.4): outer FGMRES on the scaled system with the SCR
- * preconditioner of Algorithm 1; `a` controls the two intermediate A-solves
- * (eq. seg_sol_int_disp, seg_sol_disp), `s` the Schur solve (eq. seg_sol_pres)
- * right-preconditioned by point-Jacobi on diag(S^), S^ = D - C diag(A)^-1 B,
- * and `inner` the A-solve inside the matrix-free S product (Algorithm 2,
- * eq. S_inner_A_eqn). A-solves are right-preconditioned by the inverses of the
- * 3x3 node-diagonal blocks of A.
+ * preconditioner of Algorithm 1 (or the block variant block_precond selects);
+ * `a` controls the two intermediate A-solves (eq. seg_sol_int_disp,
+ * seg_sol_disp), `s` the Schur solve (eq. seg_sol_pres), right-preconditioned
+ * as s_precond selects (point-Jacobi on diag(S^), S^ = D - C diag(A)^-1 B, by
+ * default), and `inner` the A-solve inside the matrix-free S product
+ * (Algorithm 2, eq. S_inner_A_eqn). A-solves are right-preconditioned as
+ * a_precond selects (the inverses of the 3x3 node-diagonal blocks of A by
+ * default).
  * graph = 1 (default): the whole nested solve is one CUDA graph whose Krylov
  * loops are device-driven `while` conditional nodes (no host round trip until
  * the solve ends); the graph is built once per context and parameter set.
@@ -183,9 +185,10 @@ enum { HYEL_APREC_BJACOBI = 0, HYEL_APREC_AMG = 1, HYEL_APREC_CHEB = 2 };
  *   s_cheb_ratio = 0 uses that lmin (clamped to [lmax / 1000, lmax / 1.5]),
  *   s_cheb_ratio > 1 fixes lmin = lmax / s_cheb_ratio. Rebuilt after every
  *   scaling of a new assembly. A fixed linear operator, applied inside the
- *   persistent S-solve (one grid barrier per degree); the paper's own choice
- *   is algebraic multigrid built from S^ (§5). Needs a_precond =
- *   HYEL_APREC_BJACOBI. */
+ *   persistent S-solve (one grid barrier per degree), which keeps P^-1 v_j
+ *   for every Krylov vector (flexible form: x = Z y at the end of a cycle);
+ *   the paper's own choice is algebraic multigrid built from S^ (§5). Not
+ *   with a_precond = HYEL_APREC_AMG. */
 enum { HYEL_SPREC_JACOBI = 0, HYEL_SPREC_CHEB = 1 };
 /* The block preconditioner of the outer FGMRES (§4.2–4.4; the factorization
  * of eq. a_ldu_block_factorization):
