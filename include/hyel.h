@@ -400,7 +400,9 @@ int hyel_solve_nested(hyel_ctx *ctx, const hyel_solver_params *params,
 /* One generalized-alpha time step (§3.3): predictor, then up to l_max Newton
  * corrections, each assembling, solving with hyel_solve_nested and updating
  * by eq. NR_smaller_eqn_2 and step 7. state: y_n, ydot_n in, y_{n+1},
- * ydot_{n+1} out (overwritten only on return). */
+ * ydot_{n+1} out (overwritten only on return). With Chebyshev preconditioners
+ * the intervals estimated at the first correction are kept at the later ones
+ * of the same step (S^ and A themselves are rebuilt every time). */
 int hyel_newton_step(hyel_ctx *ctx, const hyel_time_params *tp,
                      const hyel_solver_params *sp, hyel_state *state,
                      hyel_newton_stats *stats);

@@ -206,6 +206,9 @@ struct Ctx {
     Amg *amg = nullptr;
     SchurHat *sh = nullptr;
     AChebState *ach = nullptr;
+    // set by the Newton step after its first correction: the Chebyshev
+    // intervals (S^ and A) estimated at the first iteration are kept
+    bool keep_intervals = false;
     Profile prof;
     size_t bytes_held = 0;
     int num_sms = 152;

@@ -182,6 +182,13 @@ void newton_step(Ctx &c, const hyel_time_params &tp, const hyel_solver_params &s
         }
         hyel_solve_stats ss{};
         auto tsol = std::chrono::steady_clock::now();
+        // after the first correction the Chebyshev intervals of this time
+        // step's first iteration are kept (the tangent moves little)
+        struct KeepIntervals {
+            Ctx &c;
+            KeepIntervals(Ctx &cc, bool on) : c(cc) { c.keep_intervals = on; }
+            ~KeepIntervals() { c.keep_intervals = false; }
+        } keep(c, l > 1);
         try {
             solve_nested(c, sp, rhs, dx, &ss);
         } catch (const Error &e) {

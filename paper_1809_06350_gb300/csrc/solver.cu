@@ -3040,10 +3040,14 @@ void shat_setup(Ctx &c) {
     // numeric (FP32): D, C, column and diag(A) per block slot, B per
     // neighbour slot, positions, rows written; Arnoldi (FP32): S^ and the
     // basis passes per step
+    // (the interval of the first Newton iteration of a time step is kept at
+    // the later ones when keep_intervals is set: the matrix moves little)
+    const bool estimate = !(c.keep_intervals && h.h_bounds[1] > 0.0);
     const double bytes = (double)m.nnzb * (4.0 + 12.0 + 4.0 + 12.0) + (double)m.N * (12.0 + 8.0) +
                          2.0 * (double)h.ncontrib + 4.0 * (double)h.nslots +
-                         kRitzSteps * ((double)h.nnz * 8.0 + (double)m.N * (8.0 + 4.0 * (2 * kRitzSteps + 4)));
-    shat_bounds(c);
+                         (estimate ? kRitzSteps * ((double)h.nnz * 8.0 + (double)m.N * (8.0 + 4.0 * (2 * kRitzSteps + 4)))
+                                   : 0.0);
+    if (estimate) shat_bounds(c);
     prof_end(c, HYEL_K_SCHUR_HAT, ev, bytes);
     c.mat.shat_ready = true;
 }
@@ -3056,6 +3060,10 @@ void acheb_free(Ctx &c) {
 void acheb_setup(Ctx &c) {
     solve_setup(c);
     if (c.mat.acheb_ready) return;
+    if (c.keep_intervals && c.ach && c.ach->h_bounds[1] > 0.0) {
+        c.mat.acheb_ready = true;  // the first Newton iteration's interval
+        return;
+    }
     const DeviceMesh &m = c.mesh;
     const int64_t N = m.N, n = 3 * N;
     const int K1 = kRitzSteps + 1;
