@@ -357,8 +357,8 @@ int hyel_schur_hat_setup(hyel_ctx *ctx, double *bounds_out, int64_t *info, int n
  * vectors. matrix: HYEL_MAT_SCALED64 (FP64 values of S^) or HYEL_MAT_SCALED32
  * (FP32 values, as inside the S-solve, where the polynomial reads S^ in FP32
  * at every precision). x, y: device [N] double, distinct. HYEL_ESTATE before
- * hyel_schur_hat_setup on the current assembly; HYEL_EINVAL for another
- * matrix, degree outside 1..16 or another ratio. Synchronizes. */
+ * hyel_schur_hat_setup on the current assembly; HYEL_EINVAL for aliased x and
+ * y, another matrix, degree outside 1..16 or another ratio. Synchronizes. */
 int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio, const double *x, double *y);
 
 /* y = S x for the scaled system (Algorithm 2: D x - C A^-1 (B x)), the inner
@@ -375,15 +375,15 @@ int hyel_a_cheb_setup(hyel_ctx *ctx, double *bounds_out);
 /* y = p(M^-1 A) M^-1 x, the HYEL_APREC_CHEB polynomial of the given degree
  * (1..16) on the interval of hyel_a_cheb_setup, as inside the A-solves: FP32
  * A values and directions, FP64 residual and result. x, y: device [3N]
- * double, distinct. HYEL_ESTATE before hyel_a_cheb_setup on the current
- * assembly. Synchronizes. */
+ * double, distinct (HYEL_EINVAL otherwise). HYEL_ESTATE before
+ * hyel_a_cheb_setup on the current assembly. Synchronizes. */
 int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y);
 
 /* z = P^-1 r once, P the block preconditioner of params->block_precond on the
  * scaled system (§4.2–4.4), its sub-solves controlled by params (precision,
  * levels, A- and S-preconditioners) exactly as inside hyel_solve_nested.
- * r, z: device [4N] double ([v ; p] ordering). stats: host or NULL (a, s and
- * inner counts). Synchronizes. */
+ * r, z: device [4N] double ([v ; p] ordering), distinct (HYEL_EINVAL
+ * otherwise). stats: host or NULL (a, s and inner counts). Synchronizes. */
 int hyel_block_precond_apply(hyel_ctx *ctx, const hyel_solver_params *params,
                              const double *r, double *z, hyel_solve_stats *stats);
 

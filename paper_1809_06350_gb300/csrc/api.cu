@@ -298,6 +298,7 @@ int hyel_schur_hat_setup(hyel_ctx *ctx, double *bounds_out, int64_t *info, int n
 int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio, const double *x, double *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "schur_hat_cheb: null vector");
+        if (x == y) hyel::fail(HYEL_EINVAL, "schur_hat_cheb: x and y must be distinct");
         hyel::shat_cheb_apply(c, matrix, degree, ratio, x, y);
     });
 }
@@ -323,6 +324,7 @@ int hyel_a_cheb_setup(hyel_ctx *ctx, double *bounds_out) {
 int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "a_cheb_apply: null vector");
+        if (x == y) hyel::fail(HYEL_EINVAL, "a_cheb_apply: x and y must be distinct");
         hyel::acheb_apply(c, degree, x, y);
     });
 }
@@ -331,6 +333,7 @@ int hyel_block_precond_apply(hyel_ctx *ctx, const hyel_solver_params *params, co
                              hyel_solve_stats *stats) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!params || !r || !z) hyel::fail(HYEL_EINVAL, "block_precond_apply: null argument");
+        if (r == z) hyel::fail(HYEL_EINVAL, "block_precond_apply: r and z must be distinct");
         hyel::block_precond_apply(c, *params, r, z, stats);
     });
 }

@@ -173,4 +173,7 @@ def test_bad_degree(cube):
                                     raise_on_error=False)
         assert rc == H.HYEL_EINVAL, kw
     y = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
-    assert H.lib().hyel_a_cheb_apply(gp.ctx, 0, y.data_ptr(), y.data_ptr()) == H.HYEL_EINVAL
+    y2 = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    H.hyel_a_cheb_setup(gp.ctx)
+    assert H.lib().hyel_a_cheb_apply(gp.ctx, 0, y.data_ptr(), y2.data_ptr()) == H.HYEL_EINVAL
+    assert H.lib().hyel_a_cheb_apply(gp.ctx, 4, y.data_ptr(), y.data_ptr()) == H.HYEL_EINVAL

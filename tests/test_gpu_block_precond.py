@@ -165,3 +165,5 @@ def test_bad_block_precond(cube):
     rc = H.lib().hyel_block_precond_apply(gp.ctx, H.solver_params(block_precond=7), cube["rhs"].data_ptr(),
                                           x.data_ptr(), None)
     assert rc == H.HYEL_EINVAL
+    rc = H.lib().hyel_block_precond_apply(gp.ctx, H.solver_params(), x.data_ptr(), x.data_ptr(), None)
+    assert rc == H.HYEL_EINVAL

@@ -217,6 +217,7 @@ def test_argument_checks():
     for deg, ratio in ((0, 20.0), (17, 20.0), (4, 1.0), (4, -2.0), (4, float("nan"))):
         assert L.hyel_schur_hat_cheb(gp.ctx, H.HYEL_MAT_SCALED64, deg, ratio, x.data_ptr(), y.data_ptr()) == H.HYEL_EINVAL
     assert L.hyel_schur_hat_cheb(gp.ctx, H.HYEL_MAT_ASSEMBLED, 4, 0.0, x.data_ptr(), y.data_ptr()) == H.HYEL_EINVAL
+    assert L.hyel_schur_hat_cheb(gp.ctx, H.HYEL_MAT_SCALED64, 4, 0.0, x.data_ptr(), x.data_ptr()) == H.HYEL_EINVAL
     rhs = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
     xs = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
     for kw in ({"s_precond": 2}, {"s_precond": 1, "s_cheb_degree": 0}, {"s_precond": 1, "s_cheb_ratio": 0.5}, {"s_precond": 1, "s_cheb_ratio": -1.0},
