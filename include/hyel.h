@@ -9,6 +9,8 @@
  * paper; equations are named by their LaTeX labels.
  *
  * Conventions (every entry point):
+ *   - The context's device is made current for the call and the caller's
+ *     current device is restored before it returns.
  *   - Returns int: HYEL_OK (0) or a negative HYEL_E* code. After a non-zero
  *     return, hyel_last_error(ctx) holds a one-line message.
  *   - The caller owns every pointer it passes. Host arrays are copied before
@@ -266,7 +268,7 @@ const char *hyel_last_error(const hyel_ctx *ctx);
 /* Upload a P1 tetrahedral mesh (§3.1). X: host [n_nodes][3] reference
  * coordinates; tets: host [n_tets][4] node indices. Tetrahedra with negative
  * signed volume are reoriented; a zero-volume tetrahedron is HYEL_EINVERTED.
- * Builds the node-adjacency block pattern (sliced by 32 rows, see DESIGN), the
+ * Builds the node-adjacency block pattern (SELL-32: rows in slices of 32), the
  * element-to-block-slot gather lists and the per-element reference geometry
  * (shape-function gradients, volume, tau_M). Replaces any previous mesh. */
 int hyel_mesh_upload(hyel_ctx *ctx, int64_t n_nodes, const double *X,
@@ -279,19 +281,30 @@ int hyel_mesh_info(hyel_ctx *ctx, int64_t *info, int n);
 
 /* ---------------------------------------------------------------- assembly */
 
+/* What hyel_assemble computes: HYEL_RES the residual (the element pass that
+ * Newton's stopping test needs, §3.3 step 2), HYEL_TAN the consistent tangent
+ * (§3.3 step 4) with the residual and the right-hand side that come with it. */
+#define HYEL_RES 1u
+#define HYEL_TAN 2u
+
 /* Assemble at a stage state (Appendix A; §3.3 steps 2 and 4): residuals R_m,
- * R_p (with traction at t_n + alpha_f dt) and the consistent tangent blocks
+ * R_p (with traction at t_n + alpha_f dt) and, with HYEL_TAN in flags, the
+ * consistent tangent blocks
  * A = K_{m,vdot} + (a_f g dt/a_m) K_{m,udot}, B = K_{m,pdot},
  * C = K_{p,vdot} + (a_f g dt/a_m) K_{p,udot}, D = K_{p,pdot}
  * (eq. def_matrix_A, def_matrix_D), stored internally with Dirichlet rows and
  * columns of constrained velocity components replaced by identity.
+ *   flags    HYEL_RES (residual only: the stored blocks are left as they
+ *            were), HYEL_TAN or HYEL_RES | HYEL_TAN (residual and tangent);
+ *            anything else is HYEL_EINVAL.
  *   res_out  device [4N] or NULL: [R_m ; R_p], zero on Dirichlet components.
  *   rhs_out  device [4N] or NULL: right-hand side of eq. NR_smaller_eqn_1
- *            (or the literal step-5 form), zero on Dirichlet components.
+ *            (or the literal step-5 form), zero on Dirichlet components;
+ *            needs HYEL_TAN (HYEL_EINVAL otherwise).
  *   norms_out host [4] or NULL: ||R||, ||R_k||, ||R_p||, ||R_m|| over free
  *            components, R_k = udot_{n+am} - v_{n+af}. (Synchronizes.)
  * Returns HYEL_EINVERTED if some element has J <= 0 (then outputs are void). */
-int hyel_assemble(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_state *stage,
+int hyel_assemble(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_state *stage, unsigned flags,
                   double *res_out, double *rhs_out, double *norms_out);
 
 /* Copy the assembled (unscaled) blocks to host arrays in block-CSR order:
@@ -321,7 +334,9 @@ enum { HYEL_MAT_ASSEMBLED = 0, HYEL_MAT_SCALED64 = 1, HYEL_MAT_SCALED32 = 2, HYE
  * diagonal of the scaled A, i.e. A right-preconditioned by block-Jacobi; the
  * A-solves iterate on this operator (stored block by block as A_(r,c) M_c^-1).
  * SHAT ([N] -> [N], HYEL_MAT_SCALED64 or HYEL_MAT_SCALED32): y = S^ x with
- * the explicit S^ of hyel_schur_hat_setup (HYEL_ESTATE before it). */
+ * the explicit S^ of hyel_schur_hat_setup (HYEL_ESTATE before it).
+ * x and y must be distinct, non-overlapping ranges (HYEL_EINVAL otherwise):
+ * each row reads entries of x that other rows' threads are writing into y. */
 int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y);
 
 /* Prepare the scaled system for the current assembly (§4.1): W_ii =
@@ -356,14 +371,16 @@ int hyel_schur_hat_setup(hyel_ctx *ctx, double *bounds_out, int64_t *info, int n
  * (ratio = 0: the estimated one; ratio > 1: [lmax / ratio, lmax]), FP64
  * vectors. matrix: HYEL_MAT_SCALED64 (FP64 values of S^) or HYEL_MAT_SCALED32
  * (FP32 values, as inside the S-solve, where the polynomial reads S^ in FP32
- * at every precision). x, y: device [N] double, distinct. HYEL_ESTATE before
- * hyel_schur_hat_setup on the current assembly; HYEL_EINVAL for aliased x and
- * y, another matrix, degree outside 1..16 or another ratio. Synchronizes. */
+ * at every precision). x, y: device [N] double, distinct, non-overlapping.
+ * HYEL_ESTATE before hyel_schur_hat_setup on the current assembly; HYEL_EINVAL
+ * for overlapping x and y, another matrix, degree outside 1..16 or another
+ * ratio. Synchronizes. */
 int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio, const double *x, double *y);
 
 /* y = S x for the scaled system (Algorithm 2: D x - C A^-1 (B x)), the inner
  * A-solve controlled by params->inner, params->inner_solver (A_sym with CG)
- * and params->precision. x, y: device [N] double. */
+ * and params->precision. x, y: device [N] double, distinct, non-overlapping
+ * ranges (HYEL_EINVAL otherwise). */
 int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params,
                      const double *x, double *y, hyel_solve_stats *stats);
 
@@ -375,15 +392,15 @@ int hyel_a_cheb_setup(hyel_ctx *ctx, double *bounds_out);
 /* y = p(M^-1 A) M^-1 x, the HYEL_APREC_CHEB polynomial of the given degree
  * (1..16) on the interval of hyel_a_cheb_setup, as inside the A-solves: FP32
  * A values and directions, FP64 residual and result. x, y: device [3N]
- * double, distinct (HYEL_EINVAL otherwise). HYEL_ESTATE before
+ * double, distinct, non-overlapping (HYEL_EINVAL otherwise). HYEL_ESTATE before
  * hyel_a_cheb_setup on the current assembly. Synchronizes. */
 int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y);
 
 /* z = P^-1 r once, P the block preconditioner of params->block_precond on the
  * scaled system (§4.2–4.4), its sub-solves controlled by params (precision,
  * levels, A- and S-preconditioners) exactly as inside hyel_solve_nested.
- * r, z: device [4N] double ([v ; p] ordering), distinct (HYEL_EINVAL
- * otherwise). stats: host or NULL (a, s and inner counts). Synchronizes. */
+ * r, z: device [4N] double ([v ; p] ordering), distinct, non-overlapping
+ * (HYEL_EINVAL otherwise). stats: host or NULL (a, s and inner counts). Synchronizes. */
 int hyel_block_precond_apply(hyel_ctx *ctx, const hyel_solver_params *params,
                              const double *r, double *z, hyel_solve_stats *stats);
 
@@ -464,6 +481,30 @@ int hyel_profile(hyel_ctx *ctx, int enable);
  * Synchronizes. */
 int hyel_profile_read(hyel_ctx *ctx, double *ms, int64_t *launches, double *bytes);
 
+/* ---------------------------------------------------------------- failure detection */
+
+/* The persistent solver kernels (one cooperative launch per A-, S- or
+ * S^-solve and per Ritz-interval estimate) synchronize their blocks with grid
+ * barriers. Every wait at such a barrier is bounded: a block that waits
+ * longer than the limit sets an abort word, every block leaves at its next
+ * barrier, and the entry point returns HYEL_ECUDA with the context still
+ * usable (no device fault, no lost context). The paper has no counterpart
+ * (its solvers run on CPUs); the limit guards against a stalled or
+ * pre-empted block turning into a hang of the whole device.
+ * seconds: the limit, 1e-6 .. 60 (default 1). Takes effect at the next launch
+ * (also in CUDA graphs already built: the limit is read from device memory
+ * when a launch starts). Synchronizes. */
+int hyel_set_wait_limit(hyel_ctx *ctx, double seconds);
+
+/* Host-made fault injection for tests of the failure path above:
+ * HYEL_FAULT_BARRIER_SKIP makes block 0 of the next persistent launch leave
+ * one grid barrier without arriving, so the other blocks' waits run into the
+ * limit and the call reports HYEL_ECUDA; one launch takes it, later ones run
+ * normally. HYEL_FAULT_NONE withdraws a pending injection. Nothing here
+ * faults the device or waits without a bound. Synchronizes. */
+enum { HYEL_FAULT_NONE = 0, HYEL_FAULT_BARRIER_SKIP = 1 };
+int hyel_inject_fault(hyel_ctx *ctx, int kind);
+
 /* Number of kernel launches this library has issued in the process so far
  * (all contexts). count: host. */
 int hyel_launch_count(int64_t *count);
@@ -477,16 +518,19 @@ int hyel_launch_count(int64_t *count);
  * Stream-ordered, no synchronization.
  *
  * The paper has no counterpart: this serves callers that cannot allocate
- * device memory where they need a residual check (code running during CUDA
- * stream capture, frameworks whose pool allocator owns all device memory,
- * latency-critical loops). Its reduction scratch is a fixed 128 KB
- * file-scope device array, held by every GPU that loads the library until the
- * process exits; it calls no cudaMalloc, cudaFree or allocating routine.
- * Limit: N <= 1,048,576 nodes (HYEL_EINVAL beyond). The first call on a device
- * looks up the array's device address; make that first call before any stream
- * capture. All calls share the one array: calls whose kernels overlap on the
- * GPU (different streams or contexts at the same time) race and give wrong
- * results; serialize them. */
+ * device memory where they need a residual check (frameworks whose pool
+ * allocator owns all device memory and forbids cudaMalloc beside it, callers
+ * whose device-memory budget is spent, latency-critical loops where an
+ * allocation costs more than the check). Its reduction scratch is a fixed
+ * 128 KB file-scope device array, held by every GPU that loads the library
+ * until the process exits; it calls no cudaMalloc, cudaFree or allocating
+ * routine. Limit: N <= 1,048,576 nodes (HYEL_EINVAL beyond; HYEL_ESTATE with
+ * no mesh). The first call on a device looks up the array's device address
+ * and caches it for the process; make that first call before any stream
+ * capture, and do not call again after a cudaDeviceReset of that device (the
+ * cached address is then stale). All calls share the one array: calls whose
+ * kernels overlap on the GPU (different streams or contexts at the same time)
+ * race and give wrong results; serialize them. */
 int hyel_residual_norm_static(hyel_ctx *ctx, int matrix, const double *x, const double *b, double *out);
 
 #ifdef __cplusplus

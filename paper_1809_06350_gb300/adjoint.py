@@ -80,12 +80,16 @@ class HyelObjective(torch.autograd.Function):
                 ckpt[n + 1] = (y.clone(), yd.clone())
         fctx.problem = problem
         fctx.ckpt = ckpt
+        # the moduli this forward ran with: another forward on the same problem
+        # may replace the context's material before this backward runs
+        fctx.params = (mu_e.detach().clone(), kappa_e.detach().clone())
         fctx.shapes = (mu_e.shape, kappa_e.shape, mu_e.dtype, mu_e.device)
         return torch.dot(problem.w, y).reshape(())
 
     @staticmethod
     def backward(fctx, gJ):
         P = fctx.problem
+        P.set_params(*fctx.params)
         ybar = (gJ.to(P.w.device) * P.w).contiguous()
         ydbar = P.zeros()
         grad = torch.zeros((P.E, 4), dtype=torch.float64, device=P.w.device)

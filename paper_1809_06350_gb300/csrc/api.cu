@@ -94,19 +94,56 @@ void prof_end(Ctx &c, int cls, cudaEvent_t ev, double bytes) {
     }
 }
 
+void bar_reset(Ctx &c, unsigned *bar) {
+    HYEL_CK(cudaMemsetAsync(bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    HYEL_CK(cudaMemcpyAsync(bar + kBarCtl, c.ctl, 32 * sizeof(unsigned), cudaMemcpyDeviceToDevice, c.stream));
+}
+
 }  // namespace hyel
 
 namespace {
 
 thread_local std::string g_create_error;
 
+// Makes the context's device current for the duration of one entry point and
+// gives the caller's current device back on every exit path, so that a call
+// on a context for another device leaves the host thread (and any framework
+// that tracks the current device on it) where it was.
+struct DeviceGuard {
+    int prev = -1;
+    // raise = false (teardown): a failure to switch is ignored, not thrown
+    explicit DeviceGuard(int dev, bool raise = true) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) {
+            cudaError_t e = cudaSetDevice(dev);
+            if (e != cudaSuccess) {
+                if (raise) hyel::check_cuda(e, "cudaSetDevice");
+                (void)cudaGetLastError();
+            }
+        }
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) (void)cudaSetDevice(prev);
+    }
+};
+
+// [a, a + na) and [b, b + nb) (bytes) share at least one byte
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    if (!a || !b || na == 0 || nb == 0) return false;
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
 template <typename F>
 int guarded(hyel_ctx *ctx, F &&f) {
     if (!ctx) return HYEL_EINVAL;
     ctx->c.last_error.clear();
     try {
-        cudaError_t e = cudaSetDevice(ctx->c.device);
-        if (e != cudaSuccess) hyel::check_cuda(e, "cudaSetDevice");
+        DeviceGuard dg(ctx->c.device);
         f(ctx->c);
         return HYEL_OK;
     } catch (const hyel::Error &e) {
@@ -142,9 +179,20 @@ int hyel_create(hyel_ctx **out, int device, void *cuda_stream) {
         HYEL_CK(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
         HYEL_CK(cudaMallocHost(&c.h_red, 64 * sizeof(double)));
         HYEL_CK(cudaMallocHost(&c.h_err, 4 * sizeof(unsigned)));
+        HYEL_CK(cudaMalloc(&c.ctl, 32 * sizeof(unsigned)));
+        // words 4..5: the control line's own address, so that the block that
+        // takes an injected fault can withdraw it at the source (one-shot,
+        // also across replays of a CUDA graph)
+        unsigned h[32] = {0};
+        const unsigned long long self = (unsigned long long)(uintptr_t)c.ctl;
+        std::memcpy(h + 4, &self, sizeof self);
+        HYEL_CK(cudaMemcpy(c.ctl, h, sizeof h, cudaMemcpyHostToDevice));
     });
     if (rc != HYEL_OK) {
         g_create_error = ctx->c.last_error;
+        if (ctx->c.ctl) cudaFree(ctx->c.ctl);
+        if (ctx->c.h_red) cudaFreeHost(ctx->c.h_red);
+        if (ctx->c.h_err) cudaFreeHost(ctx->c.h_err);
         delete ctx;
         return rc;
     }
@@ -154,7 +202,7 @@ int hyel_create(hyel_ctx **out, int device, void *cuda_stream) {
 
 int hyel_destroy(hyel_ctx *ctx) {
     if (!ctx) return HYEL_EINVAL;
-    cudaSetDevice(ctx->c.device);
+    DeviceGuard dg(ctx->c.device, false);
     cudaStreamSynchronize(ctx->c.stream);
     hyel::free_workspace(ctx->c);
     hyel::amg_free(ctx->c);
@@ -168,6 +216,7 @@ int hyel_destroy(hyel_ctx *ctx) {
     for (auto e : ctx->c.prof.pool) cudaEventDestroy(e);
     if (ctx->c.h_red) cudaFreeHost(ctx->c.h_red);
     if (ctx->c.h_err) cudaFreeHost(ctx->c.h_err);
+    if (ctx->c.ctl) cudaFree(ctx->c.ctl);
     delete ctx;
     return HYEL_OK;
 }
@@ -194,13 +243,18 @@ int hyel_mesh_info(hyel_ctx *ctx, int64_t *info, int n) {
     });
 }
 
-int hyel_assemble(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_state *stage, double *res_out,
-                  double *rhs_out, double *norms_out) {
+int hyel_assemble(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_state *stage, unsigned flags,
+                  double *res_out, double *rhs_out, double *norms_out) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!tp || !stage || !stage->u || !stage->p || !stage->v || !stage->udot || !stage->pdot || !stage->vdot)
             hyel::fail(HYEL_EINVAL, "assemble: null argument");
+        if (flags == 0 || (flags & ~(unsigned)(HYEL_RES | HYEL_TAN)))
+            hyel::fail(HYEL_EINVAL, "assemble: flags must be HYEL_RES, HYEL_TAN or both");
+        const bool tangent = (flags & HYEL_TAN) != 0;
+        if (!tangent && rhs_out)
+            hyel::fail(HYEL_EINVAL, "assemble: the right-hand side needs HYEL_TAN (its K_{.,udot} R_k terms)");
         hyel::TimeConsts tc = hyel::time_consts(c.mesh, *tp);
-        hyel::assemble(c, tc, *stage, res_out, rhs_out, norms_out);
+        hyel::assemble(c, tc, *stage, res_out, rhs_out, norms_out, tangent);
     });
 }
 
@@ -213,6 +267,21 @@ int hyel_spmv(hyel_ctx *ctx, int op, int matrix, const void *x, void *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "spmv: null vector");
         if (op < HYEL_OP_FULL || op > HYEL_OP_SHAT) hyel::fail(HYEL_EINVAL, "spmv: bad op");
+        {
+            // input and output lengths of the operator, in elements
+            const size_t N = (size_t)c.mesh.N;
+            size_t nx = N, ny = N;
+            switch (op) {
+                case HYEL_OP_FULL: nx = ny = 4 * N; break;
+                case HYEL_OP_A:
+                case HYEL_OP_AM: nx = ny = 3 * N; break;
+                case HYEL_OP_B: ny = 3 * N; break;
+                case HYEL_OP_C: nx = 3 * N; break;
+                default: break;
+            }
+            const size_t es = (matrix == HYEL_MAT_SCALED32 || matrix == HYEL_MAT_SCALED_BF16S) ? 4 : 8;
+            if (overlaps(x, nx * es, y, ny * es)) hyel::fail(HYEL_EINVAL, "spmv: x and y must not overlap");
+        }
         if (op == HYEL_OP_SHAT) {
             if (matrix == HYEL_MAT_SCALED64)
                 hyel::shat_spmv<double>(c, (const double *)x, (double *)y);
@@ -298,7 +367,8 @@ int hyel_schur_hat_setup(hyel_ctx *ctx, double *bounds_out, int64_t *info, int n
 int hyel_schur_hat_cheb(hyel_ctx *ctx, int matrix, int32_t degree, double ratio, const double *x, double *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "schur_hat_cheb: null vector");
-        if (x == y) hyel::fail(HYEL_EINVAL, "schur_hat_cheb: x and y must be distinct");
+        const size_t n = (size_t)c.mesh.N * sizeof(double);
+        if (overlaps(x, n, y, n)) hyel::fail(HYEL_EINVAL, "schur_hat_cheb: x and y must not overlap");
         hyel::shat_cheb_apply(c, matrix, degree, ratio, x, y);
     });
 }
@@ -307,6 +377,8 @@ int hyel_schur_apply(hyel_ctx *ctx, const hyel_solver_params *params, const doub
                      hyel_solve_stats *stats) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!params || !x || !y) hyel::fail(HYEL_EINVAL, "schur_apply: null argument");
+        const size_t n = (size_t)c.mesh.N * sizeof(double);
+        if (overlaps(x, n, y, n)) hyel::fail(HYEL_EINVAL, "schur_apply: x and y must not overlap");
         hyel::schur_apply(c, *params, x, y, stats);
     });
 }
@@ -324,7 +396,8 @@ int hyel_a_cheb_setup(hyel_ctx *ctx, double *bounds_out) {
 int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!x || !y) hyel::fail(HYEL_EINVAL, "a_cheb_apply: null vector");
-        if (x == y) hyel::fail(HYEL_EINVAL, "a_cheb_apply: x and y must be distinct");
+        const size_t n = 3 * (size_t)c.mesh.N * sizeof(double);
+        if (overlaps(x, n, y, n)) hyel::fail(HYEL_EINVAL, "a_cheb_apply: x and y must not overlap");
         hyel::acheb_apply(c, degree, x, y);
     });
 }
@@ -333,7 +406,8 @@ int hyel_block_precond_apply(hyel_ctx *ctx, const hyel_solver_params *params, co
                              hyel_solve_stats *stats) {
     return guarded(ctx, [&](hyel::Ctx &c) {
         if (!params || !r || !z) hyel::fail(HYEL_EINVAL, "block_precond_apply: null argument");
-        if (r == z) hyel::fail(HYEL_EINVAL, "block_precond_apply: r and z must be distinct");
+        const size_t n = 4 * (size_t)c.mesh.N * sizeof(double);
+        if (overlaps(r, n, z, n)) hyel::fail(HYEL_EINVAL, "block_precond_apply: r and z must not overlap");
         hyel::block_precond_apply(c, *params, r, z, stats);
     });
 }
@@ -407,6 +481,25 @@ int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solv
 
 int hyel_residual_norm_static(hyel_ctx *ctx, int matrix, const double *x, const double *b, double *out) {
     return guarded(ctx, [&](hyel::Ctx &c) { hyel::residual_norm_static(c, matrix, x, b, out); });
+}
+
+int hyel_set_wait_limit(hyel_ctx *ctx, double seconds) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!(seconds >= 1e-6 && seconds <= 60.0)) hyel::fail(HYEL_EINVAL, "set_wait_limit: seconds must be in [1e-6, 60]");
+        const unsigned long long ns = (unsigned long long)(seconds * 1e9);
+        HYEL_CK(cudaMemcpyAsync(c.ctl, &ns, sizeof ns, cudaMemcpyHostToDevice, c.stream));
+        HYEL_CK(cudaStreamSynchronize(c.stream));
+    });
+}
+
+int hyel_inject_fault(hyel_ctx *ctx, int kind) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (kind != HYEL_FAULT_NONE && kind != HYEL_FAULT_BARRIER_SKIP)
+            hyel::fail(HYEL_EINVAL, "inject_fault: unknown kind");
+        const unsigned v = kind == HYEL_FAULT_BARRIER_SKIP ? 1u : 0u;  // block 0 + 1
+        HYEL_CK(cudaMemcpyAsync(c.ctl + 2, &v, sizeof v, cudaMemcpyHostToDevice, c.stream));
+        HYEL_CK(cudaStreamSynchronize(c.stream));
+    });
 }
 
 int hyel_launch_count(int64_t *count) {

@@ -45,6 +45,14 @@ void check_cuda(cudaError_t e, const char *what);
 // Device error word bits (set by kernels, read by the host at sync points).
 enum : unsigned { ERR_INVERTED = 1u, ERR_NAN = 2u, ERR_SINGULAR = 4u };
 
+// Grid-barrier words of the persistent (cooperative) kernels, one 128-byte
+// line each: arrivals, release, abort (cleared before every launch) and the
+// control line (wait limit in ns as a 64-bit word at kBarCtl, an injected
+// fault at kBarCtl + 2, the address of the context's control line as a 64-bit
+// word at kBarCtl + 4), copied from the context before every launch.
+constexpr int kBarArrive = 0, kBarRelease = 32, kBarAbort = 64, kBarWords = 96;
+constexpr int kBarCtl = 96, kBarAlloc = 128;
+
 struct DeviceMesh {
     int64_t N = 0, E = 0, nnzb = 0;
     int32_t nslices = 0;
@@ -213,7 +221,14 @@ struct Ctx {
     size_t bytes_held = 0;
     int num_sms = 152;
     std::vector<void *> allocations;
+    // control line of the grid barriers (see kBarCtl): device [32] words,
+    // owned apart from `allocations` (it outlives mesh replacements)
+    unsigned *ctl = nullptr;
 };
+
+// Clears the barrier words of one persistent launch and copies the context's
+// control line (wait limit, injected fault) beside them, in stream order.
+void bar_reset(Ctx &c, unsigned *bar);
 
 // process-wide count of kernel launches issued by this library; while a graph
 // is being recorded (g_capture_count set) launches are counted there instead

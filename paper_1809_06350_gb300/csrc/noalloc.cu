@@ -2,13 +2,20 @@
 // coupled operator M = [[A, B], [C, D]] without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// residual check: code that runs while a CUDA stream is being captured into a
-// graph (cudaMalloc is not allowed during capture), frameworks that hand all
-// device memory to their own pool allocator and forbid direct allocation, and
-// latency-critical loops that cannot afford an allocation. For them this
-// entry point keeps its reduction scratch (per-block partial sums and the
-// completion counter) in a fixed, file-scope device array instead of the
-// context's workspace; it calls no cudaMalloc, cudaFree or allocating routine.
+// residual check: frameworks that hand all device memory to their own pool
+// allocator and forbid direct cudaMalloc calls beside it, callers that run
+// with a hard device-memory budget already spent, and latency-critical loops
+// in which an allocation (and the device synchronization cudaFree implies)
+// costs more than the check itself. For them this entry point keeps its
+// reduction scratch (per-block partial sums and the completion counter) in a
+// fixed, file-scope device array instead of the context's workspace; it calls
+// no cudaMalloc, cudaFree or allocating routine.
+//
+// The array's device address is looked up once per device (at the first call
+// with that device current) and cached for the life of the process. A
+// cudaDeviceReset of that device, or any other teardown of its primary
+// context, unloads the module and invalidates the cached address: do not call
+// this entry point again in a process that has reset the device.
 //
 // The arithmetic is that of the solver's true-residual check: each block row
 // is formed in the same order as the full-operator SpMV, squared and summed
@@ -133,6 +140,7 @@ void residual_norm_static(Ctx &c, int matrix, const double *x, const double *b, 
     if (!c.mat.assembled) fail(HYEL_ESTATE, "residual_norm_static: nothing assembled");
     if (matrix == HYEL_MAT_SCALED64 && !c.mat.scaled) fail(HYEL_ESTATE, "residual_norm_static: call hyel_solve_setup first");
     const DeviceMesh &m = c.mesh;
+    if (m.N <= 0) fail(HYEL_ESTATE, "residual_norm_static: no mesh uploaded");
     const int64_t blocks = (m.N + kNsThreads - 1) / kNsThreads;
     if (blocks > kNsMaxBlocks)
         fail(HYEL_EINVAL, "residual_norm_static: mesh has " + std::to_string(m.N) +

@@ -185,7 +185,7 @@ void shat_build(Ctx &c) {
     h->v32 = dalloc_n<float>(c, (size_t)nslots);
     h->bounds = dalloc_n<double>(c, 2);
     h->work = dalloc_n<double>(c, 3 * (size_t)N);
-    h->bar = (unsigned *)dalloc(c, 96 * sizeof(unsigned));  // the grid barrier's three 128-byte lines
+    h->bar = (unsigned *)dalloc(c, kBarAlloc * sizeof(unsigned));  // the grid barrier's four 128-byte lines
 }
 
 }  // namespace

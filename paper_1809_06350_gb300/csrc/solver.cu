@@ -608,23 +608,39 @@ struct SgArgs {
 };
 
 // Barrier words, each on its own 128-byte line: arrivals (they only grow
-// within a launch), release (the number of completed barriers), abort.
-constexpr int kBarArrive = 0, kBarRelease = 32, kBarAbort = 64, kBarWords = 96;
+// within a launch), release (the number of completed barriers), abort. The
+// fourth line (kBarCtl, copied from the context's control line before every
+// launch, see bar_reset) holds the wait limit in ns (64-bit; 0 = kBarrierNs),
+// the injected fault (a value b + 1 makes block b skip one arrival; the block
+// clears it in the context's line, whose address is the 64-bit word at
+// kBarCtl + 4, so one launch takes it) (hyel_inject_fault).
 
 // Grid barrier number `phase` (then phase + 1). The last block to arrive
-// releases the others; a wait is bounded by kBarrierNs. false: the wait ran
-// out of time or a block gave up (every block then leaves). The fences around
-// the wait make writes issued before the barrier by any block visible to
-// ordinary loads of every thread of the block after it.
+// releases the others; a wait is bounded by the limit of the control line
+// (kBarrierNs by default). false: the wait ran out of time or a block gave up
+// (every block then leaves). The fences around the wait make writes issued
+// before the barrier by any block visible to ordinary loads of every thread
+// of the block after it.
 __device__ bool pg_barrier(unsigned *bw, unsigned &phase) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
+        volatile unsigned *vb = bw;
+        int ok = 1;
+        const unsigned me = blockIdx.x + 1u;
+        unsigned *src = reinterpret_cast<unsigned *>(
+            (uintptr_t)*reinterpret_cast<volatile unsigned long long *>(bw + kBarCtl + 4));
+        if (vb[kBarCtl + 2] == me && src && atomicCAS(src + 2, me, 0u) == me) {
+            // injected fault, withdrawn at its source so that one launch takes
+            // it: this block leaves the barrier without arriving, and every
+            // other block's wait runs into its limit
+            vb[kBarCtl + 2] = 0u;
+        } else {
         const unsigned target = (phase + 1u) * gridDim.x;
         const unsigned prev = atomicAdd(&bw[kBarArrive], 1u);
-        int ok = 1;
-        volatile unsigned *vb = bw;
+        unsigned long long limit = *reinterpret_cast<volatile unsigned long long *>(bw + kBarCtl);
+        if (limit == 0ull) limit = kBarrierNs;
         if (prev + 1u == target) {
             __threadfence();
             atomicExch(&bw[kBarRelease], phase + 1u);
@@ -632,12 +648,13 @@ __device__ bool pg_barrier(unsigned *bw, unsigned &phase) {
             const unsigned long long t0 = global_ns();
             while (vb[kBarRelease] < phase + 1u) {
                 __nanosleep(32);
-                if (vb[kBarAbort] != 0u || global_ns() - t0 > kBarrierNs) {
+                if (vb[kBarAbort] != 0u || global_ns() - t0 > limit) {
                     atomicExch(&bw[kBarAbort], 1u);
                     ok = 0;
                     break;
                 }
             }
+        }
         }
         if (vb[kBarAbort] != 0u) ok = 0;
         s_ok = ok;
@@ -2063,7 +2080,7 @@ void level_init(Ctx &c, Workspace &w, Level<T> &L, int64_t n, int m, int kind) {
         const int64_t nodes = kind == 0 ? n / 3 : n;
         L.z2 = (T *)walloc(c, w, sizeof(T) * (size_t)n);
         if (kind == 0) L.ach = (unsigned char *)walloc(c, w, (size_t)n * (2 * sizeof(T) + 2 * sizeof(float)));
-        L.bar = (unsigned *)walloc(c, w, sizeof(unsigned) * kBarWords);
+        L.bar = (unsigned *)walloc(c, w, sizeof(unsigned) * kBarAlloc);
         const int64_t need = std::max<int64_t>(1, (nodes + 31) / 32);  // no block without a slice
         int occ = 0, occ16 = 0;
         if (kind == 0)
@@ -2369,7 +2386,7 @@ void a_solve(Rec &R, Workspace &w, LevelState *st, const hyel_krylov_level &P, c
     bool h16 = false;
     Level<T> &L = Sys<T>::la(w);
     PgArgs<T> a = pg_args<T>(c, w, st, P, b, x, h16);
-    HYEL_CK(cudaMemsetAsync(L.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    bar_reset(c, L.bar);
     cudaLaunchConfig_t cfg = coop_config(c, h16 ? L.pg_grid16 : L.pg_grid);
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -2522,7 +2539,7 @@ void s_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T *x
         g.it_fixed += (d - 1) * ((double)h.nnz * 8.0 + (double)N * (sizeof(T) + 8.0)) +
                       (3.0 + 6.0 * (d - 1)) * (double)N * sizeof(T);
     }
-    HYEL_CK(cudaMemsetAsync(La.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    bar_reset(c, La.bar);
     const bool ach = w.a_cheb > 0;
     const void *kicg = cheb ? (const void *)k_gmres_s<T, false, true, true, false>
                             : (const void *)k_gmres_s<T, false, false, true, false>;
@@ -2585,7 +2602,7 @@ void schur_op(Rec &R, Workspace &w, const hyel_solver_params &p, const T *x, T *
         // one cooperative launch of the CG inner solve on A_sym
         CgArgs<T> cg = cg_args<T>(c, w, p, xbar, xtil);
         Level<T> &La = Sys<T>::la(w);
-        HYEL_CK(cudaMemsetAsync(La.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+        bar_reset(c, La.bar);
         cudaLaunchConfig_t cfg = coop_config(c, resident_grid(c, (const void *)k_cg_a<T>));
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeCooperative;
@@ -2651,7 +2668,7 @@ void shat_solve(Rec &R, Workspace &w, const hyel_solver_params &p, const T *b, T
                       (3.0 + 6.0 * (d - 1)) * (double)N * sizeof(T);
     }
     g.it_unit = (double)N * sizeof(T);
-    HYEL_CK(cudaMemsetAsync(Ls.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    bar_reset(c, Ls.bar);
     cudaLaunchConfig_t cfg = coop_config(c, cheb ? Ls.pg_grid_shc : Ls.pg_grid_sh);
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -3000,7 +3017,7 @@ void shat_bounds(Ctx &c) {
     a.partial = h.partial;
     a.bar = h.bar;
     a.N = N;
-    HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    bar_reset(c, h.bar);
     HYEL_CK(cudaMemsetAsync(h.arn_H, 0, sizeof(double) * K1 * kRitzSteps, c.stream));
     void *args[] = {&a};
     coop_launch(c, grid, (const void *)k_shat_arnoldi, args);
@@ -3076,7 +3093,7 @@ void acheb_setup(Ctx &c) {
         h->U = dalloc_n<float>(c, 3 * (size_t)n);
         h->H = dalloc_n<double>(c, (size_t)K1 * kRitzSteps);
         h->partial = dalloc_n<double>(c, 2 * gmax * K1);
-        h->bar = (unsigned *)dalloc(c, kBarWords * sizeof(unsigned));
+        h->bar = (unsigned *)dalloc(c, kBarAlloc * sizeof(unsigned));
         h->work = dalloc_n<double>(c, (size_t)n);
         h->dwork = dalloc_n<float>(c, 2 * (size_t)n);
     }
@@ -3094,7 +3111,7 @@ void acheb_setup(Ctx &c) {
     a.partial = h.partial;
     a.bar = h.bar;
     a.N = N;
-    HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    bar_reset(c, h.bar);
     HYEL_CK(cudaMemsetAsync(h.H, 0, sizeof(double) * K1 * kRitzSteps, c.stream));
     void *args[] = {&a};
     coop_launch(c, coop_grid(c, (const void *)k_a_arnoldi), (const void *)k_a_arnoldi, args);
@@ -3144,7 +3161,7 @@ void acheb_apply(Ctx &c, int degree, const double *x, double *y) {
     a.g.N = m.N;
     a.g.bar = h.bar;
     unsigned *status = c.err;
-    HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    bar_reset(c, h.bar);
     HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
     void *args[] = {&a, (void *)&x, (void *)&y, &status};
     coop_launch(c, coop_grid(c, (const void *)k_acheb_apply), (const void *)k_acheb_apply, args);
@@ -3162,7 +3179,7 @@ void shat_cheb_apply(Ctx &c, int matrix, int degree, double ratio, const double 
     const int64_t N = c.mesh.N;
     unsigned *bar = h.bar, *status = c.err;
     int64_t n = N;
-    HYEL_CK(cudaMemsetAsync(h.bar, 0, kBarWords * sizeof(unsigned), c.stream));
+    bar_reset(c, h.bar);
     HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
     if (matrix == HYEL_MAT_SCALED64) {
         shat_ensure64(c);
@@ -3211,6 +3228,9 @@ void schur_apply(Ctx &c, const hyel_solver_params &p, const double *x, double *y
         out->inner_its = w.h_states[ST_INNER].its;
         out->inner_solves = w.h_states[ST_INNER].solves;
     }
+    if (w.h_states[ST_INNER].status_any & 8)
+        fail(HYEL_ECUDA, "schur_apply: a grid barrier of the inner A-solve timed out");
+    if (w.h_states[ST_INNER].status_any & 1) fail(HYEL_ENAN, "schur_apply: NaN or Inf in the inner A-solve");
 }
 
 void block_precond_apply(Ctx &c, const hyel_solver_params &p, const double *r, double *z, hyel_solve_stats *out) {

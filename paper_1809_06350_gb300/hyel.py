@@ -19,6 +19,8 @@ HYEL_OK = 0
 HYEL_EINVAL, HYEL_ECUDA, HYEL_ENOMEM, HYEL_ENOCONV = -1, -2, -3, -4
 HYEL_EBREAKDOWN, HYEL_ENAN, HYEL_EINVERTED, HYEL_ESINGULAR, HYEL_ESTATE = -5, -6, -7, -8, -9
 HYEL_VOL_GIBBS, HYEL_VOL_INCOMPRESSIBLE = 0, 1
+HYEL_RES, HYEL_TAN = 1, 2
+HYEL_FAULT_NONE, HYEL_FAULT_BARRIER_SKIP = 0, 1
 HYEL_PREC_FP64, HYEL_PREC_FP32, HYEL_PREC_BF16S = 0, 1, 2
 HYEL_APREC_BJACOBI, HYEL_APREC_AMG, HYEL_APREC_CHEB = 0, 1, 2
 HYEL_SPREC_JACOBI, HYEL_SPREC_CHEB = 0, 1
@@ -40,7 +42,7 @@ EXPORTS = [
     "hyel_launch_count", "hyel_residual_norm_static", "hyel_update_material",
     "hyel_solve_nested_transpose", "hyel_param_sensitivity", "hyel_adjoint_step",
     "hyel_schur_hat_setup", "hyel_schur_hat_cheb", "hyel_block_precond_apply", "hyel_a_cheb_setup",
-    "hyel_a_cheb_apply",
+    "hyel_a_cheb_apply", "hyel_set_wait_limit", "hyel_inject_fault",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -127,7 +129,8 @@ def lib():
             "hyel_mesh_upload": (C.c_int, [vp, C.c_int64, _dp, C.c_int64, _ip, C.POINTER(HyelBC),
                                            C.POINTER(HyelMaterial)]),
             "hyel_mesh_info": (C.c_int, [vp, C.POINTER(C.c_int64), C.c_int]),
-            "hyel_assemble": (C.c_int, [vp, C.POINTER(HyelTimeParams), C.POINTER(HyelState), vp, vp, _dp]),
+            "hyel_assemble": (C.c_int, [vp, C.POINTER(HyelTimeParams), C.POINTER(HyelState), C.c_uint, vp, vp,
+                                        _dp]),
             "hyel_matrix_download": (C.c_int, [vp, _ip, _ip, _dp, _dp, _dp, _dp]),
             "hyel_spmv": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
             "hyel_solve_setup": (C.c_int, [vp, vp]),
@@ -152,6 +155,8 @@ def lib():
             "hyel_a_cheb_apply": (C.c_int, [vp, C.c_int32, vp, vp]),
             "hyel_block_precond_apply": (C.c_int, [vp, C.POINTER(HyelSolverParams), vp, vp,
                                                    C.POINTER(HyelSolveStats)]),
+            "hyel_set_wait_limit": (C.c_int, [vp, C.c_double]),
+            "hyel_inject_fault": (C.c_int, [vp, C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -212,9 +217,9 @@ def hyel_mesh_info(ctx):
     return {"N": out[0], "E": out[1], "nnzb": out[2], "nslots": out[3], "bytes": out[4]}
 
 
-def hyel_assemble(ctx, tp, stage, res_out=0, rhs_out=0, want_norms=True):
+def hyel_assemble(ctx, tp, stage, res_out=0, rhs_out=0, want_norms=True, flags=HYEL_RES | HYEL_TAN):
     norms = (C.c_double * 4)()
-    _check(ctx, lib().hyel_assemble(ctx, C.byref(tp), C.byref(stage), C.c_void_p(res_out or 0),
+    _check(ctx, lib().hyel_assemble(ctx, C.byref(tp), C.byref(stage), int(flags), C.c_void_p(res_out or 0),
                                     C.c_void_p(rhs_out or 0), norms if want_norms else None))
     return list(norms)
 
@@ -335,6 +340,14 @@ def hyel_residual_norm_static(ctx, matrix, x_ptr, b_ptr, out_ptr):
     the device (fixed scratch array inside the library)."""
     return _check(ctx, lib().hyel_residual_norm_static(ctx, int(matrix), C.c_void_p(x_ptr), C.c_void_p(b_ptr),
                                                        C.c_void_p(out_ptr)))
+
+
+def hyel_set_wait_limit(ctx, seconds):
+    return _check(ctx, lib().hyel_set_wait_limit(ctx, float(seconds)))
+
+
+def hyel_inject_fault(ctx, kind):
+    return _check(ctx, lib().hyel_inject_fault(ctx, int(kind)))
 
 
 def hyel_launch_count():

@@ -9,6 +9,9 @@ top-face u_z after 20 generalized-alpha steps, checkpoints every 5 steps.
   moves J by ~1e-11 relative, so at h = 1e-6 the forward runs' 1e-12
   Newton tolerance already puts the difference quotient at the 1e-6 max|g|
   noise floor; h = 1e-5 keeps the check clear of it;
+* the same element-wise check on 10 of those elements with FP64 levels;
+* a perturbed forward run between a forward and its backward leaves the
+  gradient unchanged (to 1e-12 of its largest entry);
 * FP32 preconditioner levels give the FP64 gradient to 1e-6.
 """
 import numpy as np
@@ -43,20 +46,45 @@ def test_config5_adjoint_vs_finite_differences():
         J = HyelObjective.apply(mu_t, ka_t, P)
         J.backward()
         grads[prec] = (mu_t.grad.numpy().copy(), ka_t.grad.numpy().copy())
+        gm, gk = grads[prec]
+        rng = np.random.default_rng(2)
+        dmu, dka = rng.standard_normal(E), rng.standard_normal(E)
+        els = rng.choice(E, 50, replace=False)
+
+        def J_of(a, b):
+            with torch.no_grad():
+                return float(HyelObjective.apply(torch.tensor(a), torch.tensor(b), P))
+
+        if prec == H.HYEL_PREC_FP64:
+            # a perturbed forward between forward and backward must not change
+            # the gradient (the backward restores the moduli of its forward)
+            mu_t2 = torch.tensor(mu, requires_grad=True)
+            ka_t2 = torch.tensor(ka, requires_grad=True)
+            J2 = HyelObjective.apply(mu_t2, ka_t2, P)
+            J_of(mu * 1.01, ka * 0.99)
+            J2.backward()
+            # (the perturbation moves the gradient by ~1e-2 relative; rerunning the
+            # same forward and backward reproduces it to rounding)
+            for g2, g1 in ((mu_t2.grad.numpy(), gm), (ka_t2.grad.numpy(), gk)):
+                assert np.max(np.abs(g2 - g1)) <= 1e-12 * np.abs(g1).max()
+            # element-wise central differences on the first 10 of the 50 elements
+            h = 1e-5
+            for which, sel in ((0, els[:5]), (1, els[25:30])):
+                base, g = (mu, gm) if which == 0 else (ka, gk)
+                for e in sel:
+                    p, q = base.copy(), base.copy()
+                    p[e] *= 1 + h
+                    q[e] *= 1 - h
+                    if which == 0:
+                        d = (J_of(p, ka) - J_of(q, ka)) / (2 * h * base[e])
+                    else:
+                        d = (J_of(mu, p) - J_of(mu, q)) / (2 * h * base[e])
+                    assert abs(g[e] - d) <= 1e-6 * np.abs(g).max(), (which, e, g[e], d)
         if prec == H.HYEL_PREC_FP32:
-            gm, gk = grads[prec]
-            rng = np.random.default_rng(2)
-            dmu, dka = rng.standard_normal(E), rng.standard_normal(E)
-
-            def J_of(a, b):
-                with torch.no_grad():
-                    return float(HyelObjective.apply(torch.tensor(a), torch.tensor(b), P))
-
             h = 1e-6
             fd = (J_of(mu * (1 + h * dmu), ka * (1 + h * dka)) - J_of(mu * (1 - h * dmu), ka * (1 - h * dka))) / (2 * h)
             ad = np.sum(gm * mu * dmu) + np.sum(gk * ka * dka)
             assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
-            els = rng.choice(E, 50, replace=False)
             h = 1e-5
             for which, sel in ((0, els[:25]), (1, els[25:])):
                 base, g = (mu, gm) if which == 0 else (ka, gk)

@@ -1,6 +1,7 @@
 """hyel_residual_norm_static: the residual check for callers that cannot
-allocate device memory (code running during CUDA stream capture, frameworks
-whose pool allocator owns all device memory, latency-critical loops). Its
+allocate device memory (frameworks whose pool allocator owns all device memory
+and forbids cudaMalloc beside it, callers whose device-memory budget is spent,
+latency-critical loops where an allocation costs more than the check). Its
 scratch is a fixed device array inside the library.
 
 Checked against the existing entry points on two calls in a row:
@@ -59,6 +60,17 @@ def test_residual_norm_static_matches_existing_entry_points():
         o = out.cpu().numpy()
         assert o[0] == pytest.approx(ref_r, rel=1e-12)
         assert o[1] == pytest.approx(ref_b, rel=1e-12)
+    # the property the entry point exists for: after the calls above, two more
+    # calls leave both PyTorch's allocator and the device's free memory as
+    # they were
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _call in range(2):
+        H.hyel_residual_norm_static(gp.ctx, H.HYEL_MAT_ASSEMBLED, xr.data_ptr(), br.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0
     with pytest.raises(H.HyelError) as ei:
         H.hyel_residual_norm_static(gp.ctx, H.HYEL_MAT_SCALED32, xs.data_ptr(), bs.data_ptr(), out.data_ptr())
     assert ei.value.code == H.HYEL_EINVAL
