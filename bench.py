@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-sweep", action="store_true", help="skip the Poisson-ratio sweep keys")
     p.add_argument("--host-loops", action="store_true",
                    help="drive the Krylov loops from the host (for per-kernel ncu launch lists)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16s"],
@@ -212,6 +213,54 @@ def cpu_sample(n_sample=12, steps=2, args=None):
                       f"(n={n} unknowns, {solves} direct solves, {sec:.1f} s); rate in unknowns*solves/s"}
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return os.uname().machine
+
+
+def cpu_plan(args):
+    """The CPU side of the measurement plan, on the host cores of the GPU machine:
+    (1) the oracle's element assembly (the complex-step residual Jacobian of
+    the Appendix A element routine, vectorized numpy over elements, one
+    thread) timed on a 16^3-hex sample (24,576 tets) of the workload's cube
+    and scaled to one pass over the 48^3 cube's 663,552 tets; (2) the
+    oracle's direct solve (SuperLU, COLAMD) of one Newton system of the
+    16^3-hex cube (n = 19,652). The 48^3 direct solve is not attempted: its
+    banded storage alone is about 74 GB."""
+    from oracle import system as S
+    from paper_1809_06350_gb300 import inputs
+    n = 16
+    mesh = inputs.cube_mesh(n, jitter=0.05, seed=0)
+    mu = 1e5
+    mat = inputs.material_nh(mu, inputs.kappa_from_nu(mu, args.nu), 1e3)
+    prob = S.Problem(mesh, mat, load={"p_max": 2e4, "t_ramp": 10 * args.dt})
+    st = inputs.random_state(prob.N, seed=17, u_scale=0.02 / n, v_scale=0.02, p_scale=1e3, rate_scale=2.0)
+    am, af, gam = S.gen_alpha(0.5)
+    ga = (am, af, gam, args.dt)
+    t0 = time.perf_counter()
+    K = S.assemble_matrix(prob, st, ga)
+    t_asm = time.perf_counter() - t0
+    rhs, _, _, _ = S.newton_rhs(prob, st, af * args.dt, ga)
+    Kd, r = S.apply_dirichlet(K, rhs, S.dirichlet_dofs(prob))
+    t0 = time.perf_counter()
+    S.direct_solve(Kd, r)
+    t_lu = time.perf_counter() - t0
+    E48 = 6 * 48 ** 3
+    return {"cpu_model": cpu_model(),
+            "oracle_assembly_pass_s_cube48": t_asm * E48 / prob.E,
+            "oracle_assembly_sample": f"tangent assembly of the {n}^3-hex cube ({prob.E} tets, {t_asm:.2f} s, one "
+                                      f"thread), scaled by 663,552 / {prob.E}",
+            "oracle_direct_solve_s_cube16": t_lu,
+            "oracle_direct_solve_sample": f"SuperLU (COLAMD) factor + solve of one Newton system, n = {4 * prob.N}",
+            "oracle_direct_solve_cube48": "not attempted: banded storage about 74 GB"}
+
+
 # ------------------------------------------------------------------ arms
 
 def run_reference(args, rank, world):
@@ -227,14 +276,73 @@ def run_reference(args, rank, world):
     sec = time.perf_counter() - t0
     v = statistics.mean(vals)
     mesh, _, _, _ = workload(args)
+    cfg = config_dict(args, mesh)
+    cfg["workload"] += " (oracle timed on a 10^3-hex sample of it)"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(1, args.steps + args.warmup),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(args, mesh),
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                              "sample": "each step: oracle Newton step t=0 on the 10^3-hex cube (direct solve)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def nu_sweep(ctx, H, torch, stream, args, names, sizes, dev, state, sprec_kw, graph, steps=5):
+    """The Poisson-ratio sweep of the cube workload (nu = 0.45, 0.499 and the
+    incompressible model nu = 0.5), same mesh, load and solver options as the
+    headline run: `steps` time steps from rest with FP64 levels and with FP32
+    levels, each timed with CUDA events on the library's stream after one
+    warm-up step, and the relative difference of the FP32-level state from the
+    FP64-level state after every step (untimed rerun)."""
+    from paper_1809_06350_gb300 import inputs
+    out = {}
+    mu = 1e5
+    mesh = inputs.cube_mesh(args.n, jitter=0.05, seed=0)
+    load = {"p_max": 2e4, "t_ramp": 10 * args.dt}
+    for nu in (0.45, 0.499, 0.5):
+        mat = inputs.material_nh(mu, inputs.kappa_from_nu(mu, nu), 1e3)
+        inp = H.MeshInputs(mesh, mat, None, load)
+        H.hyel_mesh_upload(ctx, inp.X, inp.tets, inp.bc, inp.mat)
+        row = {}
+        states = {}
+        for lab, prec in (("fp64", H.HYEL_PREC_FP64), ("fp32", H.HYEL_PREC_FP32)):
+            sp = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=prec, graph=graph, **sprec_kw)
+            for t in dev.values():
+                t.zero_()
+            H.hyel_newton_step(ctx, H.time_params(dt=args.dt, t_n=0.0), sp, state, raise_on_error=False)
+            for t in dev.values():
+                t.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            its = 0
+            e0.record(stream)
+            for k in range(steps):
+                st, rc = H.hyel_newton_step(ctx, H.time_params(dt=args.dt, t_n=k * args.dt), sp, state,
+                                            raise_on_error=False)
+                if rc not in (H.HYEL_OK, H.HYEL_ENOCONV):
+                    raise H.HyelError(rc, H.hyel_last_error(ctx))
+                its += st.iterations
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[lab + "_ms_per_step"] = ms / steps
+            row[lab + "_newton_solves"] = its
+            for t in dev.values():
+                t.zero_()
+            seq = []
+            for k in range(steps):
+                H.hyel_newton_step(ctx, H.time_params(dt=args.dt, t_n=k * args.dt), sp, state, raise_on_error=False)
+                seq.append(torch.cat([dev[nm] for nm in names]).clone())
+            states[lab] = seq
+        row["fp32_per_step_rel_diff_vs_fp64"] = [
+            float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(states["fp32"], states["fp64"])]
+        row["speedup_fp32_vs_fp64"] = row["fp64_ms_per_step"] / row["fp32_ms_per_step"]
+        out[f"nu={nu}"] = row
+    out["note"] = (f"{steps} time steps from rest per run after one warm-up step, 48^3 cube, dead load ramped over 10 "
+                   "steps, headline solver options; nu = 0.5 is the incompressible model")
+    return out
 
 
 def run_hyel(args, rank, world, local_rank):
@@ -407,6 +515,24 @@ def run_hyel(args, rank, world, local_rank):
     by_live = pl["bytes"] / max(1, pl["launches"])
     gbs_live = by_live / (us_live * 1e-6) / 1e9 if pl["launches"] else None
 
+    def fp64_peak(reps=5):
+        """FP64 FMA rate of this GPU, measured now by the library's probe
+        kernel (independent FMA chains, no memory traffic), best of reps."""
+        sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+        H.hyel_fp64_fma_probe(ctx, 1 << 10, sink.data_ptr())
+        best = 0.0
+        for _ in range(reps):
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            fl = H.hyel_fp64_fma_probe(ctx, 1 << 14, sink.data_ptr())
+            a1.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, fl / (a0.elapsed_time(a1) * 1e-3) / 1e12)
+        return best
+
+    fp64_tflops = fp64_peak()
+
     H.hyel_solve_setup(ctx)
     gbs64, us64, by64 = spmv_timed(H.HYEL_MAT_SCALED64, torch.float64, "spmv_A64")
     gbs32, us32, by32 = spmv_timed(H.HYEL_MAT_SCALED32, torch.float32, "spmv_A32")
@@ -442,13 +568,65 @@ def run_hyel(args, rank, world, local_rank):
                 "spmv_A32": {"achieved": gbs32, "frac": gbs32 / peak, "bytes_per_launch": by32, "avg_launch_us": us32},
                 "spmv_A16": {"achieved": gbs16, "frac": gbs16 / peak, "bytes_per_launch": by16,
                              "avg_launch_us": us16}}}
+    # the element pass: FP64-arithmetic bound (its FP64 instructions per tet
+    # come from the committed ncu counters of the same source)
+    E = int(mesh["tets"].shape[0])
+
+    def elem_entry(cls, field, desc):
+        pe = prof_host[cls]
+        us = 1e3 * pe["ms"] / max(1, pe["launches"])
+        fpt = profile_traffic("element_cube48", "assemble.cu", field)
+        dram = profile_traffic("element_cube48", "assemble.cu", field.replace("fp64_flops", "dram_bytes"))
+        ach = fpt * E / (us * 1e-6) / 1e12 if (fpt and pe["launches"]) else None
+        return {"kernel": desc, "bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": ach / fp64_tflops if ach else None,
+                "traffic": dram * E if dram is not None else None,
+                "peak_source": "measured in this run: FP64 FMA-chain probe kernel (hyel_fp64_fma_probe), best of 5; "
+                               "nominal GB300 FP64 1.25 TFLOP/s",
+                "flops_per_tet": fpt, "tets": E, "avg_launch_us": us, "launches": pe["launches"],
+                "algorithmic_flops": "FP64 flops per tet (2 per DFMA, 1 per DADD/DMUL) counted by ncu on the element "
+                                     "kernel of the same source (profiles/element_cube48.md) x tets per launch",
+                "measured": "CUDA events around every launch on the library stream (host-driven replay)"}
+
+    roof_k = {
+        dom: roof,
+        "assemble_elem": elem_entry("assemble_elem", "fp64_flops_per_tet_tangent",
+                                    "k_element<true, *> (element residual and tangent blocks, one thread per tet)"),
+        "assemble_res": elem_entry("assemble_res", "fp64_flops_per_tet_residual",
+                                   "k_element<false, false> (residual-only element pass)")}
+    other = "gmres_A" if dom == "gmres_S" else "gmres_S"
+    po = prof_host[other]
+    if po["launches"]:
+        us_o = 1e3 * po["ms"] / po["launches"]
+        by_o = po["bytes"] / po["launches"]
+        roof_k[other] = {"kernel": kdesc[other], "bound": "hbm", "achieved": by_o / (us_o * 1e-6) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": by_o / (us_o * 1e-6) / 1e9 / peak,
+                         "bytes_per_launch": by_o, "avg_launch_us": us_o, "launches": po["launches"]}
+    for k in ("gmres_A", "gmres_S"):
+        if k in roof_k and roof_k[k].get("achieved"):
+            pn = "gmres_" + k[-1].lower() + ("_cheb" if k == "gmres_S" and args.s_precond == "cheb" else "")
+            ratio = profile_traffic(pn + "_cube48", "solver.cu", "dram_over_algorithmic")
+            roof_k[k]["dram_frac"] = (ratio * roof_k[k]["achieved"] / peak) if (ratio and args.precision == "fp64") \
+                else None
+            roof_k[k]["dram_note"] = ("DRAM bytes = the committed ncu capture's DRAM / algorithmic ratio x the "
+                                      "algorithmic bytes; where it is below 1 the rest is served from L2")
+    # the dominant kernel by replay time takes the top-level roofline
+    top = max(("gmres_S", "gmres_A", "assemble_elem"),
+              key=lambda k: prof_host[k]["ms"] if k in roof_k else -1.0)
+    roof = dict(roof_k[top])
+    roof["dominant_by_replay_ms"] = {k: prof_host[k]["ms"] for k in ("gmres_S", "gmres_A", "assemble_elem",
+                                                                     "assemble_res", "gather", "schur_hat")}
+
     kclass = {k: {"ms": v["ms"], "launches": v["launches"],
                   "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None)}
               for k, v in prof_host.items()}
+    sweep = None if args.no_sweep else nu_sweep(ctx, H, torch, stream, args, names, sizes, dev, state, sprec_kw,
+                                                graph)
     H.hyel_destroy(ctx)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_sample(args=args)
+        cpu.update(cpu_plan(args))
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -456,7 +634,7 @@ def run_hyel(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64 outer / f32 levels",
                                              "bf16s": "f64 outer / f32 levels, bf16 A"}[args.precision], "data": "synthetic (seeded jittered cube, no dataset)",
             "config": config_dict(args, mesh), "clocks": ck, "e2e": e2e, "gpu_launches": launches,
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_kernels": roof_k, "cpu_baseline": cpu, "nu_sweep": sweep,
             "newton_solves": its, "solve_ms_per_newton_it": solve_ms, "assembly_ms_per_step": asm_ms,
             "mixed_fp32_preconditioner": mixed, "mixed_bf16s_preconditioner": mixed16,
             "kernel_classes_host_replay": kclass}

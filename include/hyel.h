@@ -468,10 +468,13 @@ int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solv
  * launch per S-solve, its inner A-solves included); their algorithmic bytes
  * are counted on the device per iteration (the operator's values and indices
  * plus the passes over the Krylov vectors) and added when the solve returns.
- * HYEL_K_SCHUR_HAT times the numeric S^ and its Ritz interval together. */
+ * HYEL_K_SCHUR_HAT times the numeric S^ and its Ritz interval together.
+ * HYEL_K_ASSEMBLE is the element pass with the tangent (Appendix A residual
+ * and blocks), HYEL_K_ASSEMBLE_RES the residual-only element pass (Newton's
+ * stopping test). */
 enum { HYEL_K_SPMV_A64 = 0, HYEL_K_SPMV_A32 = 1, HYEL_K_SPMV_FULL64 = 2,
        HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_SPMV_A16 = 5, HYEL_K_GMRES_A = 6,
-       HYEL_K_GMRES_S = 7, HYEL_K_SCHUR_HAT = 8, HYEL_K_NCLASSES = 9 };
+       HYEL_K_GMRES_S = 7, HYEL_K_SCHUR_HAT = 8, HYEL_K_ASSEMBLE_RES = 9, HYEL_K_NCLASSES = 10 };
 
 /* enable != 0 starts event timing of the kernel classes (and clears the
  * totals); 0 stops it. */
@@ -504,6 +507,17 @@ int hyel_set_wait_limit(hyel_ctx *ctx, double seconds);
  * faults the device or waits without a bound. Synchronizes. */
 enum { HYEL_FAULT_NONE = 0, HYEL_FAULT_BARRIER_SKIP = 1 };
 int hyel_inject_fault(hyel_ctx *ctx, int kind);
+
+/* A measurement aid (the paper has no counterpart): one launch of a
+ * compute-only kernel of independent FP64 FMA chains (no memory traffic in
+ * its loop), 8 blocks of 256 threads per SM, each thread 8 chains of `iters`
+ * FMAs (1 <= iters <= 2^24; HYEL_EINVAL otherwise). The caller times the
+ * launch on the context's stream; *flops_out (host, or NULL) receives the
+ * launch's FP64 flop count (2 per FMA), so that flops / time is the device's
+ * FP64 FMA rate, the peak of the FP64-bound element kernel. sink: device [1]
+ * double, never written in practice (it keeps the chains alive). Stream-
+ * ordered, no synchronization. */
+int hyel_fp64_fma_probe(hyel_ctx *ctx, int64_t iters, double *sink, double *flops_out);
 
 /* Number of kernel launches this library has issued in the process so far
  * (all contexts). count: host. */

@@ -502,6 +502,13 @@ int hyel_inject_fault(hyel_ctx *ctx, int kind) {
     });
 }
 
+int hyel_fp64_fma_probe(hyel_ctx *ctx, int64_t iters, double *sink, double *flops_out) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        const double f = hyel::fp64_fma_probe(c, iters, sink);
+        if (flops_out) *flops_out = f;
+    });
+}
+
 int hyel_launch_count(int64_t *count) {
     if (!count) return HYEL_EINVAL;
     *count = (int64_t)hyel::g_launches.load(std::memory_order_relaxed);

@@ -639,7 +639,8 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     a.err = c.err;
     HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
     cudaEvent_t ev;
-    prof_begin(c, HYEL_K_ASSEMBLE, &ev);
+    const int cls = tangent ? HYEL_K_ASSEMBLE : HYEL_K_ASSEMBLE_RES;
+    prof_begin(c, cls, &ev);
     if (!tangent)
         (k_element<false, false><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
     else if (a.corr)
@@ -648,7 +649,8 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
         (k_element<true, false><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());
     HYEL_CK(cudaGetLastError());
     // algorithmic bytes: element geometry+material (18 doubles), 4 nodes x 17 state doubles, staging writes
-    prof_end(c, HYEL_K_ASSEMBLE, ev, (double)m.E * (8.0 * 18 + 16 + 4 * 8.0 * 17 + 8.0 * kRecords * kRecordDoubles));
+    prof_end(c, cls, ev,
+             (double)m.E * (8.0 * 18 + 16 + 4 * 8.0 * 17 + 8.0 * (tangent ? kRecords : 1) * kRecordDoubles));
 
     if (tangent) {
         GatherArgs g;

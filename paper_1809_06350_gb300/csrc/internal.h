@@ -328,6 +328,9 @@ void adjoint_step(Ctx &c, const hyel_time_params &tp, const hyel_solver_params &
                   hyel_solve_stats *stats);
 void update_material(Ctx &c, const hyel_material *mat);
 
+// probe.cu: launches the FP64 FMA probe; returns the flops of the launch
+double fp64_fma_probe(Ctx &c, int64_t iters, double *sink);
+
 // noalloc.cu
 void residual_norm_static(Ctx &c, int matrix, const double *x, const double *b, double *out);
 

@@ -29,10 +29,10 @@ HYEL_INNER_GMRES, HYEL_INNER_CG_SYM = 0, 1
 HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D, HYEL_OP_AM, HYEL_OP_SHAT = 0, 1, 2, 3, 4, 5, 6
 HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32, HYEL_MAT_TRANSPOSED, HYEL_MAT_SCALED_BF16S = 0, 1, 2, 3, 4
 (HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER, HYEL_K_SPMV_A16,
- HYEL_K_GMRES_A, HYEL_K_GMRES_S, HYEL_K_SCHUR_HAT) = range(9)
-HYEL_K_NCLASSES = 9
+ HYEL_K_GMRES_A, HYEL_K_GMRES_S, HYEL_K_SCHUR_HAT, HYEL_K_ASSEMBLE_RES) = range(10)
+HYEL_K_NCLASSES = 10
 K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather", "spmv_A16", "gmres_A", "gmres_S",
-           "schur_hat"]
+           "schur_hat", "assemble_res"]
 
 # every symbol include/hyel.h declares
 EXPORTS = [
@@ -43,6 +43,7 @@ EXPORTS = [
     "hyel_solve_nested_transpose", "hyel_param_sensitivity", "hyel_adjoint_step",
     "hyel_schur_hat_setup", "hyel_schur_hat_cheb", "hyel_block_precond_apply", "hyel_a_cheb_setup",
     "hyel_a_cheb_apply", "hyel_set_wait_limit", "hyel_inject_fault",
+    "hyel_fp64_fma_probe",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -157,6 +158,7 @@ def lib():
                                                    C.POINTER(HyelSolveStats)]),
             "hyel_set_wait_limit": (C.c_int, [vp, C.c_double]),
             "hyel_inject_fault": (C.c_int, [vp, C.c_int]),
+            "hyel_fp64_fma_probe": (C.c_int, [vp, C.c_int64, vp, _dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -348,6 +350,13 @@ def hyel_set_wait_limit(ctx, seconds):
 
 def hyel_inject_fault(ctx, kind):
     return _check(ctx, lib().hyel_inject_fault(ctx, int(kind)))
+
+
+def hyel_fp64_fma_probe(ctx, iters, sink_ptr):
+    """Launches the FP64 FMA probe on the context's stream; returns its flops."""
+    f = C.c_double()
+    _check(ctx, lib().hyel_fp64_fma_probe(ctx, int(iters), C.c_void_p(sink_ptr), C.byref(f)))
+    return f.value
 
 
 def hyel_launch_count():

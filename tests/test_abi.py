@@ -22,7 +22,7 @@ def libpath():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(hyel_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(hyel_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_and_binding_list_agree():

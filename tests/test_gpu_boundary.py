@@ -6,7 +6,7 @@
   hyel_block_precond_apply, each with y one element past x; adjacent,
   non-overlapping ranges are accepted;
 * hyel_assemble's HYEL_RES pass gives the residual and norms of the full
-  pass and leaves the stored blocks untouched; a right-hand side needs
+  pass (to rounding) and leaves the stored blocks untouched; a right-hand side needs
   HYEL_TAN; other flag values are rejected;
 * a call leaves the host thread's current device where it was.
 """
@@ -101,8 +101,11 @@ def test_residual_only_pass(cube):
         assert np.array_equal(a, b)
     res_full2 = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
     n_full2 = H.hyel_assemble(gp.ctx, tp, sst2, res_full2.data_ptr(), 0, flags=H.HYEL_RES | H.HYEL_TAN)
-    assert torch.equal(res_only, res_full2)
-    assert n_only == n_full2
+    # the same formulas in two instantiations of the element kernel: equal up
+    # to the compiler's contraction of multiply-adds
+    scale = torch.max(torch.abs(res_full2)).item()
+    assert torch.max(torch.abs(res_only - res_full2)).item() <= 1e-13 * scale
+    assert n_only == pytest.approx(n_full2, rel=1e-13)
     assert not torch.equal(res_full, res_full2) and n_full != n_only
     H.hyel_assemble(gp.ctx, tp, sst2, 0, 0, flags=H.HYEL_TAN)
     rhs = torch.zeros(4 * N, dtype=torch.float64, device="cuda")

@@ -9,8 +9,10 @@
   for the nested solve in graph and host-driven modes (the fault hits the
   first intermediate A-solve; FGMRES carries on and the solve reports
   HYEL_ECUDA);
-* a node that belongs to no tetrahedron gives a zero 3x3 diagonal block of A:
-  hyel_solve_setup and hyel_solve_nested return HYEL_ESINGULAR;
+* a material whose density and shear modulus vanish (1e-300) gives 3x3
+  diagonal blocks of A with no representable determinant: hyel_solve_setup
+  and hyel_solve_nested return HYEL_ESINGULAR (a node in no element, the
+  other way to a zero block, is refused at upload);
 * argument checks of the two failure-detection entry points.
 """
 import time
@@ -109,11 +111,14 @@ def test_withdrawn_injection_and_arguments(cube):
     assert ei.value.code == H.HYEL_EINVAL
 
 
-def test_node_in_no_element_is_singular():
+def test_vanishing_velocity_block_is_singular():
+    """rho0 and mu at 1e-300 (both must be > 0 at upload): the mass and
+    stiffness parts of A, and with them every 3x3 diagonal block, fall below
+    the range of a double's determinant; kappa stays 1e6, so the pressure
+    rows stay regular."""
     m = inputs.cube_mesh(3)
-    m = dict(m)
-    m["X"] = np.vstack([m["X"], [[2.0, 2.0, 2.0]]])  # referenced by no tetrahedron, not constrained
-    gp = GpuProblem(m, inputs.material_nh(1e5, 1e6, 1e3), load={"p_max": 2e4, "t_ramp": DT}, with_oracle=False)
+    gp = GpuProblem(m, inputs.material_nh(1e-300, 1e6, 1e-300), load={"p_max": 0.0, "t_ramp": DT},
+                    with_oracle=False)
     N = gp.N
     dev, sst = gp.stage(inputs.zero_state(N))
     rhs = torch.zeros(4 * N, dtype=torch.float64, device="cuda")

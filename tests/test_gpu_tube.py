@@ -22,8 +22,12 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("precision", [H.HYEL_PREC_FP64, H.HYEL_PREC_FP32])
-def test_small_tube_newton_steps_match_oracle(precision):
+@pytest.mark.parametrize("precision,bench_opts", [(H.HYEL_PREC_FP64, False), (H.HYEL_PREC_FP32, False),
+                                                  (H.HYEL_PREC_FP64, True), (H.HYEL_PREC_FP32, True),
+                                                  (H.HYEL_PREC_BF16S, True)])
+def test_small_tube_newton_steps_match_oracle(precision, bench_opts):
+    """bench_opts: the timed benchmark's solver options (CUDA graph, degree-8
+    Chebyshev polynomial in the explicit S^ as the S-preconditioner)."""
     m = inputs.tube_mesh(3, 24, 6)
     mat = inputs.material_hgo(3e4, 2e5, 5.0, 0.0)
     load = {"p_max": 0.0, "t_ramp": 10 * DT}
@@ -32,7 +36,8 @@ def test_small_tube_newton_steps_match_oracle(precision):
     z = inputs.zero_state(N)
     dev = {k: gp.dev(z[k]) for k in z}
     state = H.state_struct(dev["u"], dev["p"], dev["v"], dev["udot"], dev["pdot"], dev["vdot"])
-    sp_ = H.solver_params(outer_rtol=1e-13, precision=precision)
+    kw = {"graph": 1, "s_precond": H.HYEL_SPREC_CHEB, "s_cheb_degree": 8} if bench_opts else {}
+    sp_ = H.solver_params(outer_rtol=1e-13, precision=precision, **kw)
     yn = {k: z[k] for k in ("u", "p", "v")}
     ydn = {k: z[k] for k in ("udot", "pdot", "vdot")}
     for step in range(2):
