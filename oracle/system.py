@@ -286,13 +286,21 @@ def block_jacobi_inverse(K, N):
 
 
 def direct_solve(K, rhs):
-    """Direct solve of the assembled system: dense LAPACK LU for small systems,
-    SuperLU otherwise (library primitives)."""
+    """Direct solve of the assembled system, x = W (W K W)^-1 W rhs with the
+    symmetric diagonal scaling W of §4.1 (it leaves x unchanged in exact
+    arithmetic): dense LAPACK LU for small systems, SuperLU otherwise (library
+    primitives). Without the scaling the velocity and pressure rows differ by
+    about ten orders of magnitude and the LU loses digits in the pressure (a
+    1e-16 relative change of the entries moved the unscaled solution of a
+    16^3-hex cube by 2e-9; the scaled one by 5e-16)."""
     n = K.shape[0]
+    w = diag_scaling(K)
+    Ks = (sp.diags(w) @ K @ sp.diags(w))
+    b = w * rhs
     if n <= 4000:
-        return np.linalg.solve(K.toarray(), rhs)
-    lu = spla.splu(K.tocsc(), permc_spec="COLAMD")
-    return lu.solve(rhs)
+        return w * np.linalg.solve(Ks.toarray(), b)
+    lu = spla.splu(Ks.tocsc(), permc_spec="COLAMD")
+    return w * lu.solve(b)
 
 
 BLOCK_KINDS = ("LDU", "DU", "D", "SIMPLE")

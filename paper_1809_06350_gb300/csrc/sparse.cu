@@ -247,7 +247,24 @@ __global__ void k_transpose(const int32_t *__restrict__ col_slice, const int32_t
     Dt[b * 32 + t] = D[mb * 32 + mt];
 }
 
-template <typename T>
+// A-block SpMVs, L lanes per block row: a warp covers 32 / L consecutive
+// rows of one 32-row slice, and lane k of a row takes the row's blocks
+// j = k, k + L, k + 2L, ...; the L partial sums meet by shuffles. For a given
+// j the L lanes of a component read L runs of 32 / L consecutive slots, whole
+// 32-byte sectors; L times more warps than one thread per row keep enough
+// loads in flight to stream the block values (a 117,649-node matrix has only
+// 3,677 slices).
+template <int L, typename T>
+__device__ __forceinline__ void lanes_reduce3(T &a0, T &a1, T &a2) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+}
+
+template <typename T, int L>
 __global__ void __launch_bounds__(128) k_spmv_A(const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ row_len,
                                                 const int32_t *__restrict__ col, const T *__restrict__ A,
                                                 const T *__restrict__ x, T *__restrict__ y, int64_t N,
@@ -258,14 +275,17 @@ __global__ void __launch_bounds__(128) k_spmv_A(const int32_t *__restrict__ slic
         if (kd[1]) return;
         y += (int64_t)(kd[0] + 1) * ystride;
     }
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= N) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = g / L;
+    const int k = (int)(g % L);
+    // rows past N (the last slice may be short) stay for the shuffles with no blocks
+    const bool live = r < N;
     const int t = (int)(r & 31);
-    const int64_t b0 = slice_ptr[r >> 5];
-    const int len = row_len[r];
+    const int64_t b0 = live ? slice_ptr[r >> 5] : 0;
+    const int len = live ? row_len[r] : 0;
     T a0 = 0, a1 = 0, a2 = 0;
-#pragma unroll 4
-    for (int j = 0; j < len; j++) {
+#pragma unroll 2
+    for (int j = k; j < len; j += L) {
         const int64_t b = b0 + j;
         const int64_t c = __ldg(col + b * 32 + t);
         const T *Ab = A + b * 288 + t;
@@ -280,15 +300,19 @@ __global__ void __launch_bounds__(128) k_spmv_A(const int32_t *__restrict__ slic
         a2 = fma(__ldg(Ab + 224), x1, a2);
         a2 = fma(__ldg(Ab + 256), x2, a2);
     }
-    y[3 * r] = a0;
-    y[3 * r + 1] = a1;
-    y[3 * r + 2] = a2;
+    lanes_reduce3<L>(a0, a1, a2);
+    if (live && k == 0) {
+        y[3 * r] = a0;
+        y[3 * r + 1] = a1;
+        y[3 * r + 2] = a2;
+    }
 }
 
 // A-SpMV on the BF16-with-block-scale copy, FP32 accumulation: per block,
 // t_i = sum_j e_ij x_j, y_i += s t_i. Entry 2k of a block sits in the low half
 // of word k of its 16-byte record, entry 2k+1 in the high half; a BF16 value
-// widens to FP32 by a 16-bit shift.
+// widens to FP32 by a 16-bit shift. L lanes per row as above.
+template <int L>
 __global__ void __launch_bounds__(128) k_spmv_A16(const int32_t *__restrict__ slice_ptr,
                                                   const int32_t *__restrict__ row_len, const int32_t *__restrict__ col,
                                                   const uint4 *__restrict__ Ah8, const uint16_t *__restrict__ Ah1,
@@ -298,14 +322,16 @@ __global__ void __launch_bounds__(128) k_spmv_A16(const int32_t *__restrict__ sl
         if (kd[1]) return;
         y += (int64_t)(kd[0] + 1) * ystride;
     }
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= N) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = g / L;
+    const int k = (int)(g % L);
+    const bool live = r < N;
     const int t = (int)(r & 31);
-    const int64_t b0 = slice_ptr[r >> 5];
-    const int len = row_len[r];
+    const int64_t b0 = live ? slice_ptr[r >> 5] : 0;
+    const int len = live ? row_len[r] : 0;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll 4
-    for (int j = 0; j < len; j++) {
+#pragma unroll 2
+    for (int j = k; j < len; j += L) {
         const int64_t q = (b0 + j) * 32 + t;
         const int64_t c = __ldg(col + q);
         const uint4 w = __ldg(Ah8 + q);
@@ -325,9 +351,12 @@ __global__ void __launch_bounds__(128) k_spmv_A16(const int32_t *__restrict__ sl
         a1 = fmaf(s, t1, a1);
         a2 = fmaf(s, t2, a2);
     }
-    y[3 * r] = a0;
-    y[3 * r + 1] = a1;
-    y[3 * r + 2] = a2;
+    lanes_reduce3<L>(a0, a1, a2);
+    if (live && k == 0) {
+        y[3 * r] = a0;
+        y[3 * r + 1] = a1;
+        y[3 * r + 2] = a2;
+    }
 }
 
 __global__ void __launch_bounds__(128) k_spmv_full64(const int32_t *__restrict__ slice_ptr,
@@ -638,10 +667,11 @@ void spmv_A_ind(Ctx &c, const T *Av, const T *x, T *y, int64_t ystride, const in
     const int cls = sizeof(T) == 8 ? HYEL_K_SPMV_A64 : HYEL_K_SPMV_A32;
     cudaEvent_t ev;
     prof_begin(c, cls, &ev);
-    // one-warp blocks: with one thread per row the grid is too small to fill
-    // the SMs, and single-slice blocks spread it evenly over them
-    (k_spmv_A<T><<<blocks_for(m.N, 32), 32, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, kd,
-                                                            ystride), ::hyel::count_launch());
+    // L lanes per row: 2 in FP64 (the FP64 pipe, not the load rate, is the
+    // limit there), 4 in FP32; 128-thread blocks cover 128 / L rows
+    constexpr int L = sizeof(T) == 8 ? 2 : 4;
+    (k_spmv_A<T, L><<<blocks_for(L * m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, kd,
+                                                                     ystride), ::hyel::count_launch());
     // algorithmic bytes: 9 values + 1 column index per block, x and y once
     prof_end(c, cls, ev, (double)m.nnzb * (9.0 * sizeof(T) + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * sizeof(T));
 }
@@ -659,8 +689,8 @@ void spmv_A16_ind(Ctx &c, const uint4 *h8, const uint16_t *h1, const float *hs, 
     const DeviceMesh &m = c.mesh;
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_SPMV_A16, &ev);
-    (k_spmv_A16<<<blocks_for(m.N, 32), 32, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, h8, h1, hs, x, y, m.N, kd,
-                                                            ystride), ::hyel::count_launch());
+    (k_spmv_A16<4><<<blocks_for(4 * m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, h8, h1, hs, x, y,
+                                                                     m.N, kd, ystride), ::hyel::count_launch());
     // algorithmic bytes: 9 BF16 values + 1 FP32 scale + 1 column index per block, x and y once
     prof_end(c, HYEL_K_SPMV_A16, ev, (double)m.nnzb * (18.0 + 4.0 + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * 4);
 }

@@ -5,11 +5,11 @@ persistent kernels' cooperative grid owns rows:
 * 16^3 hexes (4,913 nodes, n = 19,652) and 24^3 hexes (15,625 nodes,
   n = 62,500; 489 SELL-32 slices for a grid of at most 304 blocks): the
   linear update of one Newton system at a random state with non-zero rates
-  against SuperLU, outer tolerance 1e-14, relative error <= 1e-9 (the
+  against SuperLU, outer tolerance 1e-13, relative error <= 1e-9 (the
   "1e-9 at linear relative residual 1e-10" reading: the parity run solves
-  tighter so that the bar measures the method, not the stopping rule; the
-  forward error is about cond(A*) times the relative residual, and at these
-  sizes 1e-13 already gives 1.6e-9 to 1.8e-9 in FP64);
+  tighter so that the bar measures the method, not the stopping rule). The
+  oracle's LU runs on the §4.1-scaled system: unscaled, its own pressure
+  digits were off by 1.7e-9 at 16^3;
 * 16^3: two Newton steps of the ramped cube from rest against the oracle's
   direct-solve Newton steps, 1e-9 relative on every state field and the same
   number of corrections.
@@ -35,7 +35,7 @@ DT = 1e-3
 PRECISIONS = (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32, H.HYEL_PREC_BF16S)
 
 
-def _bench_params(precision, outer_rtol=1e-14):
+def _bench_params(precision, outer_rtol=1e-13):
     return H.solver_params(outer_rtol=outer_rtol, sub_rtol=1e-2, precision=precision, graph=1,
                            s_precond=H.HYEL_SPREC_CHEB, s_cheb_degree=8, a_precond=H.HYEL_APREC_BJACOBI,
                            block_precond=H.HYEL_BLOCK_LDU, inner_solver=H.HYEL_INNER_GMRES)
