@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the Poisson-ratio sweep keys")
+    p.add_argument("--no-tube", action="store_true", help="skip the full-size tube (config 3) step")
     p.add_argument("--host-loops", action="store_true",
                    help="drive the Krylov loops from the host (for per-kernel ncu launch lists)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16s"],
@@ -345,6 +346,44 @@ def nu_sweep(ctx, H, torch, stream, args, names, sizes, dev, state, sprec_kw, gr
     return out
 
 
+def tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=1e-5):
+    """Config 3 at full size: the thick-walled HGO tube (10 x 200 x 100 hexes,
+    1.2M tets, 222,200 nodes, fully incompressible, fibres at +-40 degrees),
+    the first time step of the 20 % stretch ramp (10 steps) from rest at the
+    paper's small HGO time step dt = 1e-5, FP64 and FP32 levels: one untimed
+    step (builds the workspaces and graphs), then the same step from rest
+    timed with CUDA events on the library's stream."""
+    from paper_1809_06350_gb300 import inputs
+    m = inputs.tube_mesh()
+    mat = inputs.material_hgo(3e4, 2e5, 5.0, 0.0)
+    inp = H.MeshInputs(m, mat, None, {"p_max": 0.0, "t_ramp": 10 * dt})
+    H.hyel_mesh_upload(ctx, inp.X, inp.tets, inp.bc, inp.mat)
+    N = m["X"].shape[0]
+    z = {k: torch.zeros(3 * N if k in ("u", "v", "udot", "vdot") else N, dtype=torch.float64, device="cuda")
+         for k in ("u", "p", "v", "udot", "pdot", "vdot")}
+    state = H.state_struct(z["u"], z["p"], z["v"], z["udot"], z["pdot"], z["vdot"])
+    out = {"workload": f"tube 10x200x100 HGO (N={N}, E={m['tets'].shape[0]}, n={4 * N}), dt={dt:g}, "
+                       "first step of a 10-step stretch ramp to 20 %, from rest"}
+    for lab, prec in (("fp64", H.HYEL_PREC_FP64), ("fp32", H.HYEL_PREC_FP32)):
+        sp = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=prec, graph=graph, **sprec_kw)
+        tp = H.time_params(dt=dt, t_n=0.0, l_max=8)
+        for rep in range(2):
+            for t in z.values():
+                t.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, rc = H.hyel_newton_step(ctx, tp, sp, state, raise_on_error=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        out[lab] = {"ms_per_step": e0.elapsed_time(e1), "newton_its": st.iterations, "converged": bool(st.converged),
+                    "rel_residual": st.res_norm / st.res_norm0 if st.res_norm0 else None, "outer_its": st.outer_its,
+                    "a_its": st.a_its, "s_its": st.s_its, "inner_its": st.inner_its, "status": rc,
+                    "unknowns_solves_per_s": 4 * N * st.iterations / (e0.elapsed_time(e1) * 1e-3)}
+    return out
+
+
 def run_hyel(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -626,6 +665,7 @@ def run_hyel(args, rank, world, local_rank):
               for k, v in prof_host.items()}
     sweep = None if args.no_sweep else nu_sweep(ctx, H, torch, stream, args, names, sizes, dev, state, sprec_kw,
                                                 graph)
+    tube = None if args.no_tube else tube_step(ctx, H, torch, stream, graph, sprec_kw)
     H.hyel_destroy(ctx)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -639,6 +679,7 @@ def run_hyel(args, rank, world, local_rank):
                                              "bf16s": "f64 outer / f32 levels, bf16 A"}[args.precision], "data": "synthetic (seeded jittered cube, no dataset)",
             "config": config_dict(args, mesh), "clocks": ck, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "roofline_kernels": roof_k, "cpu_baseline": cpu, "nu_sweep": sweep,
+            "config3_tube": tube,
             "newton_solves": its, "solve_ms_per_newton_it": solve_ms, "assembly_ms_per_step": asm_ms,
             "mixed_fp32_preconditioner": mixed, "mixed_bf16s_preconditioner": mixed16,
             "kernel_classes_host_replay": kclass}
