@@ -470,11 +470,14 @@ int hyel_adjoint_step(hyel_ctx *ctx, const hyel_time_params *tp, const hyel_solv
  * plus the passes over the Krylov vectors) and added when the solve returns.
  * HYEL_K_SCHUR_HAT times the numeric S^ and its Ritz interval together.
  * HYEL_K_ASSEMBLE is the element pass with the tangent (Appendix A residual
- * and blocks), HYEL_K_ASSEMBLE_RES the residual-only element pass (Newton's
- * stopping test). */
+ * and blocks), HYEL_K_ASSEMBLE_CORR the same pass that also forms the
+ * K_{.,udot} R_k right-hand-side terms (the first correction of a step), and
+ * HYEL_K_ASSEMBLE_RES the residual-only element pass (Newton's stopping
+ * test). */
 enum { HYEL_K_SPMV_A64 = 0, HYEL_K_SPMV_A32 = 1, HYEL_K_SPMV_FULL64 = 2,
        HYEL_K_ASSEMBLE = 3, HYEL_K_GATHER = 4, HYEL_K_SPMV_A16 = 5, HYEL_K_GMRES_A = 6,
-       HYEL_K_GMRES_S = 7, HYEL_K_SCHUR_HAT = 8, HYEL_K_ASSEMBLE_RES = 9, HYEL_K_NCLASSES = 10 };
+       HYEL_K_GMRES_S = 7, HYEL_K_SCHUR_HAT = 8, HYEL_K_ASSEMBLE_RES = 9, HYEL_K_ASSEMBLE_CORR = 10,
+       HYEL_K_NCLASSES = 11 };
 
 /* enable != 0 starts event timing of the kernel classes (and clears the
  * totals); 0 stops it. */

@@ -639,7 +639,7 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     a.err = c.err;
     HYEL_CK(cudaMemsetAsync(c.err, 0, sizeof(unsigned), c.stream));
     cudaEvent_t ev;
-    const int cls = tangent ? HYEL_K_ASSEMBLE : HYEL_K_ASSEMBLE_RES;
+    const int cls = !tangent ? HYEL_K_ASSEMBLE_RES : a.corr ? HYEL_K_ASSEMBLE_CORR : HYEL_K_ASSEMBLE;
     prof_begin(c, cls, &ev);
     if (!tangent)
         (k_element<false, false><<<blocks_for(m.E, 128), 128, 0, c.stream>>>(a), ::hyel::count_launch());

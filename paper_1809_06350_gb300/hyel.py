@@ -29,10 +29,10 @@ HYEL_INNER_GMRES, HYEL_INNER_CG_SYM = 0, 1
 HYEL_OP_FULL, HYEL_OP_A, HYEL_OP_B, HYEL_OP_C, HYEL_OP_D, HYEL_OP_AM, HYEL_OP_SHAT = 0, 1, 2, 3, 4, 5, 6
 HYEL_MAT_ASSEMBLED, HYEL_MAT_SCALED64, HYEL_MAT_SCALED32, HYEL_MAT_TRANSPOSED, HYEL_MAT_SCALED_BF16S = 0, 1, 2, 3, 4
 (HYEL_K_SPMV_A64, HYEL_K_SPMV_A32, HYEL_K_SPMV_FULL64, HYEL_K_ASSEMBLE, HYEL_K_GATHER, HYEL_K_SPMV_A16,
- HYEL_K_GMRES_A, HYEL_K_GMRES_S, HYEL_K_SCHUR_HAT, HYEL_K_ASSEMBLE_RES) = range(10)
-HYEL_K_NCLASSES = 10
+ HYEL_K_GMRES_A, HYEL_K_GMRES_S, HYEL_K_SCHUR_HAT, HYEL_K_ASSEMBLE_RES, HYEL_K_ASSEMBLE_CORR) = range(11)
+HYEL_K_NCLASSES = 11
 K_NAMES = ["spmv_A64", "spmv_A32", "spmv_full64", "assemble_elem", "gather", "spmv_A16", "gmres_A", "gmres_S",
-           "schur_hat", "assemble_res"]
+           "schur_hat", "assemble_res", "assemble_corr"]
 
 # every symbol include/hyel.h declares
 EXPORTS = [
