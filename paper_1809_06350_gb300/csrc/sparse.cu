@@ -251,9 +251,8 @@ __global__ void k_transpose(const int32_t *__restrict__ col_slice, const int32_t
 // rows of one 32-row slice, and lane k of a row takes the row's blocks
 // j = k, k + L, k + 2L, ...; the L partial sums meet by shuffles. For a given
 // j the L lanes of a component read L runs of 32 / L consecutive slots, whole
-// 32-byte sectors; L times more warps than one thread per row keep enough
-// loads in flight to stream the block values (a 117,649-node matrix has only
-// 3,677 slices).
+// 32-byte sectors; in FP32 twice the warps of one thread per row keep more
+// loads in flight (a 117,649-node matrix has only 3,677 slices).
 template <int L, typename T>
 __device__ __forceinline__ void lanes_reduce3(T &a0, T &a1, T &a2) {
 #pragma unroll
@@ -667,11 +666,17 @@ void spmv_A_ind(Ctx &c, const T *Av, const T *x, T *y, int64_t ystride, const in
     const int cls = sizeof(T) == 8 ? HYEL_K_SPMV_A64 : HYEL_K_SPMV_A32;
     cudaEvent_t ev;
     prof_begin(c, cls, &ev);
-    // L lanes per row: 2 in FP64 (the FP64 pipe, not the load rate, is the
-    // limit there), 4 in FP32; 128-thread blocks cover 128 / L rows
-    constexpr int L = sizeof(T) == 8 ? 2 : 4;
-    (k_spmv_A<T, L><<<blocks_for(L * m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, kd,
-                                                                     ystride), ::hyel::count_launch());
+    // FP64: one thread per row in one-warp blocks (the FP64 pipe, not the
+    // load rate, limits it; single-slice blocks spread the rows evenly over
+    // the SMs); FP32: two lanes per row in 128-thread blocks. Both were the
+    // fastest of a sweep over 1-8 lanes per row and 32-256 threads per block
+    // on the 48^3 cube's pattern.
+    if constexpr (sizeof(T) == 8)
+        (k_spmv_A<T, 1><<<blocks_for(m.N, 32), 32, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N, kd,
+                                                                   ystride), ::hyel::count_launch());
+    else
+        (k_spmv_A<T, 2><<<blocks_for(2 * m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, Av, x, y, m.N,
+                                                                         kd, ystride), ::hyel::count_launch());
     // algorithmic bytes: 9 values + 1 column index per block, x and y once
     prof_end(c, cls, ev, (double)m.nnzb * (9.0 * sizeof(T) + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * sizeof(T));
 }
@@ -689,7 +694,7 @@ void spmv_A16_ind(Ctx &c, const uint4 *h8, const uint16_t *h1, const float *hs, 
     const DeviceMesh &m = c.mesh;
     cudaEvent_t ev;
     prof_begin(c, HYEL_K_SPMV_A16, &ev);
-    (k_spmv_A16<4><<<blocks_for(4 * m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, h8, h1, hs, x, y,
+    (k_spmv_A16<2><<<blocks_for(2 * m.N, 128), 128, 0, c.stream>>>(m.slice_ptr, m.row_len, m.col, h8, h1, hs, x, y,
                                                                      m.N, kd, ystride), ::hyel::count_launch());
     // algorithmic bytes: 9 BF16 values + 1 FP32 scale + 1 column index per block, x and y once
     prof_end(c, HYEL_K_SPMV_A16, ev, (double)m.nnzb * (18.0 + 4.0 + 4.0) + 4.0 * (m.N + 1) + 2.0 * 3 * m.N * 4);
