@@ -529,23 +529,44 @@ def run_hyel(args, rank, world, local_rank):
 
     def spmv_timed(matrix, dtype, cls, reps=25):
         """The A-block SpMV of the scaled system timed alone: CUDA events on
-        the library's stream around each launch, L2 flushed before each."""
+        the library's stream around each launch, L2 flushed before each; and,
+        after the same flush, a plain streaming read of the same byte count
+        (hyel_stream_read_probe): the rate a kernel that reads that many bytes
+        once can reach."""
         x = torch.randn(3 * N, dtype=dtype, device="cuda")
         y = torch.empty(3 * N, dtype=dtype, device="cuda")
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         clean = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
-        H.hyel_profile(ctx, 1)
-        for _ in range(reps):
-            # L2 flush: write 256 MB, then read another 256 MB so that the
-            # flush's dirty lines are written back before the timed launch
+        src = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+        sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+        def l2_flush():
+            # write 256 MB, then read another 256 MB so that the flush's dirty
+            # lines are written back before the timed launch
             flush.zero_()
             clean.sum()
+
+        H.hyel_profile(ctx, 1)
+        for _ in range(reps):
+            l2_flush()
             H.hyel_spmv(ctx, H.HYEL_OP_A, matrix, x.data_ptr(), y.data_ptr())
         pr = H.hyel_profile_read(ctx)[cls]
         H.hyel_profile(ctx, 0)
         us = 1e3 * pr["ms"] / pr["launches"]
         by = pr["bytes"] / pr["launches"]
-        return by / (us * 1e-6) / 1e9, us, by
+        nb = int(by) // 16 * 16
+        tr = 0.0
+        for _ in range(reps):
+            l2_flush()
+            r0 = torch.cuda.Event(enable_timing=True)
+            r1 = torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            H.hyel_stream_read_probe(ctx, src.data_ptr(), nb, sink.data_ptr())
+            r1.record(stream)
+            torch.cuda.synchronize()
+            tr += r0.elapsed_time(r1)
+        read_gbs = nb / (tr / reps * 1e-3) / 1e9
+        return by / (us * 1e-6) / 1e9, us, by, read_gbs
 
     # per-launch CUDA events need host-launched kernels: replay the same K
     # steps with host-driven Krylov loops (same kernels, same order, same
@@ -577,9 +598,9 @@ def run_hyel(args, rank, world, local_rank):
     fp64_tflops = fp64_peak()
 
     H.hyel_solve_setup(ctx)
-    gbs64, us64, by64 = spmv_timed(H.HYEL_MAT_SCALED64, torch.float64, "spmv_A64")
-    gbs32, us32, by32 = spmv_timed(H.HYEL_MAT_SCALED32, torch.float32, "spmv_A32")
-    gbs16, us16, by16 = spmv_timed(H.HYEL_MAT_SCALED_BF16S, torch.float32, "spmv_A16")
+    gbs64, us64, by64, rd64 = spmv_timed(H.HYEL_MAT_SCALED64, torch.float64, "spmv_A64")
+    gbs32, us32, by32, rd32 = spmv_timed(H.HYEL_MAT_SCALED32, torch.float32, "spmv_A32")
+    gbs16, us16, by16, rd16 = spmv_timed(H.HYEL_MAT_SCALED_BF16S, torch.float32, "spmv_A16")
     tname = {"fp64": "<double>", "fp32": "<float>", "bf16s": "<float, bf16>"}[args.precision]
     kdesc = {"gmres_A": "k_gmres_a" + tname + " (persistent A-solve, one cooperative launch per intermediate "
                         "A-solve: SELL-32 SpMV of A M^-1, Gram-Schmidt, Givens, solution update)",
@@ -607,10 +628,14 @@ def run_hyel(args, rank, world, local_rank):
                               "5.1 TB/s",
             "alone_l2_flushed": {
                 "note": "one launch between two events after an L2 flush (256 MB written, then 256 MB of another buffer read, so that no dirty line of the flush is written back during the launch)",
-                "spmv_A64": {"achieved": gbs64, "frac": gbs64 / peak, "bytes_per_launch": by64, "avg_launch_us": us64},
-                "spmv_A32": {"achieved": gbs32, "frac": gbs32 / peak, "bytes_per_launch": by32, "avg_launch_us": us32},
+                "same_size_read": "read_gbs: hyel_stream_read_probe reading the same byte count after the same "
+                                  "flush; frac_of_same_size_read = achieved / read_gbs",
+                "spmv_A64": {"achieved": gbs64, "frac": gbs64 / peak, "bytes_per_launch": by64, "avg_launch_us": us64,
+                             "read_gbs": rd64, "frac_of_same_size_read": gbs64 / rd64},
+                "spmv_A32": {"achieved": gbs32, "frac": gbs32 / peak, "bytes_per_launch": by32, "avg_launch_us": us32,
+                             "read_gbs": rd32, "frac_of_same_size_read": gbs32 / rd32},
                 "spmv_A16": {"achieved": gbs16, "frac": gbs16 / peak, "bytes_per_launch": by16,
-                             "avg_launch_us": us16}}}
+                             "avg_launch_us": us16, "read_gbs": rd16, "frac_of_same_size_read": gbs16 / rd16}}}
     # the element pass: FP64-arithmetic bound (its FP64 instructions per tet
     # come from the committed ncu counters of the same source)
     E = int(mesh["tets"].shape[0])

@@ -522,6 +522,15 @@ int hyel_inject_fault(hyel_ctx *ctx, int kind);
  * ordered, no synchronization. */
 int hyel_fp64_fma_probe(hyel_ctx *ctx, int64_t iters, double *sink, double *flops_out);
 
+/* A measurement aid (the paper has no counterpart): one launch that reads
+ * `bytes` of the device buffer `buf` once with 16-byte loads (8 blocks of 256
+ * threads per SM, grid-stride), the plain streaming read of that size. Timed
+ * by the caller like the SpMVs, it gives the read rate a kernel reading that
+ * many bytes once can reach, launch ramp and tail included. bytes: a positive
+ * multiple of 16; buf: 16-byte aligned (HYEL_EINVAL otherwise). sink: device
+ * [1] double, never written in practice. Stream-ordered. */
+int hyel_stream_read_probe(hyel_ctx *ctx, const void *buf, int64_t bytes, double *sink);
+
 /* Number of kernel launches this library has issued in the process so far
  * (all contexts). count: host. */
 int hyel_launch_count(int64_t *count);

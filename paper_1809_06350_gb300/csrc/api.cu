@@ -509,6 +509,10 @@ int hyel_fp64_fma_probe(hyel_ctx *ctx, int64_t iters, double *sink, double *flop
     });
 }
 
+int hyel_stream_read_probe(hyel_ctx *ctx, const void *buf, int64_t bytes, double *sink) {
+    return guarded(ctx, [&](hyel::Ctx &c) { hyel::stream_read_probe(c, buf, bytes, sink); });
+}
+
 int hyel_launch_count(int64_t *count) {
     if (!count) return HYEL_EINVAL;
     *count = (int64_t)hyel::g_launches.load(std::memory_order_relaxed);

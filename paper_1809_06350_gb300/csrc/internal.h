@@ -330,6 +330,7 @@ void update_material(Ctx &c, const hyel_material *mat);
 
 // probe.cu: launches the FP64 FMA probe; returns the flops of the launch
 double fp64_fma_probe(Ctx &c, int64_t iters, double *sink);
+void stream_read_probe(Ctx &c, const void *buf, int64_t bytes, double *sink);
 
 // noalloc.cu
 void residual_norm_static(Ctx &c, int matrix, const double *x, const double *b, double *out);

@@ -1,3 +1,5 @@
+// Measurement aids (the paper has no counterpart):
+//
 // hyel_fp64_fma_probe: a compute-only kernel that measures the FP64 FMA rate
 // of the device it runs on, the denominator of the element kernel's roofline
 // (that kernel is bound by FP64 arithmetic, not by memory).
@@ -35,7 +37,27 @@ __global__ void __launch_bounds__(kProbeThreads) k_fp64_fma_probe(int64_t iters,
     if (s == 12345.678) sink[0] = s;
 }
 
+__global__ void __launch_bounds__(kProbeThreads) k_stream_read_probe(const uint4 *__restrict__ p, int64_t n16,
+                                                                    double *sink) {
+    unsigned acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldg(p + i);
+        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x9e3779b9u) sink[0] = (double)acc;  // keeps the loads; practically never taken
+}
+
 }  // namespace
+
+void stream_read_probe(Ctx &c, const void *buf, int64_t bytes, double *sink) {
+    if (!buf || !sink) fail(HYEL_EINVAL, "stream_read_probe: null pointer");
+    if (bytes < 16 || bytes % 16 != 0 || ((uintptr_t)buf & 15u))
+        fail(HYEL_EINVAL, "stream_read_probe: bytes must be a positive multiple of 16 and buf 16-byte aligned");
+    const int grid = kProbeBlocksPerSm * c.num_sms;
+    (k_stream_read_probe<<<grid, kProbeThreads, 0, c.stream>>>(static_cast<const uint4 *>(buf), bytes / 16, sink),
+     ::hyel::count_launch());
+    HYEL_CK(cudaGetLastError());
+}
 
 double fp64_fma_probe(Ctx &c, int64_t iters, double *sink) {
     if (iters < 1 || iters > (int64_t)1 << 24) fail(HYEL_EINVAL, "fp64_fma_probe: iters must be in [1, 2^24]");

@@ -43,7 +43,7 @@ EXPORTS = [
     "hyel_solve_nested_transpose", "hyel_param_sensitivity", "hyel_adjoint_step",
     "hyel_schur_hat_setup", "hyel_schur_hat_cheb", "hyel_block_precond_apply", "hyel_a_cheb_setup",
     "hyel_a_cheb_apply", "hyel_set_wait_limit", "hyel_inject_fault",
-    "hyel_fp64_fma_probe",
+    "hyel_fp64_fma_probe", "hyel_stream_read_probe",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -159,6 +159,7 @@ def lib():
             "hyel_set_wait_limit": (C.c_int, [vp, C.c_double]),
             "hyel_inject_fault": (C.c_int, [vp, C.c_int]),
             "hyel_fp64_fma_probe": (C.c_int, [vp, C.c_int64, vp, _dp]),
+            "hyel_stream_read_probe": (C.c_int, [vp, vp, C.c_int64, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -357,6 +358,10 @@ def hyel_fp64_fma_probe(ctx, iters, sink_ptr):
     f = C.c_double()
     _check(ctx, lib().hyel_fp64_fma_probe(ctx, int(iters), C.c_void_p(sink_ptr), C.byref(f)))
     return f.value
+
+
+def hyel_stream_read_probe(ctx, buf_ptr, nbytes, sink_ptr):
+    return _check(ctx, lib().hyel_stream_read_probe(ctx, C.c_void_p(buf_ptr), int(nbytes), C.c_void_p(sink_ptr)))
 
 
 def hyel_launch_count():
