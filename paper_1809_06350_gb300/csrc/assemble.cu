@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int I = 0; I < 3; I++) I1 += F[i][I] * F[i][I];
-    const double cJ = cbrt(J);
-    const double aJ = 1.0 / (cJ * cJ);  // J^{-2/3}
+    const double rJ = rcbrt(J);
+    const double aJ = rJ * rJ;  // J^{-2/3} (one reciprocal cube root: fewer FP64 steps than cbrt and a division)
 
     // velocity and pressure gradients
     double Lv[3][3];  // v_i,j
@@ -156,8 +156,10 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
         Sp += pq;
         double rho, beta, rhop, betap;
         if (a.vol == HYEL_VOL_GIBBS) {
-            const double s = sqrt(pq * pq + kappa * kappa);
-            beta = 1.0 / s;
+            // beta = 1 / sqrt(p^2 + kappa^2) by one reciprocal square root, s = (p^2 + kappa^2) beta
+            const double s2 = fma(pq, pq, kappa * kappa);
+            beta = rsqrt(s2);
+            const double s = s2 * beta;
             rho = rk0 * (pq + s);
             rhop = rho * beta;
             betap = -pq * beta * beta * beta;
@@ -351,11 +353,31 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
 #pragma unroll
         for (int j = 0; j < 3; j++) q3n[A][j] = q3 * n[A][j];
     const double c2jv4 = c2 * JV4;
-    double corr[4][4];
+    // K_{.,udot} R_k: A_u R_k and C_u R_k, A_u = dR_m/du (the A block less its
+    // mass part, over c2) and C_u = dR_p/du. Every part of A_u and C_u is a sum
+    // of rank-one node-pair terms, so the products with R_k contract over the
+    // second node once per element (s_n = sum_B n_B . R_B and the like) instead
+    // of once per pair: C_u R_k here, c2 A_u R_k after the pair loop (fewer
+    // values live through the loop).
+    double cu[4] = {0.0, 0.0, 0.0, 0.0};
+    if (CORR) {
+        double sn = 0.0, sL = 0.0, cbr[3] = {0.0, 0.0, 0.0}, ngp[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int A = 0; A < 4; A++)
+        for (int B = 0; B < 4; B++) {
+            const double gr = gp[0] * rk[B][0] + gp[1] * rk[B][1] + gp[2] * rk[B][2];
 #pragma unroll
-        for (int k = 0; k < 4; k++) corr[A][k] = 0.0;
+            for (int j = 0; j < 3; j++) {
+                sn = fma(n[B][j], rk[B][j], sn);
+                sL = fma(LvTn[B][j], rk[B][j], sL);
+                cbr[j] = fma(cB[B], rk[B][j], cbr[j]);
+                ngp[j] = fma(n[B][j], gr, ngp[j]);
+            }
+        }
+#pragma unroll
+        for (int A = 0; A < 4; A++)
+            cu[A] = fma(cA[A], sn, n[A][0] * cbr[0] + n[A][1] * cbr[1] + n[A][2] * cbr[2]) - JV4 * sL -
+                    tau * JV * (n[A][0] * ngp[0] + n[A][1] * ngp[1] + n[A][2] * ngp[2]);
+    }
 
 #pragma unroll 1
     for (int A = 0; A < 4; A++) {
@@ -400,37 +422,71 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
                 out[12 + j] = fma(cAs[A], n[B][j], fma(cBs[B], n[A][j], fma(-c2jv4, LvTn[B][j], -gpc[j] * nn)));
             out[15] = fma(c1tJV, nn, same ? ddw[A] : odw[A] + odw[B]) +
                       fma(n[A][0], qrc[B][0], fma(n[A][1], qrc[B][1], n[A][2] * qrc[B][2]));
-            if (CORR) {
-                // c2 A_u R_k (the A block less its mass part) and C_u R_k
-#pragma unroll
-                for (int i = 0; i < 3; i++) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int j = 0; j < 3; j++) s += (out[3 * i + j] - (i == j ? mass : 0.0)) * rk[B][j];
-                    corr[A][i] += s;
-                }
-                double sp = 0.0;
-#pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    const double Cu = cA[A] * n[B][j] + cB[B] * n[A][j] - JV4 * LvTn[B][j] - tau * JV * gp[j] * nn;
-                    sp += Cu * rk[B][j];
-                }
-                corr[A][3] += sp;
-            }
             double2 *rec = reinterpret_cast<double2 *>(record(a.stage, e, 4 * A + B));
 #pragma unroll
             for (int k = 0; k < 8; k++) rec[k] = make_double2(out[2 * k], out[2 * k + 1]);
         }
     }
     // A_u = dR_m/du and C_u = dR_p/du; since K_{.,udot} = c1 d(.)/du,
-    // (1/a_m) K_{.,udot} R_k = (c1/a_m) [A_u ; C_u] R_k. corr[.][0..2] holds
-    // c2 A_u R_k (c2 > 0 whenever the correction is formed: dt > 0).
+    // (1/a_m) K_{.,udot} R_k = (c1/a_m) [A_u ; C_u] R_k, c2 A_u R_k formed
+    // below (c2 > 0 whenever the correction is formed: dt > 0).
     double2 *rc = reinterpret_cast<double2 *>(record(a.stage, e, 17));
-    const double su = CORR ? c1 / (am * c2) : 0.0, sp = CORR ? c1 / am : 0.0;
+    if (CORR) {
+        double sn = 0.0, sf = 0.0, Gn[3][3], Rg[3][3];
 #pragma unroll
-    for (int A = 0; A < 4; A++) {
-        rc[2 * A] = make_double2(su * corr[A][0], su * corr[A][1]);
-        rc[2 * A + 1] = make_double2(su * corr[A][2], sp * corr[A][3]);
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) Gn[i][j] = Rg[i][j] = 0.0;
+#pragma unroll
+        for (int B = 0; B < 4; B++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                sn = fma(n[B][j], rk[B][j], sn);
+                sf = fma(f[B][j], rk[B][j], sf);
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    Gn[i][j] = fma(n[B][i], rk[B][j], Gn[i][j]);  // sum_B n_Bi R_Bj
+                    Rg[i][j] = fma(rk[B][i], g[B][j], Rg[i][j]);  // sum_B R_Bi g_Bj
+                }
+            }
+        double sfe[2] = {0.0, 0.0}, sfa[2] = {0.0, 0.0}, tfa[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        if (a.nfib) {
+#pragma unroll
+            for (int tf = 0; tf < 2; tf++)
+#pragma unroll
+                for (int B = 0; B < 4; B++) {
+                    const double far = fFa[tf][0] * rk[B][0] + fFa[tf][1] * rk[B][1] + fFa[tf][2] * rk[B][2];
+                    sfa[tf] = fma(fga[tf][B], far, sfa[tf]);
+#pragma unroll
+                    for (int i = 0; i < 3; i++) {
+                        sfe[tf] = fma(fE[tf][B][i], rk[B][i], sfe[tf]);
+                        tfa[tf][i] = fma(fga[tf][B], rk[B][i], tfa[tf][i]);
+                    }
+                }
+        }
+        const double su = c1 / (am * c2), sp = c1 / am;
+#pragma unroll
+        for (int A = 0; A < 4; A++) {
+            double cv[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const double gnA = Gn[i][0] * n[A][0] + Gn[i][1] * n[A][1] + Gn[i][2] * n[A][2];
+                const double rgA = Rg[i][0] * g[A][0] + Rg[i][1] * g[A][1] + Rg[i][2] * g[A][2];
+                double s = fma(Q1[A][i], sn, fma(Q2[A][i], sf, fma(q3, gnA, q4 * rgA)));
+                if (a.nfib) {
+#pragma unroll
+                    for (int tf = 0; tf < 2; tf++)
+                        s += w2c[tf] * fE[tf][A][i] * sfe[tf] + w1c[tf] * n[A][i] * (kd * sf + kd3 * sfa[tf]) +
+                             w0c[tf] * (kd * rgA + kd3 * fga[tf][A] * tfa[tf][i]);
+                }
+                cv[i] = su * s;
+            }
+            rc[2 * A] = make_double2(cv[0], cv[1]);
+            rc[2 * A + 1] = make_double2(cv[2], sp * cu[A]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; k++) rc[k] = make_double2(0.0, 0.0);
     }
 }
 
