@@ -124,3 +124,29 @@ def test_current_device_is_kept(cube):
     H.hyel_mesh_info(gp.ctx)
     H.hyel_solve_setup(gp.ctx)
     assert torch.cuda.current_device() == before
+
+
+def test_measurement_probes(cube):
+    """The FP64 FMA-chain probe reports its flop count and runs at a
+    plausible FP64 rate (0.1 to 3 TFLOP/s: GB300's nominal is 1.25); the
+    streaming-read probe checks its arguments."""
+    gp = cube["gp"]
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    H.hyel_fp64_fma_probe(gp.ctx, 16, sink.data_ptr())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    fl = H.hyel_fp64_fma_probe(gp.ctx, 1 << 12, sink.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(0)
+    assert fl == 2.0 * (1 << 12) * 8 * 256 * 8 * props.multi_processor_count
+    tflops = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    assert 0.1 < tflops < 3.0, tflops
+    assert sink.item() == 0.0
+    buf = torch.zeros(1 << 20, dtype=torch.float32, device="cuda")
+    H.hyel_stream_read_probe(gp.ctx, buf.data_ptr(), 4 << 20, sink.data_ptr())
+    torch.cuda.synchronize()
+    for bad in ((buf.data_ptr(), 15), (buf.data_ptr(), 0), (buf.data_ptr() + 4, 64)):
+        _einval(lambda: H.hyel_stream_read_probe(gp.ctx, bad[0], bad[1], sink.data_ptr()))
+    _einval(lambda: H.hyel_fp64_fma_probe(gp.ctx, 0, sink.data_ptr()))
