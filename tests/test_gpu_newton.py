@@ -91,3 +91,33 @@ def test_newton_iteration_cap_reports_noconv():
     st, rc = H.hyel_newton_step(gp.ctx, tp, H.solver_params(), state, raise_on_error=False)
     assert rc == H.HYEL_ENOCONV and st.iterations == 1 and not st.converged
     gp.close()
+
+
+def test_degenerate_meshes():
+    """A single tetrahedron with no Dirichlet data (one ragged 4-row slice;
+    A and S stay regular through the mass terms) takes a Newton step under a
+    traction load equal to the oracle's; with no load and a state at rest the
+    predictor is already converged (no correction)."""
+    X = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    m = {"X": X, "tets": np.array([[0, 1, 2, 3]], dtype=np.int32),
+         "traction_tris": np.array([[1, 2, 3]], dtype=np.int32), "traction_dir": np.array([1.0, 1.0, 1.0]),
+         "dirichlet": np.zeros((0, 2), dtype=np.int32), "dirichlet_values": np.zeros(0)}
+    mat = inputs.material_nh(1e5, 1e6, 1e3)
+    for p_max, expect_its in ((2e4, None), (0.0, 0)):
+        gp = GpuProblem(m, mat, load={"p_max": p_max, "t_ramp": DT})
+        prob, N = gp.prob, gp.N
+        z = inputs.zero_state(N)
+        dev = {k: gp.dev(z[k]) for k in z}
+        state = H.state_struct(dev["u"], dev["p"], dev["v"], dev["udot"], dev["pdot"], dev["vdot"])
+        tp = H.time_params(dt=DT, tol_r=1e-10, tol_a=1e-12)
+        st, rc = H.hyel_newton_step(gp.ctx, tp, H.solver_params(outer_rtol=1e-13), state)
+        y1, yd1, info = Nw.newton_step(prob, {k: z[k] for k in ("u", "p", "v")},
+                                       {k: z[k] for k in ("udot", "pdot", "vdot")}, 0.0, DT, tol_r=1e-10, tol_a=1e-12)
+        assert st.converged and info["converged"] and st.iterations == info["iterations"]
+        if expect_its is not None:
+            assert st.iterations == expect_its
+        else:
+            assert st.iterations >= 1
+        for k in ("u", "p", "v"):
+            assert _rel(dev[k].cpu().numpy().reshape(y1[k].shape), y1[k]) <= 1e-9, (p_max, k)
+        gp.close()
