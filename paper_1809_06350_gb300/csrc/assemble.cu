@@ -570,14 +570,24 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_residual(ResArgs a) {
-    __shared__ double sm[8][3];
+// Four lanes per node (kResLanes): lane k sums the node's element records
+// k, k + 4, ...; the four partial sums meet by shuffles in a fixed order, so
+// the result is the same on every run. (One thread per node left a chain of
+// about 24 dependent record loads per thread.)
+constexpr int kResLanes = 4;
+constexpr int kResThreads = 1024;  // 256 nodes per block
+
+__global__ void __launch_bounds__(kResThreads) k_residual(ResArgs a) {
+    __shared__ double sm[kResThreads / 32][3];
     __shared__ bool last;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = g / kResLanes;
+    const int lane = (int)(g % kResLanes);
+    const bool live = i < a.N;
     double sk = 0.0, sp = 0.0, sr = 0.0;
-    if (i < a.N) {
-        double R[4] = {0, 0, 0, 0}, G[4] = {0, 0, 0, 0};
-        for (int k = a.node_ptr[i]; k < a.node_ptr[i + 1]; k++) {
+    double R[4] = {0, 0, 0, 0}, G[4] = {0, 0, 0, 0};
+    if (live) {
+        for (int k = a.node_ptr[i] + lane; k < a.node_ptr[i + 1]; k += kResLanes) {
             const int ent = a.node_list[k];
             const int64_t e = ent >> 2;
             const int A = ent & 3;
@@ -589,6 +599,15 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
 #pragma unroll
                 for (int m = 0; m < 4; m++) G[m] += r17[m];
         }
+    }
+#pragma unroll
+    for (int o = 1; o < kResLanes; o <<= 1)
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            R[m] += __shfl_xor_sync(0xffffffffu, R[m], o);
+            G[m] += __shfl_xor_sync(0xffffffffu, G[m], o);
+        }
+    if (live && lane == 0) {
         const unsigned d = a.dir[i];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -743,12 +762,14 @@ void assemble(Ctx &c, const TimeConsts &tc, const hyel_state &st, double *res_ou
     r.literal = tc.literal;
     r.res_out = res_out;
     r.rhs_out = rhs_out;
-    int nb = blocks_for(m.N, 256);
+    // kResLanes lanes per node, 256 nodes per block: the partials of at most
+    // (65536 - 64) / 3 blocks fit the context's reduction buffer
+    int nb = blocks_for(m.N, kResThreads / kResLanes);
     r.partial = c.red + 64;
     r.counter = c.counter;
     r.norms = c.red;
     r.use_g = (rhs_out && !tc.literal) ? 1 : 0;
-    (k_residual<<<nb, 256, 0, c.stream>>>(r), ::hyel::count_launch());
+    (k_residual<<<nb, kResThreads, 0, c.stream>>>(r), ::hyel::count_launch());
     HYEL_CK(cudaGetLastError());
     if (tangent) {
         c.mat.assembled = true;

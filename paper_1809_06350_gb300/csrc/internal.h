@@ -108,6 +108,7 @@ struct DeviceMatrix {
     float *Amhs = nullptr;
     double *w = nullptr;        // [4N] scaling
     double *jac64 = nullptr;    // [9][N] inverses of scaled diagonal blocks of A
+    double *rdiag64 = nullptr;  // [3N] 1 / (scalar diagonal of the scaled A)
     float *jac32 = nullptr;
     double *shat64 = nullptr;   // [N] 1 / diag(S^) of the scaled system
     float *shat32 = nullptr;

@@ -324,6 +324,7 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     M.Amhs = dalloc_n<float>(c, ns);
     M.w = dalloc_n<double>(c, 4 * (size_t)N);
     M.jac64 = dalloc_n<double>(c, 9 * (size_t)N);
+    M.rdiag64 = dalloc_n<double>(c, 3 * (size_t)N);
     M.jac32 = dalloc_n<float>(c, 9 * (size_t)N);
     M.shat64 = dalloc_n<double>(c, (size_t)N);
     M.shat32 = dalloc_n<float>(c, (size_t)N);

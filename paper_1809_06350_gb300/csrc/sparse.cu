@@ -33,6 +33,7 @@ struct ScaleArgs {
     double *w;  // [4N]
     double *jac64;
     float *jac32;
+    double *rdiag64;  // [3N] 1 / A_ii[s][s]
     double *shat64;
     float *shat32;
     unsigned *err;
@@ -153,6 +154,9 @@ __global__ void k_jacobi(ScaleArgs a) {
             a.jac64[(3 * r + s) * a.N + i] = v;
             a.jac32[(3 * r + s) * a.N + i] = (float)v;
         }
+    // reciprocals of the scalar diagonal, for diag(S^) (k_schur_hat)
+#pragma unroll
+    for (int s = 0; s < 3; s++) a.rdiag64[3 * i + s] = 1.0 / m[s][s];
 }
 
 // A~ = A M^-1 block by block: A~_(r,c) = A_(r,c) M_c^-1, M_c^-1 the inverse of
@@ -192,7 +196,9 @@ __global__ void k_fold_jacobi(ScaleArgs a) {
     quant_block(v, q, a.Amh8, a.Amh1, a.Amhs);
 }
 
-// diag(S^)_i = D_ii - sum_c sum_s C_(i,c)[s] B_(c,i)[s] / A_(c,c)[s][s]  (scaled system)
+// diag(S^)_i = D_ii - sum_c sum_s C_(i,c)[s] B_(c,i)[s] / A_(c,c)[s][s]  (scaled system);
+// the reciprocals 1 / A_(c,c)[s][s] come from k_jacobi (one division per
+// node component instead of one per block entry)
 __global__ void k_schur_hat(ScaleArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.N) return;
@@ -204,12 +210,9 @@ __global__ void k_schur_hat(ScaleArgs a) {
         const int64_t b = b0 + j, q = b * 32 + t;
         const int64_t c = a.col[q];
         const int64_t mq = a.mirror[q], mb = mq >> 5, mt = mq & 31;
-        const int64_t dq = a.diag_slot[c], db = dq >> 5, dt = dq & 31;
 #pragma unroll
-        for (int s = 0; s < 3; s++) {
-            const double ad = a.As[(db * 9 + 4 * s) * 32 + dt];
-            acc += a.Cs[(b * 3 + s) * 32 + t] * a.Bs[(mb * 3 + s) * 32 + mt] / ad;
-        }
+        for (int s = 0; s < 3; s++)
+            acc += a.Cs[(b * 3 + s) * 32 + t] * a.Bs[(mb * 3 + s) * 32 + mt] * a.rdiag64[3 * c + s];
     }
     const int64_t dq = a.diag_slot[i], db = dq >> 5, dt = dq & 31;
     const double sh = a.Ds[db * 32 + dt] - acc;
@@ -526,6 +529,7 @@ ScaleArgs scale_args(Ctx &c) {
     a.Amhs = M.Amhs;
     a.w = M.w;
     a.jac64 = M.jac64;
+    a.rdiag64 = M.rdiag64;
     a.jac32 = M.jac32;
     a.shat64 = M.shat64;
     a.shat32 = M.shat32;
