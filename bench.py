@@ -678,8 +678,11 @@ def run_hyel(args, rank, world, local_rank):
     if po["launches"]:
         us_o = 1e3 * po["ms"] / po["launches"]
         by_o = po["bytes"] / po["launches"]
+        pn_o = "gmres_" + other[-1].lower() + ("_cheb" if other == "gmres_S" and args.s_precond == "cheb" else "")
+        ratio_o = profile_traffic(pn_o + "_cube48", "solver.cu", "dram_over_algorithmic")
         roof_k[other] = {"kernel": kdesc[other], "bound": "hbm", "achieved": by_o / (us_o * 1e-6) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": by_o / (us_o * 1e-6) / 1e9 / peak,
+                         "traffic": (ratio_o * by_o if ratio_o is not None and args.precision == "fp64" else None),
                          "bytes_per_launch": by_o, "avg_launch_us": us_o, "launches": po["launches"]}
     for k in ("gmres_A", "gmres_S"):
         if k in roof_k and roof_k[k].get("achieved"):
