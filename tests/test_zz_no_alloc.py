@@ -8,8 +8,9 @@ Checked against the existing entry points on two calls in a row:
 * the true relative residual that hyel_solve_nested reports for the scaled
   system, and
 * ||b - M x|| formed from hyel_spmv's product on the host in float64.
-Collected last so that a run stopping at the first failure has already run
-every other test; it also passes alone in a fresh process.
+A mesh beyond the scratch's limit is refused (HYEL_EINVAL). Collected last so
+that a run stopping at the first failure has already run every other test; it
+also passes alone in a fresh process.
 """
 import numpy as np
 import pytest
@@ -74,4 +75,24 @@ def test_residual_norm_static_matches_existing_entry_points():
     with pytest.raises(H.HyelError) as ei:
         H.hyel_residual_norm_static(gp.ctx, H.HYEL_MAT_SCALED32, xs.data_ptr(), bs.data_ptr(), out.data_ptr())
     assert ei.value.code == H.HYEL_EINVAL
+    gp.close()
+
+
+def test_residual_norm_static_rejects_meshes_beyond_its_scratch():
+    """The fixed scratch holds the per-block partial sums of at most 8,192
+    blocks of 128 rows: a 102^3-hex cube (1,092,727 nodes) is refused with
+    HYEL_EINVAL and a message naming the limit, without touching the array."""
+    m = inputs.cube_mesh(102, jitter=0.0)
+    gp = GpuProblem(m, inputs.material_nh(1e5, 1e6, 1e3), with_oracle=False)
+    N = gp.N
+    assert N == 103 ** 3 > 8192 * 128
+    dev, sst = gp.stage(inputs.zero_state(N))
+    H.hyel_assemble(gp.ctx, H.time_params(dt=DT), sst, 0, 0, want_norms=False)
+    x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(H.HyelError) as ei:
+        H.hyel_residual_norm_static(gp.ctx, H.HYEL_MAT_ASSEMBLED, x.data_ptr(), x.data_ptr(), out.data_ptr())
+    assert ei.value.code == H.HYEL_EINVAL
+    assert "1048576" in str(ei.value)
+    assert torch.equal(out.cpu(), torch.tensor([-1.0, -1.0], dtype=torch.float64))
     gp.close()
