@@ -14,7 +14,8 @@ BENCH = os.path.join(ROOT, "bench.py")
 def test_help():
     r = subprocess.run([sys.executable, BENCH, "--help"], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
-    for opt in ("--s-precond", "--cheb-degree", "--a-precond", "--block", "--inner", "--dt", "--nu"):
+    for opt in ("--s-precond", "--cheb-degree", "--a-precond", "--block", "--inner", "--dt", "--nu", "--no-sweep",
+                "--no-tube", "--no-mixed", "--no-e2e", "--no-cpu"):
         assert opt in r.stdout, opt
 
 
@@ -33,3 +34,5 @@ def test_options_reach_the_config(tmp_path):
     assert c["s_precond"] == "diag(S^)" and c["block_precond"] == "SIMPLE"
     assert c["inner_solver"].startswith("CG") and c["a_precond"] == "cheb"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    # the reference arm names the sample it actually times
+    assert "sample" in c["workload"] and "10^3" in c["workload"]
