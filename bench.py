@@ -51,6 +51,12 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the Poisson-ratio sweep keys")
     p.add_argument("--no-tube", action="store_true", help="skip the full-size tube (config 3) step")
+    p.add_argument("--tube-dt", type=float, default=1e-5, help="time step of the full-size tube step")
+    p.add_argument("--tube-only", action="store_true",
+                   help="instead of the benchmark: only the full-size tube step (--tube-dt, solver options as given)")
+    p.add_argument("--compare-a-precond", action="store_true",
+                   help="instead of the benchmark: one nested solve of a stiffness-dominated tube system per "
+                        "A-preconditioner (block-Jacobi, multigrid, Chebyshev), iteration counts and times")
     p.add_argument("--host-loops", action="store_true",
                    help="drive the Krylov loops from the host (for per-kernel ncu launch lists)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16s"],
@@ -346,7 +352,7 @@ def nu_sweep(ctx, H, torch, stream, args, names, sizes, dev, state, sprec_kw, gr
     return out
 
 
-def tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=1e-5):
+def tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=1e-5, precisions=None):
     """Config 3 at full size: the thick-walled HGO tube (10 x 200 x 100 hexes,
     1.2M tets, 222,200 nodes, fully incompressible, fibres at +-40 degrees),
     the first time step of the 20 % stretch ramp (10 steps) from rest at the
@@ -364,10 +370,10 @@ def tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=1e-5):
     state = H.state_struct(z["u"], z["p"], z["v"], z["udot"], z["pdot"], z["vdot"])
     out = {"workload": f"tube 10x200x100 HGO (N={N}, E={m['tets'].shape[0]}, n={4 * N}), dt={dt:g}, "
                        "first step of a 10-step stretch ramp to 20 %, from rest"}
-    for lab, prec in (("fp64", H.HYEL_PREC_FP64), ("fp32", H.HYEL_PREC_FP32)):
+    for lab, prec in (precisions or (("fp64", H.HYEL_PREC_FP64), ("fp32", H.HYEL_PREC_FP32))):
         sp = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=prec, graph=graph, **sprec_kw)
         tp = H.time_params(dt=dt, t_n=0.0, l_max=8)
-        for rep in range(2):
+        for rep in range(1 if len(precisions or ()) else 2):
             for t in z.values():
                 t.zero_()
             torch.cuda.synchronize()
@@ -382,6 +388,53 @@ def tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=1e-5):
                     "a_its": st.a_its, "s_its": st.s_its, "inner_its": st.inner_its, "status": rc,
                     "unknowns_solves_per_s": 4 * N * st.iterations / (e0.elapsed_time(e1) * 1e-3)}
     return out
+
+
+def compare_a_precond(args):
+    """The A-preconditioners on a stiffness-dominated system: the 10 x 100 x 50
+    HGO tube (56,100 nodes) at dt = 1e-3 (c2 K about 10^3 alpha_m M on the thin
+    wall), the tangent at rest, one nested solve (outer 1e-10, sub-solvers
+    1e-2) of a seeded random right-hand side per case; block-Jacobi runs with
+    FP64 levels only (with FP32 levels it reaches the 200-iteration outer cap)."""
+    import torch
+    from paper_1809_06350_gb300 import build as bld
+    from paper_1809_06350_gb300 import hyel as H
+    from paper_1809_06350_gb300 import inputs
+    bld.build()
+    dt = 1e-3
+    m = inputs.tube_mesh(10, 100, 50)
+    N = m["X"].shape[0]
+    ctx = H.hyel_create(0, torch.cuda.current_stream().cuda_stream)
+    inp = H.MeshInputs(m, inputs.material_hgo(3e4, 2e5, 5.0, 0.0), None, {"p_max": 0.0, "t_ramp": 10 * dt})
+    H.hyel_mesh_upload(ctx, inp.X, inp.tets, inp.bc, inp.mat)
+    z = {k: torch.zeros(3 * N if k in ("u", "v", "udot", "vdot") else N, dtype=torch.float64, device="cuda")
+         for k in ("u", "p", "v", "udot", "pdot", "vdot")}
+    H.hyel_assemble(ctx, H.time_params(dt=dt), H.state_struct(*(z[k] for k in ("u", "p", "v", "udot", "pdot",
+                                                                                 "vdot"))), 0, 0)
+    rhs = torch.as_tensor(inputs.random_vector(4 * N, seed=1), device="cuda")
+    cases = [("block-Jacobi, diag(S^)", H.HYEL_PREC_FP64, H.HYEL_APREC_BJACOBI, H.HYEL_SPREC_JACOBI),
+             ("block-Jacobi, Chebyshev-8 on S^", H.HYEL_PREC_FP64, H.HYEL_APREC_BJACOBI, H.HYEL_SPREC_CHEB),
+             ("multigrid, diag(S^)", H.HYEL_PREC_FP64, H.HYEL_APREC_AMG, H.HYEL_SPREC_JACOBI),
+             ("multigrid, diag(S^)", H.HYEL_PREC_FP32, H.HYEL_APREC_AMG, H.HYEL_SPREC_JACOBI),
+             ("Chebyshev-8 on A, Chebyshev-8 on S^", H.HYEL_PREC_FP64, H.HYEL_APREC_CHEB, H.HYEL_SPREC_CHEB),
+             ("Chebyshev-8 on A, Chebyshev-8 on S^", H.HYEL_PREC_FP32, H.HYEL_APREC_CHEB, H.HYEL_SPREC_CHEB)]
+    out = []
+    for name, prec, ap, sp_ in cases:
+        sp = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=prec, graph=1, a_precond=ap, s_precond=sp_,
+                             s_cheb_degree=8, a_cheb_degree=8)
+        x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rc = H.hyel_solve_nested(ctx, sp, rhs.data_ptr(), x.data_ptr(), raise_on_error=False)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        out.append({"case": name, "levels": "fp64" if prec == H.HYEL_PREC_FP64 else "fp32", "status": rc,
+                    "seconds": sec, "outer_its": st.outer_its, "a_its_per_solve": st.a_its / max(1, st.a_solves),
+                    "inner_its_per_solve": st.inner_its / max(1, st.inner_solves),
+                    "s_its_per_solve": st.s_its / max(1, st.s_solves), "rel_residual": st.rel_residual})
+    H.hyel_destroy(ctx)
+    print(json.dumps({"compare_a_precond": out, "workload": "tube 10x100x50 HGO (N=%d), dt=1e-3, tangent at rest, "
+                                                            "random right-hand side (seed 1)" % N}), flush=True)
 
 
 def run_hyel(args, rank, world, local_rank):
@@ -467,6 +520,16 @@ def run_hyel(args, rank, world, local_rank):
                 "a_precond": {"bjacobi": H.HYEL_APREC_BJACOBI, "cheb": H.HYEL_APREC_CHEB,
                               "amg": H.HYEL_APREC_AMG}[args.a_precond]}
     main_prec = {"fp64": H.HYEL_PREC_FP64, "fp32": H.HYEL_PREC_FP32, "bf16s": H.HYEL_PREC_BF16S}[args.precision]
+    if args.tube_only:
+        # one timed step per run, no warm-up: the step itself takes seconds
+        res = tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=args.tube_dt,
+                        precisions=((args.precision, main_prec),))
+        H.hyel_destroy(ctx)
+        if rank == 0:
+            cfg = config_dict(args, mesh)
+            res["solver"] = {k: cfg[k] for k in ("levels", "s_precond", "block_precond", "inner_solver", "a_precond")}
+            print(json.dumps({"config3_tube": res}), flush=True)
+        return
     sp64 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=main_prec, graph=graph, **sprec_kw)
     sp32 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, graph=graph, **sprec_kw)
     sp16 = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_BF16S, graph=graph, **sprec_kw)
@@ -706,7 +769,7 @@ def run_hyel(args, rank, world, local_rank):
               for k, v in prof_host.items()}
     sweep = None if args.no_sweep else nu_sweep(ctx, H, torch, stream, args, names, sizes, dev, state, sprec_kw,
                                                 graph)
-    tube = None if args.no_tube else tube_step(ctx, H, torch, stream, graph, sprec_kw)
+    tube = None if args.no_tube else tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=args.tube_dt)
     H.hyel_destroy(ctx)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -740,7 +803,10 @@ def main():
             torch.cuda.set_device(local_rank)
         dist.init_process_group(backend)
     try:
-        if args.impl == "reference":
+        if args.compare_a_precond:
+            if rank == 0:
+                compare_a_precond(args)
+        elif args.impl == "reference":
             run_reference(args, rank, world)
         else:
             run_hyel(args, rank, world, local_rank)
