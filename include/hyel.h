@@ -396,6 +396,13 @@ int hyel_a_cheb_setup(hyel_ctx *ctx, double *bounds_out);
  * hyel_a_cheb_setup on the current assembly. Synchronizes. */
 int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y);
 
+/* The multigrid hierarchy of HYEL_APREC_AMG (built by the first solve that
+ * selects it on the current mesh): info[0] = number of levels L (0 before
+ * that solve), then per level l = 0..L-1 info[1 + 2l] = block-nodes (3
+ * unknowns each; level 0 is the mesh's nodes) and info[2 + 2l] = stored 3x3
+ * blocks. Writes at most n entries of the host array info. */
+int hyel_amg_info(hyel_ctx *ctx, int64_t *info, int n);
+
 /* z = P^-1 r once, P the block preconditioner of params->block_precond on the
  * scaled system (§4.2–4.4), its sub-solves controlled by params (precision,
  * levels, A- and S-preconditioners) exactly as inside hyel_solve_nested.

@@ -1,5 +1,6 @@
 // C-ABI entry points of libhyel (see include/hyel.h): argument checks, error
 // translation, context and memory management, kernel-class event timing.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -399,6 +400,16 @@ int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y)
         const size_t n = 3 * (size_t)c.mesh.N * sizeof(double);
         if (overlaps(x, n, y, n)) hyel::fail(HYEL_EINVAL, "a_cheb_apply: x and y must not overlap");
         hyel::acheb_apply(c, degree, x, y);
+    });
+}
+
+int hyel_amg_info(hyel_ctx *ctx, int64_t *info, int n) {
+    return guarded(ctx, [&](hyel::Ctx &c) {
+        if (!info || n < 1) hyel::fail(HYEL_EINVAL, "amg_info: need an output of at least one entry");
+        int64_t v[1 + 2 * 16] = {0};
+        const int L = hyel::amg_levels(c, v + 1, 2 * 16);
+        v[0] = L;
+        for (int k = 0; k < n && k < 1 + 2 * std::min(L, 16); k++) info[k] = v[k];
     });
 }
 

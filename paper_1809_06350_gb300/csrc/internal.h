@@ -85,6 +85,7 @@ struct DeviceMesh {
     std::vector<int32_t> h_row_ptr, h_col;  // block CSR
     std::vector<int64_t> h_csr_slot;        // CSR position -> slot
     std::vector<double> h_hmax;             // longest reference edge per element (tau_M updates)
+    std::vector<double> h_X;                // [3N] reference coordinates (multigrid rigid-body modes)
     double c_m = 1e-3;
 };
 
@@ -267,7 +268,7 @@ void matrix_download(Ctx &c, int32_t *row_ptr, int32_t *col, double *A, double *
 // amg.cu
 void amg_free(Ctx &c);
 void amg_numeric(Ctx &c);  // builds the hierarchy on first use, then the level operators
-int amg_levels(const Ctx &c, int64_t *sizes, int max);
+int amg_levels(const Ctx &c, int64_t *sizes, int max);  // per level: block-nodes, stored blocks; returns levels
 template <typename T>
 void amg_apply(Ctx &c, const T *v, T *z);  // z = V-cycle(v), [3N]
 

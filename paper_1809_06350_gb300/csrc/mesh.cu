@@ -297,6 +297,7 @@ static void mesh_upload_impl(Ctx &c, int64_t N, const double *X, int64_t E, cons
     m.h_col = cols;
     m.h_csr_slot = csr_slot;
     m.h_hmax = std::move(hmax_all);
+    m.h_X.assign(X, X + 3 * (size_t)N);
     m.c_m = mat->c_m;
 
     // ---- matrices, staging and scratch

@@ -42,7 +42,7 @@ EXPORTS = [
     "hyel_launch_count", "hyel_residual_norm_static", "hyel_update_material",
     "hyel_solve_nested_transpose", "hyel_param_sensitivity", "hyel_adjoint_step",
     "hyel_schur_hat_setup", "hyel_schur_hat_cheb", "hyel_block_precond_apply", "hyel_a_cheb_setup",
-    "hyel_a_cheb_apply", "hyel_set_wait_limit", "hyel_inject_fault",
+    "hyel_a_cheb_apply", "hyel_amg_info", "hyel_set_wait_limit", "hyel_inject_fault",
     "hyel_fp64_fma_probe", "hyel_stream_read_probe",
 ]
 
@@ -154,6 +154,7 @@ def lib():
             "hyel_schur_hat_cheb": (C.c_int, [vp, C.c_int, C.c_int32, C.c_double, vp, vp]),
             "hyel_a_cheb_setup": (C.c_int, [vp, _dp]),
             "hyel_a_cheb_apply": (C.c_int, [vp, C.c_int32, vp, vp]),
+            "hyel_amg_info": (C.c_int, [vp, C.POINTER(C.c_int64), C.c_int]),
             "hyel_block_precond_apply": (C.c_int, [vp, C.POINTER(HyelSolverParams), vp, vp,
                                                    C.POINTER(HyelSolveStats)]),
             "hyel_set_wait_limit": (C.c_int, [vp, C.c_double]),
@@ -270,6 +271,13 @@ def hyel_a_cheb_setup(ctx):
 
 def hyel_a_cheb_apply(ctx, degree, x_ptr, y_ptr):
     _check(ctx, lib().hyel_a_cheb_apply(ctx, int(degree), C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
+def hyel_amg_info(ctx):
+    """[(block-nodes, stored blocks) per level] of the multigrid hierarchy ([] before it is built)."""
+    out = (C.c_int64 * 33)()
+    _check(ctx, lib().hyel_amg_info(ctx, out, 33))
+    return [(out[1 + 2 * l], out[2 + 2 * l]) for l in range(out[0])]
 
 
 def hyel_block_precond_apply(ctx, params, r_ptr, z_ptr):
