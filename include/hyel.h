@@ -161,11 +161,15 @@ typedef struct {
 /* Preconditioner of the A-solves (intermediate and inner):
  * HYEL_APREC_BJACOBI: 3x3 block-Jacobi, folded into the operator (A M^-1) of a
  *   persistent GMRES kernel (the default);
- * HYEL_APREC_AMG: one V-cycle of aggregation multigrid (the stand-in for the
- *   paper's algebraic multigrid, §4.4): unsmoothed-aggregation Galerkin levels
- *   with 3x3 blocks, damped block-Jacobi smoothing, as the right preconditioner
- *   of an FGMRES A-level. The hierarchy's pattern is built once per mesh, its
- *   operators once per assembly (after the scaling);
+ * HYEL_APREC_AMG: one V-cycle of smoothed-aggregation multigrid (the
+ *   stand-in for the paper's algebraic multigrid, §4.4) as the right
+ *   preconditioner of an FGMRES A-level: the coarse space holds the rigid-body
+ *   modes of every aggregate (two 3x3 block-nodes each: translation and
+ *   rotation), the prolongator is smoothed once by damped block-Jacobi,
+ *   Galerkin levels, a degree-3 Chebyshev smoother, a dense inverse on the
+ *   coarsest level (at most 96 block-nodes). The hierarchy's pattern is built
+ *   once per mesh (on the host), its operators once per assembly (after the
+ *   scaling, on the GPU); hyel_amg_info reports its levels;
  * HYEL_APREC_CHEB: the polynomial p(M^-1 A) M^-1 of degree a_cheb_degree
  *   (1..16), M the 3x3 block diagonal of A: that many steps of the Chebyshev
  *   iteration for A z = v from z = 0 on [lmin, lmax] from Ritz values of

@@ -1,14 +1,22 @@
-"""Aggregation multigrid as the preconditioner of the A-solves
-(HYEL_APREC_AMG): it changes iteration counts, never the solution.
+"""Smoothed-aggregation multigrid with rigid-body modes as the preconditioner
+of the A-solves (HYEL_APREC_AMG): it changes iteration counts, never the
+solution.
 
 * nested solve with the multigrid A-levels vs the oracle's direct solve
   (1e-9 at outer tolerance 1e-13), FP64 and FP32 levels, cube and tube;
 * the transposed nested solve with multigrid A-levels vs the oracle;
 * graph and host-driven runs agree bit for bit;
 * two Newton steps of the small HGO tube match the oracle;
+* a mesh of at most 96 nodes is a single level solved by its dense
+  Gauss-Jordan inverse: every A-solve then converges in one iteration;
+* the hierarchy: two coarse block-nodes (translation, rotation) per
+  aggregate, sizes falling to a dense coarsest level;
 * on a stiffness-dominated tube (5 x 50 x 25 hexes) the multigrid A-levels
   need at most a third of the block-Jacobi A-iterations for the same Newton
-  step (measured on GB300: 2,251 against 17,400).
+  step;
+* mesh independence on the stiff tube at rest (dt = 1e-3): the A-iterations
+  per A-solve stay at most 12 from 7,800 to 56,100 nodes (measured on GB300:
+  9.5 and 8.1).
 """
 import numpy as np
 import pytest
@@ -125,3 +133,54 @@ def test_amg_cuts_a_iterations_on_a_stiff_tube():
         its[aprec] = st.a_its
     assert its[AMG] * 3 <= its[H.HYEL_APREC_BJACOBI], its
     gp.close()
+
+
+def test_amg_single_dense_level_is_exact():
+    """cube 3^3 (64 nodes <= 96): level 0 is the coarsest, the V-cycle is its
+    dense inverse, and each A-solve stops after its first iteration."""
+    gp, Kd, rhs, rhs_o, _ = _system(inputs.cube_mesh(3), inputs.material_nh(1e5, 1e6, 1e3))
+    N = gp.N
+    x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
+    p = H.solver_params(outer_rtol=1e-13, sub_rtol=1e-10, a_precond=AMG)
+    st, rc = H.hyel_solve_nested(gp.ctx, p, rhs.data_ptr(), x.data_ptr())
+    assert H.hyel_amg_info(gp.ctx) == [(N, H.hyel_mesh_info(gp.ctx)["nnzb"])]
+    assert st.a_solves > 0 and st.a_its == st.a_solves, st.as_dict()
+    assert _rel(x.cpu().numpy(), S.direct_solve(Kd, rhs_o)) <= 1e-9
+    gp.close()
+
+
+def _tube_at_rest(shape):
+    m = inputs.tube_mesh(*shape)
+    mat = inputs.material_hgo(3e4, 2e5, 5.0, 0.0)
+    gp = GpuProblem(m, mat, load={"p_max": 0.0, "t_ramp": 10 * DT}, with_oracle=False)
+    z = inputs.zero_state(gp.N)
+    dev, sst = gp.stage(z)
+    H.hyel_assemble(gp.ctx, H.time_params(dt=DT), sst, 0, 0)
+    rhs = torch.as_tensor(inputs.random_vector(4 * gp.N, seed=1), device="cuda")
+    return gp, rhs
+
+
+def test_amg_hierarchy_shape():
+    gp, rhs = _tube_at_rest((5, 50, 25))
+    assert H.hyel_amg_info(gp.ctx) == []
+    x = torch.zeros(4 * gp.N, dtype=torch.float64, device="cuda")
+    H.hyel_solve_nested(gp.ctx, H.solver_params(a_precond=AMG), rhs.data_ptr(), x.data_ptr())
+    lv = H.hyel_amg_info(gp.ctx)
+    assert len(lv) >= 3 and lv[0] == (gp.N, H.hyel_mesh_info(gp.ctx)["nnzb"])
+    for (n0, _), (n1, b1) in zip(lv, lv[1:]):
+        assert n1 % 2 == 0 and n1 < n0 and n1 <= b1 <= n1 * n1
+    assert lv[-1][0] <= 96
+    gp.close()
+
+
+def test_amg_a_iterations_are_mesh_independent_on_the_stiff_tube():
+    per = []
+    for shape in ((5, 50, 25), (10, 100, 50)):
+        gp, rhs = _tube_at_rest(shape)
+        x = torch.zeros(4 * gp.N, dtype=torch.float64, device="cuda")
+        p = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, a_precond=AMG)
+        st, rc = H.hyel_solve_nested(gp.ctx, p, rhs.data_ptr(), x.data_ptr())
+        assert rc == H.HYEL_OK and st.rel_residual <= 1e-10
+        per.append(st.a_its / st.a_solves)
+        gp.close()
+    assert max(per) <= 12.0, per
