@@ -379,14 +379,28 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
                     tau * JV * (n[A][0] * ngp[0] + n[A][1] * ngp[1] + n[A][2] * ngp[2]);
     }
 
+    // the pair loop's C block takes -c2 JV/4 (grad v^T n_B) as its addend
+#pragma unroll
+    for (int B = 0; B < 4; B++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) LvTn[B][j] *= -c2jv4;
+
 #pragma unroll 1
     for (int A = 0; A < 4; A++) {
+        // B block of the pairs (A, B): db_i (B = A), ub_i + opc_iB (B != A)
+        double ubA[3], dbA[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            ubA[i] = fma(-jv4c1, n[A][i], opc[i][A]);
+            dbA[i] = fma(-jv4c1, n[A][i], dpc[i][A]);
+        }
 #pragma unroll
         for (int B = 0; B < 4; B++) {
             double out[16];
             const double gg = g[A][0] * g[B][0] + g[A][1] * g[B][1] + g[A][2] * g[B][2];
             const double nn = n[A][0] * n[B][0] + n[A][1] * n[B][1] + n[A][2] * n[B][2];
-            // A block: c2 A_u + a_m (mass) on the diagonal
+            // A block: c2 A_u + a_m (mass) on the diagonal (the diagonal terms
+            // are the innermost addend of the entry's multiply-add chain)
             const bool same = A == B;
             const double mass = same ? dm[A] : om[A] + om[B];
             const double dg = fma(q4, gg, mass);
@@ -394,9 +408,8 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
             for (int i = 0; i < 3; i++)
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    double s = fma(Q1[A][i], n[B][j], fma(Q2[A][i], f[B][j], q3n[A][j] * n[B][i]));
-                    if (i == j) s += dg;
-                    out[3 * i + j] = s;
+                    const double s0 = i == j ? fma(q3n[A][j], n[B][i], dg) : q3n[A][j] * n[B][i];
+                    out[3 * i + j] = fma(Q1[A][i], n[B][j], fma(Q2[A][i], f[B][j], s0));
                 }
             if (a.nfib) {
 #pragma unroll
@@ -416,12 +429,12 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs a) {
             }
             // B^i_AB = c1 (int rho_,p J (vdot_i - b_i) N_A N_B - J N_A,i V/4)
 #pragma unroll
-            for (int i = 0; i < 3; i++) out[9 + i] = fma(-jv4c1, n[A][i], same ? dpc[i][A] : opc[i][A] + opc[i][B]);
+            for (int i = 0; i < 3; i++) out[9 + i] = same ? dbA[i] : ubA[i] + opc[i][B];
 #pragma unroll
             for (int j = 0; j < 3; j++)
-                out[12 + j] = fma(cAs[A], n[B][j], fma(cBs[B], n[A][j], fma(-c2jv4, LvTn[B][j], -gpc[j] * nn)));
-            out[15] = fma(c1tJV, nn, same ? ddw[A] : odw[A] + odw[B]) +
-                      fma(n[A][0], qrc[B][0], fma(n[A][1], qrc[B][1], n[A][2] * qrc[B][2]));
+                out[12 + j] = fma(cAs[A], n[B][j], fma(cBs[B], n[A][j], fma(-gpc[j], nn, LvTn[B][j])));
+            const double md = same ? ddw[A] : odw[A] + odw[B];
+            out[15] = fma(n[A][0], qrc[B][0], fma(n[A][1], qrc[B][1], fma(n[A][2], qrc[B][2], fma(c1tJV, nn, md))));
             double2 *rec = reinterpret_cast<double2 *>(record(a.stage, e, 4 * A + B));
 #pragma unroll
             for (int k = 0; k < 8; k++) rec[k] = make_double2(out[2 * k], out[2 * k + 1]);
