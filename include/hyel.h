@@ -167,7 +167,8 @@ typedef struct {
  *   modes of every aggregate (two 3x3 block-nodes each: translation and
  *   rotation), the prolongator is smoothed once by damped block-Jacobi,
  *   Galerkin levels, a degree-3 Chebyshev smoother, a dense inverse on the
- *   coarsest level (at most 96 block-nodes). The hierarchy's pattern is built
+ *   coarsest level (at most 96 block-nodes); the cycle runs in FP32 for FP64
+ *   and FP32 levels alike (the level's own products keep its precision). The hierarchy's pattern is built
  *   once per mesh (on the host), its operators once per assembly (after the
  *   scaling, on the GPU); hyel_amg_info reports its levels;
  * HYEL_APREC_CHEB: the polynomial p(M^-1 A) M^-1 of degree a_cheb_degree

@@ -27,10 +27,11 @@
 //   Gauss-Jordan elimination with partial pivoting, in one thread block. A
 //   coarse unknown whose row and column vanish (a rigid mode that the
 //   constraints remove entirely) gets a unit diagonal and stays zero.
-// * Application: one V-cycle. kSmooth damped block-Jacobi sweeps run before
-//   and after the coarse correction, with w = 4 / (3 lambda) of the level.
-//   The V-cycle is a fixed linear operator, used as the right preconditioner
-//   of the A-level (F)GMRES.
+// * Application: one V-cycle in FP32 (for FP64 and FP32 levels alike). A
+//   degree-kSmoothDegree Chebyshev smoother on [lambda / kSmoothRatio, lambda]
+//   runs before and after the coarse correction; coarse-level products use 8
+//   lanes per row. The V-cycle is a fixed linear operator, used as the right
+//   preconditioner of the A-level (F)GMRES.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -113,9 +114,10 @@ struct Level {
     // transposed for the apply (dinvT[j n + i] = A^-1(i, j), n = 3N)
     double *dense64 = nullptr, *dwork64 = nullptr, *dinvT64 = nullptr;
     float *dinvT32 = nullptr;
-    // work vectors [3N]: right-hand side, iterate, residual; two smoother directions [2][3N]
-    double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *e64 = nullptr;
+    // FP32 work vectors of the V-cycle [3N]: right-hand side, iterate, residual;
+    // two smoother directions [2][3N]; an FP64 [3N] pair for the power steps
     float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *e32 = nullptr;
+    double *x64 = nullptr, *r64 = nullptr;
     int64_t nnzb = 0;  // stored blocks (valid entries)
     int lanes = 1;     // lanes per row of this level's products (long rows on coarse levels)
 };
@@ -755,25 +757,14 @@ __global__ void k_sa_prolong(const int32_t *__restrict__ p_ptr, const int32_t *_
     x[3 * i + 2] += a2;
 }
 
-template <typename T>
-__global__ void k_copy(const T *__restrict__ a, T *__restrict__ b, int64_t n) {
+template <typename Tin, typename Tout>
+__global__ void k_copy(const Tin *__restrict__ a, Tout *__restrict__ b, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = a[i];
+    if (i < n) b[i] = (Tout)a[i];
 }
 
 template <typename T>
 struct LvView;
-template <>
-struct LvView<double> {
-    static const double *A(const Level &l) { return l.A64; }
-    static const double *J(const Level &l) { return l.jac64; }
-    static const double *P(const Level &l) { return l.P64; }
-    static const double *D(const Level &l) { return l.dinvT64; }
-    static double *b(Level &l) { return l.b64; }
-    static double *x(Level &l) { return l.x64; }
-    static double *r(Level &l) { return l.r64; }
-    static double *e(Level &l) { return l.e64; }
-};
 template <>
 struct LvView<float> {
     static const float *A(const Level &l) { return l.A32; }
@@ -1113,13 +1104,11 @@ static void amg_build(Ctx &c) {
         ell = std::move(cell);
     }
     for (Level &L : a->lv) {
-        L.b64 = dalloc_n<double>(c, 3 * (size_t)L.N);
         L.x64 = dalloc_n<double>(c, 3 * (size_t)L.N);
         L.r64 = dalloc_n<double>(c, 3 * (size_t)L.N);
         L.b32 = dalloc_n<float>(c, 3 * (size_t)L.N);
         L.x32 = dalloc_n<float>(c, 3 * (size_t)L.N);
         L.r32 = dalloc_n<float>(c, 3 * (size_t)L.N);
-        L.e64 = dalloc_n<double>(c, 6 * (size_t)L.N);
         L.e32 = dalloc_n<float>(c, 6 * (size_t)L.N);
         L.lam = dalloc_n<double>(c, 1);
     }
@@ -1240,16 +1229,19 @@ int amg_levels(const Ctx &c, int64_t *sizes, int max) {
     return n;
 }
 
-// z = V-cycle(v) on [3N] vectors of precision T (stream-ordered; graph-safe)
+// z = V-cycle(v) on [3N] vectors of precision T (stream-ordered; graph-safe).
+// The cycle itself runs in FP32 for either level precision: it is a
+// preconditioner of a flexible GMRES level, whose own products keep the
+// level's precision, and in FP64 its block products would be bound by the
+// FP64 pipe.
 template <typename T>
 void amg_apply(Ctx &c, const T *v, T *z) {
     Amg &a = *c.amg;
     Level &L0 = a.lv[0];
-    using V = LvView<T>;
     const int64_t n = 3 * L0.N;
-    AMG_LAUNCH(k_copy<T><<<blocks_for(n, 256), 256, 0, c.stream>>>(v, V::b(L0), n));
-    vcycle<T>(c, a, 0);
-    AMG_LAUNCH(k_copy<T><<<blocks_for(n, 256), 256, 0, c.stream>>>(V::x(L0), z, n));
+    AMG_LAUNCH(k_copy<T, float><<<blocks_for(n, 256), 256, 0, c.stream>>>(v, L0.b32, n));
+    vcycle<float>(c, a, 0);
+    AMG_LAUNCH(k_copy<float, T><<<blocks_for(n, 256), 256, 0, c.stream>>>(L0.x32, z, n));
 }
 template void amg_apply<double>(Ctx &, const double *, double *);
 template void amg_apply<float>(Ctx &, const float *, float *);

@@ -8,7 +8,8 @@ solution.
 * graph and host-driven runs agree bit for bit;
 * two Newton steps of the small HGO tube match the oracle;
 * a mesh of at most 96 nodes is a single level solved by its dense
-  Gauss-Jordan inverse: every A-solve then converges in one iteration;
+  Gauss-Jordan inverse (applied in FP32): every A-solve then reaches 1e-10
+  in at most two iterations (the inverse, then one refinement step);
 * the hierarchy: two coarse block-nodes (translation, rotation) per
   aggregate, sizes falling to a dense coarsest level;
 * on a stiffness-dominated tube (5 x 50 x 25 hexes) the multigrid A-levels
@@ -136,15 +137,16 @@ def test_amg_cuts_a_iterations_on_a_stiff_tube():
 
 
 def test_amg_single_dense_level_is_exact():
-    """cube 3^3 (64 nodes <= 96): level 0 is the coarsest, the V-cycle is its
-    dense inverse, and each A-solve stops after its first iteration."""
+    """cube 3^3 (64 nodes <= 96): level 0 is the coarsest and the V-cycle is
+    its dense inverse, applied in FP32, so each A-solve reaches 1e-10 in at
+    most two iterations."""
     gp, Kd, rhs, rhs_o, _ = _system(inputs.cube_mesh(3), inputs.material_nh(1e5, 1e6, 1e3))
     N = gp.N
     x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
     p = H.solver_params(outer_rtol=1e-13, sub_rtol=1e-10, a_precond=AMG)
     st, rc = H.hyel_solve_nested(gp.ctx, p, rhs.data_ptr(), x.data_ptr())
     assert H.hyel_amg_info(gp.ctx) == [(N, H.hyel_mesh_info(gp.ctx)["nnzb"])]
-    assert st.a_solves > 0 and st.a_its == st.a_solves, st.as_dict()
+    assert st.a_solves > 0 and st.a_its <= 2 * st.a_solves, st.as_dict()
     assert _rel(x.cpu().numpy(), S.direct_solve(Kd, rhs_o)) <= 1e-9
     gp.close()
 
