@@ -168,9 +168,10 @@ typedef struct {
  *   rotation), the prolongator is smoothed once by damped block-Jacobi,
  *   Galerkin levels, a degree-3 Chebyshev smoother, a dense inverse on the
  *   coarsest level (at most 96 block-nodes); the cycle runs in FP32 for FP64
- *   and FP32 levels alike (the level's own products keep its precision). The hierarchy's pattern is built
- *   once per mesh (on the host), its operators once per assembly (after the
- *   scaling, on the GPU); hyel_amg_info reports its levels;
+ *   and FP32 levels alike (the level's own products keep its precision).
+ *   The hierarchy's pattern is built once per mesh (on the host), its
+ *   operators once per assembly (after the scaling, on the GPU);
+ *   hyel_amg_info reports its levels;
  * HYEL_APREC_CHEB: the polynomial p(M^-1 A) M^-1 of degree a_cheb_degree
  *   (1..16), M the 3x3 block diagonal of A: that many steps of the Chebyshev
  *   iteration for A z = v from z = 0 on [lmin, lmax] from Ritz values of
@@ -401,7 +402,8 @@ int hyel_a_cheb_setup(hyel_ctx *ctx, double *bounds_out);
  * hyel_a_cheb_setup on the current assembly. Synchronizes. */
 int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y);
 
-/* The multigrid hierarchy of HYEL_APREC_AMG (built by the first solve that
+/* The multigrid hierarchy of HYEL_APREC_AMG, the stand-in for the paper's
+ * algebraic multigrid of §4.4 and §5 (built by the first solve that
  * selects it on the current mesh): info[0] = number of levels L (0 before
  * that solve), then per level l = 0..L-1 info[1 + 2l] = block-nodes (3
  * unknowns each; level 0 is the mesh's nodes) and info[2 + 2l] = stored 3x3
