@@ -407,7 +407,8 @@ int hyel_a_cheb_apply(hyel_ctx *ctx, int32_t degree, const double *x, double *y)
  * selects it on the current mesh): info[0] = number of levels L (0 before
  * that solve), then per level l = 0..L-1 info[1 + 2l] = block-nodes (3
  * unknowns each; level 0 is the mesh's nodes) and info[2 + 2l] = stored 3x3
- * blocks. Writes at most n entries of the host array info. */
+ * blocks. Writes at most n entries of the host array info; HYEL_EINVAL if
+ * info is NULL or n < 1. */
 int hyel_amg_info(hyel_ctx *ctx, int64_t *info, int n);
 
 /* z = P^-1 r once, P the block preconditioner of params->block_precond on the
