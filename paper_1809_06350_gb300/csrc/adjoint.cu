@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(128) k_param_sensitivity(SensArgs a) {
     D4 k2 = dconst<4>(a.nfib ? a.mat[3 * E + e] : 1.0);
     k2.d[3] = 1.0;
     const double bf[3] = {a.b0, a.b1, a.b2};
-    double u[4][3], v[4][3], vdb[4][3], p[4], pd[4], lm[4][3], lp[4];
+    double u[4][3], vdb[4][3], p[4], pd[4], lm[4][3], lp[4];  // the velocity terms carry no material parameter
 #pragma unroll
     for (int A = 0; A < 4; A++) {
         const int64_t n = nd[A];
@@ -157,7 +157,6 @@ __global__ void __launch_bounds__(128) k_param_sensitivity(SensArgs a) {
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             u[A][i] = a.u[3 * n + i];
-            v[A][i] = a.v[3 * n + i];
             vdb[A][i] = a.vd[3 * n + i] - bf[i];
             lm[A][i] = ((df >> i) & 1u) ? 0.0 : a.lam[4 * N + 3 * n + i];
         }
