@@ -6,7 +6,9 @@ solution.
   (1e-9 at outer tolerance 1e-13), FP64 and FP32 levels, cube and tube;
 * the transposed nested solve with multigrid A-levels vs the oracle;
 * graph and host-driven runs agree bit for bit;
-* two Newton steps of the small HGO tube match the oracle;
+* two Newton steps of the small HGO tube match the oracle, and so does one
+  Newton step of the cube at the paper's large time step dt = 0.1 (nu = 0.3
+  and the incompressible 0.5);
 * a mesh of at most 96 nodes is a single level solved by its dense
   Gauss-Jordan inverse (applied in FP32): every A-solve then reaches 1e-10
   in at most two iterations (the inverse, then one refinement step);
@@ -209,4 +211,33 @@ def test_amg_fullsize_stiff_tube_solve():
     H.hyel_spmv(gp.ctx, H.HYEL_OP_FULL, H.HYEL_MAT_ASSEMBLED, x.data_ptr(), y.data_ptr())
     rel = (torch.linalg.norm(rhs - y) / torch.linalg.norm(rhs)).item()
     assert rel <= 1e-9, rel
+    gp.close()
+
+
+@pytest.mark.parametrize("nu", [0.3, 0.5])
+def test_amg_large_dt_newton_step_matches_oracle(nu):
+    """The paper's large time step (dt = 0.1: A dominated by the stiffness)
+    on the 6^3 cube (343 nodes, so the hierarchy has coarse levels), nu = 0.3
+    and the incompressible nu = 0.5: one Newton step with the multigrid
+    A-solves, FP64 and FP32 levels, matches the oracle's direct-solve Newton
+    step at 1e-9 relative with the same number of corrections."""
+    dt = 0.1
+    m = inputs.cube_mesh(6)
+    mat = inputs.material_nh(1e5, inputs.kappa_from_nu(1e5, nu), 1e3)
+    gp = GpuProblem(m, mat, load={"p_max": 2e4, "t_ramp": 10 * dt})
+    prob, N = gp.prob, gp.N
+    z = inputs.zero_state(N)
+    yz = {k: z[k] for k in ("u", "p", "v")}
+    ydz = {k: z[k] for k in ("udot", "pdot", "vdot")}
+    y1, yd1, info = Nw.newton_step(prob, yz, ydz, 0.0, dt, tol_r=1e-10, tol_a=1e-12)
+    assert info["converged"]
+    for precision in (H.HYEL_PREC_FP64, H.HYEL_PREC_FP32):
+        dev = {k: gp.dev(z[k]) for k in z}
+        state = H.state_struct(dev["u"], dev["p"], dev["v"], dev["udot"], dev["pdot"], dev["vdot"])
+        sp_ = H.solver_params(outer_rtol=1e-13, sub_rtol=1e-2, precision=precision, a_precond=AMG)
+        st, rc = H.hyel_newton_step(gp.ctx, H.time_params(dt=dt, tol_r=1e-10, tol_a=1e-12), sp_, state)
+        assert st.converged and st.iterations == info["iterations"], (nu, precision, st.as_dict(), info)
+        assert len(H.hyel_amg_info(gp.ctx)) >= 2
+        for k in ("u", "p", "v"):
+            assert _rel(dev[k].cpu().numpy().reshape(y1[k].shape), y1[k]) <= 1e-9, (nu, precision, k)
     gp.close()
