@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--tube-dt", type=float, default=1e-5, help="time step of the full-size tube step")
     p.add_argument("--tube-only", action="store_true",
                    help="instead of the benchmark: only the full-size tube step (--tube-dt, solver options as given)")
+    p.add_argument("--stiff-only", action="store_true",
+                   help="instead of the benchmark: only the stiff full-size tube solve with the multigrid A-solves")
     p.add_argument("--compare-a-precond", action="store_true",
                    help="instead of the benchmark: one nested solve of a stiffness-dominated tube system per "
                         "A-preconditioner (block-Jacobi, multigrid, Chebyshev), iteration counts and times")
@@ -553,6 +555,16 @@ def run_hyel(args, rank, world, local_rank):
                 "a_precond": {"bjacobi": H.HYEL_APREC_BJACOBI, "cheb": H.HYEL_APREC_CHEB,
                               "amg": H.HYEL_APREC_AMG}[args.a_precond]}
     main_prec = {"fp64": H.HYEL_PREC_FP64, "fp32": H.HYEL_PREC_FP32, "bf16s": H.HYEL_PREC_BF16S}[args.precision]
+    if args.stiff_only:
+        from paper_1809_06350_gb300 import inputs
+        tm = inputs.tube_mesh()
+        tin = H.MeshInputs(tm, inputs.material_hgo(3e4, 2e5, 5.0, 0.0), None, {"p_max": 0.0, "t_ramp": 1e-2})
+        H.hyel_mesh_upload(ctx, tin.X, tin.tets, tin.bc, tin.mat)
+        res = stiff_tube_solve(ctx, H, torch, stream, tm["X"].shape[0])
+        H.hyel_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"stiff_solve_multigrid": res}), flush=True)
+        return
     if args.tube_only:
         # one timed step per run, no warm-up: the step itself takes seconds
         res = tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=args.tube_dt,
