@@ -390,11 +390,11 @@ def tube_step(ctx, H, torch, stream, graph, sprec_kw, dt=1e-5, precisions=None):
                     "a_its": st.a_its, "s_its": st.s_its, "inner_its": st.inner_its, "status": rc,
                     "unknowns_solves_per_s": 4 * N * st.iterations / (e0.elapsed_time(e1) * 1e-3)}
     if precisions is None:
-        out["stiff_solve_multigrid"] = stiff_tube_solve(ctx, H, torch, stream, N)
+        out["stiff_solve_multigrid"] = stiff_tube_solve(ctx, H, torch, stream, N, graph)
     return out
 
 
-def stiff_tube_solve(ctx, H, torch, stream, N, dt=1e-3):
+def stiff_tube_solve(ctx, H, torch, stream, N, graph=1, dt=1e-3):
     """The same tube where A is stiffness-dominated (dt = 1e-3: c2 K about
     10^3 alpha_m M on the wall): the tangent at rest, one nested solve of a
     seeded random right-hand side (outer 1e-10, sub-solvers 1e-2) with the
@@ -405,7 +405,7 @@ def stiff_tube_solve(ctx, H, torch, stream, N, dt=1e-3):
     z = [torch.zeros(3 * N if k in (0, 2, 3, 5) else N, dtype=torch.float64, device="cuda") for k in range(6)]
     H.hyel_assemble(ctx, H.time_params(dt=dt), H.state_struct(*z), 0, 0)
     rhs = torch.as_tensor(inputs.random_vector(4 * N, seed=1), device="cuda")
-    sp = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, graph=1,
+    sp = H.solver_params(outer_rtol=1e-10, sub_rtol=1e-2, precision=H.HYEL_PREC_FP32, graph=graph,
                          a_precond=H.HYEL_APREC_AMG, s_precond=H.HYEL_SPREC_JACOBI)
     for rep in range(2):
         x = torch.zeros(4 * N, dtype=torch.float64, device="cuda")
@@ -560,7 +560,7 @@ def run_hyel(args, rank, world, local_rank):
         tm = inputs.tube_mesh()
         tin = H.MeshInputs(tm, inputs.material_hgo(3e4, 2e5, 5.0, 0.0), None, {"p_max": 0.0, "t_ramp": 1e-2})
         H.hyel_mesh_upload(ctx, tin.X, tin.tets, tin.bc, tin.mat)
-        res = stiff_tube_solve(ctx, H, torch, stream, tm["X"].shape[0])
+        res = stiff_tube_solve(ctx, H, torch, stream, tm["X"].shape[0], graph)
         H.hyel_destroy(ctx)
         if rank == 0:
             print(json.dumps({"stiff_solve_multigrid": res}), flush=True)
