@@ -29,8 +29,9 @@
 //   constraints remove entirely) gets a unit diagonal and stays zero.
 // * Application: one V-cycle in FP32 (for FP64 and FP32 levels alike). A
 //   degree-kSmoothDegree Chebyshev smoother on [lambda / kSmoothRatio, lambda]
-//   runs before and after the coarse correction; coarse-level products use 8
-//   lanes per row. The V-cycle is a fixed linear operator, used as the right
+//   runs before and after the coarse correction. Coarse-level products use 8
+//   lanes per row, or a warp on small levels; restrictions and the dense
+//   apply use a warp per row (their rows are long and few). The V-cycle is a fixed linear operator, used as the right
 //   preconditioner of the A-level (F)GMRES.
 #include <algorithm>
 #include <cmath>
@@ -50,6 +51,7 @@ constexpr int kCoarseDegree = 12;   // the smoother alone on a coarsest level ab
 constexpr int kPowerSteps = 15;
 constexpr double kLamMargin = 1.1;
 constexpr int kGjThreads = 256;
+constexpr int64_t kWarpRowsBelow = 8192;  // coarse levels with fewer block-nodes use a warp per row, others 8 lanes
 
 struct SellHost {
     std::vector<int32_t> slice_ptr, row_len, col, diag_slot, col_slice;
@@ -111,15 +113,15 @@ struct Level {
     int32_t *q_ptr = nullptr, *q_col = nullptr, *q_row = nullptr;      // CSR of Q = A_l P
     double *Q64 = nullptr;    // [nnzQ][9]
     // coarsest level with N <= kDenseMax: dense matrix and its inverse,
-    // transposed for the apply (dinvT[j n + i] = A^-1(i, j), n = 3N)
-    double *dense64 = nullptr, *dwork64 = nullptr, *dinvT64 = nullptr;
-    float *dinvT32 = nullptr;
+    // row-major (dinv[i n + j] = A^-1(i, j), n = 3N; FP64 in dwork64)
+    double *dense64 = nullptr, *dwork64 = nullptr;
+    float *dinv32 = nullptr;
     // FP32 work vectors of the V-cycle [3N]: right-hand side, iterate, residual;
     // two smoother directions [2][3N]; an FP64 [3N] pair for the power steps
     float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *e32 = nullptr;
     double *x64 = nullptr, *r64 = nullptr;
     int64_t nnzb = 0;  // stored blocks (valid entries)
-    int lanes = 1;     // lanes per row of this level's products (long rows on coarse levels)
+    int lanes = 1;     // lanes per row of this level's products: 1 on level 0, 8 or 32 on coarse levels (long rows)
 };
 
 }  // namespace
@@ -471,12 +473,11 @@ __global__ void k_dense_scatter(const int32_t *__restrict__ slice_ptr, const int
 
 // Gauss-Jordan elimination with partial pivoting of the n x n matrix M (row-
 // major, overwritten; ties in the pivot search go to the lower row), one
-// block; W receives the inverse, invT its transpose in FP64 and FP32. A row
+// block; W receives the inverse (row-major) and inv32 its FP32 copy. A row
 // and column that are entirely zero get a unit diagonal first. A pivot below
 // 1e-14 max|M| sets ERR_SINGULAR.
 __global__ void __launch_bounds__(kGjThreads) k_gauss_jordan(double *__restrict__ M, double *__restrict__ W,
-                                                             double *__restrict__ invT64, float *__restrict__ invT32,
-                                                             int n, unsigned *err) {
+                                                             float *__restrict__ inv32, int n, unsigned *err) {
     __shared__ double fcol[3 * kDenseMax];
     __shared__ double s_val[kGjThreads];
     __shared__ int s_idx[kGjThreads];
@@ -560,21 +561,22 @@ __global__ void __launch_bounds__(kGjThreads) k_gauss_jordan(double *__restrict_
         }
         __syncthreads();
     }
-    for (int64_t e = tid; e < nn; e += kGjThreads) {
-        const int i = (int)(e / n), j = (int)(e % n);
-        invT64[(int64_t)j * n + i] = W[e];
-        invT32[(int64_t)j * n + i] = (float)W[e];
-    }
+    for (int64_t e = tid; e < nn; e += kGjThreads) inv32[e] = (float)W[e];
 }
 
-// x = A^-1 b on the coarsest level from the transposed dense inverse
+// x = A^-1 b on the coarsest level from the row-major dense inverse, one warp
+// per row (lane l takes the columns j = l, l + 32, ...; shuffle sum)
 template <typename T>
-__global__ void k_dense_apply(const T *__restrict__ invT, const T *__restrict__ b, T *__restrict__ x, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__global__ void __launch_bounds__(128) k_dense_apply(const T *__restrict__ inv, const T *__restrict__ b,
+                                                     T *__restrict__ x, int n) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g >> 5, lane = g & 31;
     T s = 0;
-    for (int j = 0; j < n; j++) s = fma(invT[(int64_t)j * n + i], b[j], s);
-    x[i] = s;
+    if (i < n)
+        for (int j = lane; j < n; j += 32) s = fma(inv[(int64_t)i * n + j], b[j], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && i < n) x[i] = s;
 }
 
 // (A x)_i of a SELL level over L lanes per row: lane l takes the entries
@@ -770,7 +772,7 @@ struct LvView<float> {
     static const float *A(const Level &l) { return l.A32; }
     static const float *J(const Level &l) { return l.jac32; }
     static const float *P(const Level &l) { return l.P32; }
-    static const float *D(const Level &l) { return l.dinvT32; }
+    static const float *D(const Level &l) { return l.dinv32; }
     static float *b(Level &l) { return l.b32; }
     static float *x(Level &l) { return l.x32; }
     static float *r(Level &l) { return l.r32; }
@@ -791,7 +793,9 @@ template <typename T>
 void start_launch(Ctx &c, Level &L, T *x, const T *b, T *r, T *d, int from_zero, int with_d) {
     const LvOp<T> o = lv_op<T>(L);
     const int64_t th = L.N * L.lanes;
-    if (L.lanes == 8)
+    if (L.lanes == 32)
+        AMG_LAUNCH(k_cheb_start<T, 32><<<blocks_for(th, 128), 128, 0, c.stream>>>(o, x, b, r, d, from_zero, with_d));
+    else if (L.lanes == 8)
         AMG_LAUNCH(k_cheb_start<T, 8><<<blocks_for(th, 128), 128, 0, c.stream>>>(o, x, b, r, d, from_zero, with_d));
     else
         AMG_LAUNCH(k_cheb_start<T, 1><<<blocks_for(th, 128), 128, 0, c.stream>>>(o, x, b, r, d, from_zero, with_d));
@@ -808,7 +812,10 @@ void cheb_smooth(Ctx &c, Level &L, int degree, bool from_zero) {
     start_launch<T>(c, L, x, V::b(L), r, d[0], from_zero ? 1 : 0, 1);
     const int64_t th = L.N * L.lanes;
     for (int k = 1; k < degree; k++) {
-        if (L.lanes == 8)
+        if (L.lanes == 32)
+            AMG_LAUNCH(k_cheb_step<T, 32><<<blocks_for(th, 128), 128, 0, c.stream>>>(o, x, r, d[(k - 1) & 1],
+                                                                                     d[k & 1], k));
+        else if (L.lanes == 8)
             AMG_LAUNCH(k_cheb_step<T, 8><<<blocks_for(th, 128), 128, 0, c.stream>>>(o, x, r, d[(k - 1) & 1],
                                                                                     d[k & 1], k));
         else
@@ -823,9 +830,10 @@ void vcycle(Ctx &c, Amg &a, int l) {
     Level &L = a.lv[l];
     using V = LvView<T>;
     if (l + 1 == (int)a.lv.size()) {  // coarsest: dense inverse, or the smoother when coarsening stalled
-        if (L.dinvT64) {
+        if (L.dinv32) {
             const int n = (int)(3 * L.N);
-            AMG_LAUNCH(k_dense_apply<T><<<blocks_for(n, 128), 128, 0, c.stream>>>(V::D(L), V::b(L), V::x(L), n));
+            AMG_LAUNCH(k_dense_apply<T><<<blocks_for(32 * (int64_t)n, 128), 128, 0, c.stream>>>(V::D(L), V::b(L),
+                                                                                                 V::x(L), n));
         } else {
             cheb_smooth<T>(c, L, kCoarseDegree, true);
         }
@@ -834,9 +842,9 @@ void vcycle(Ctx &c, Amg &a, int l) {
     Level &C = a.lv[l + 1];
     cheb_smooth<T>(c, L, kSmoothDegree, true);
     start_launch<T>(c, L, V::x(L), V::b(L), V::r(L), nullptr, 0, 0);
-    const int64_t th = C.N * 8;
-    AMG_LAUNCH(k_sa_restrict<T, 8><<<blocks_for(th, 128), 128, 0, c.stream>>>(L.pt_ptr, L.pt_row, L.pt_slot, V::P(L),
-                                                                                V::r(L), V::b(C), C.N));
+    const int64_t th = C.N * 32;
+    AMG_LAUNCH(k_sa_restrict<T, 32><<<blocks_for(th, 128), 128, 0, c.stream>>>(L.pt_ptr, L.pt_row, L.pt_slot,
+                                                                                 V::P(L), V::r(L), V::b(C), C.N));
     vcycle<T>(c, a, l + 1);
     AMG_LAUNCH(k_sa_prolong<T><<<blocks_for(L.N, 128), 128, 0, c.stream>>>(L.p_ptr, L.p_col, V::P(L), V::x(C),
                                                                              V::x(L), L.N));
@@ -1090,7 +1098,7 @@ static void amg_build(Ctx &c) {
         L.jac64 = dalloc_n<double>(c, 9 * (size_t)Nc);
         L.jac32 = dalloc_n<float>(c, 9 * (size_t)Nc);
         L.nnzb = (int64_t)ccols.size();
-        L.lanes = 8;
+        L.lanes = Nc < kWarpRowsBelow ? 32 : 8;
         a->lv.push_back(L);
         // the next level's super-nodes are this level's aggregates
         N = Nc;
@@ -1117,8 +1125,7 @@ static void amg_build(Ctx &c) {
         const size_t n = 3 * (size_t)Lc.N;
         Lc.dense64 = dalloc_n<double>(c, n * n);
         Lc.dwork64 = dalloc_n<double>(c, n * n);
-        Lc.dinvT64 = dalloc_n<double>(c, n * n);
-        Lc.dinvT32 = dalloc_n<float>(c, n * n);
+        Lc.dinv32 = dalloc_n<float>(c, n * n);
     }
     a->partial = dalloc_n<double>(c, (size_t)blocks_for(a->lv[0].N, 128));
     a->pscale = dalloc_n<double>(c, 1);
@@ -1153,12 +1160,12 @@ void amg_numeric(Ctx &c) {
     for (int l = 0; l < nlev; l++) {
         Level &F = a.lv[l];
         if (l + 1 == nlev) {
-            if (F.dinvT64) {
+            if (F.dinv32) {
                 const int64_t n = 3 * F.N;
                 HYEL_CK(cudaMemsetAsync(F.dense64, 0, (size_t)(n * n) * sizeof(double), c.stream));
                 AMG_LAUNCH(k_dense_scatter<<<blocks_for(F.nslots, 128), 128, 0, c.stream>>>(
                     F.slice_ptr, F.row_len, F.col, F.col_slice, F.A64, F.dense64, F.N, F.nslots));
-                AMG_LAUNCH(k_gauss_jordan<<<1, kGjThreads, 0, c.stream>>>(F.dense64, F.dwork64, F.dinvT64, F.dinvT32,
+                AMG_LAUNCH(k_gauss_jordan<<<1, kGjThreads, 0, c.stream>>>(F.dense64, F.dwork64, F.dinv32,
                                                                          (int)n, c.err));
             } else {
                 power_estimate(c, a, F);
