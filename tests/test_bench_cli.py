@@ -15,7 +15,8 @@ def test_help():
     r = subprocess.run([sys.executable, BENCH, "--help"], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     for opt in ("--s-precond", "--cheb-degree", "--a-precond", "--block", "--inner", "--dt", "--nu", "--no-sweep",
-                "--no-tube", "--no-mixed", "--no-e2e", "--no-cpu"):
+                "--no-tube", "--no-mixed", "--no-e2e", "--no-cpu", "--tube-only", "--tube-dt", "--stiff-only",
+                "--compare-a-precond", "--host-loops"):
         assert opt in r.stdout, opt
 
 
